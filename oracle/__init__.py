@@ -1,0 +1,211 @@
+"""CPU oracle (plain C, loaded through ctypes) for the divergence estimator.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the benchmark's CPU-baseline / reference leg may import this package.
+The product path (``paper_2209_13168_gb300``) never imports it and shares no
+code with it.
+
+What each function follows (paper: McLeod et al., arXiv 2209.13168):
+  warp_cells      Eq. (11), binary32, fixed operation order
+  scale, scale_interval  the warp scale and the bound's widened scale range
+  contrast        Eqs. (12)-(13) as the integer key K = M*S - N_in^2 = M^2 C
+  bound           Eqs. (14)-(19) as Kbar = M*Sbar - N_full^2 >= K(D)
+  solve           Algorithm 1 (pop-K rounds; K_pop = 1 is Algorithm 1 itself)
+  grid_max        exhaustive dense grid (brute force)
+  sweep_max       exact breakpoint sweep (brute force)
+  fp64_disagreements  the same warp in binary64, diagnostic only
+
+Every function is pinned by tests/test_oracle_*.py against closed forms,
+invariants and brute force; none is marked "parity unpinned".
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+
+
+def build(force=False):
+    """Compile oracle.c into liboracle.so next to it (gcc, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc"] + CFLAGS + ["-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Win(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("foe_x", ctypes.c_float),
+                ("foe_y", ctypes.c_float), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("n", ctypes.c_int64), ("t0", ctypes.c_float),
+                ("tau", ctypes.c_float)]
+
+
+class _I128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_int64)]
+
+    def value(self):
+        return (int(self.hi) << 64) | int(self.lo)
+
+
+class _Res(ctypes.Structure):
+    _fields_ = [("D_star", ctypes.c_float), ("D_end", ctypes.c_float), ("contrast", ctypes.c_double),
+                ("bound_gap", ctypes.c_double), ("K_hat", _I128), ("gap_K", _I128),
+                ("nodes_expanded", ctypes.c_int64), ("point_evals", ctypes.c_int64),
+                ("bound_evals", ctypes.c_int64), ("event_warps", ctypes.c_int64),
+                ("cell_increments", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("max_queue", ctypes.c_int64), ("status", ctypes.c_int32)]
+
+
+class _Rec(ctypes.Structure):
+    _fields_ = [("D_lo", ctypes.c_float), ("D_hi", ctypes.c_float), ("D_c", ctypes.c_float),
+                ("leaf", ctypes.c_int32), ("Kbar", _I128), ("K_c", _I128)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER
+        L.or_validate.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float]
+        L.or_warp_cells.argtypes = [P(_Win), ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_warp_cells.restype = None
+        L.or_fp64_disagreements.argtypes = [P(_Win), ctypes.c_float]
+        L.or_fp64_disagreements.restype = ctypes.c_int64
+        L.or_scale.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        L.or_scale.restype = ctypes.c_float
+        L.or_scale_interval.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        P(ctypes.c_float), P(ctypes.c_float)]
+        L.or_scale_interval.restype = None
+        L.or_contrast.argtypes = [P(_Win), ctypes.c_float, P(_I128), P(ctypes.c_uint64),
+                                  P(ctypes.c_int64), ctypes.c_void_p]
+        L.or_bound.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, P(_I128), P(ctypes.c_uint64),
+                               P(ctypes.c_int64), ctypes.c_void_p]
+        L.or_solve.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_double,
+                               ctypes.c_int32, P(_Res), ctypes.c_void_p, ctypes.c_int64,
+                               P(ctypes.c_int64)]
+        L.or_grid_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, P(_I128),
+                                  P(ctypes.c_float), P(ctypes.c_int64)]
+        L.or_sweep_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, P(_I128), P(ctypes.c_float),
+                                   P(ctypes.c_int64)]
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != 0:
+        raise OracleError("oracle returned %d" % rc)
+
+
+class Window:
+    """Keeps the SoA arrays alive and exposes the C struct."""
+
+    def __init__(self, W, H, foe_x, foe_y, x, y, t, t0=0.0, tau=0.5):
+        self.x = np.ascontiguousarray(x, dtype=np.int16)
+        self.y = np.ascontiguousarray(y, dtype=np.int16)
+        self.t = np.ascontiguousarray(t, dtype=np.float32)
+        self.W, self.H = int(W), int(H)
+        self.c = _Win(int(W), int(H), float(foe_x), float(foe_y), self.x.ctypes.data,
+                      self.y.ctypes.data, self.t.ctypes.data, int(self.x.size), float(t0), float(tau))
+
+    @classmethod
+    def of(cls, w):
+        """From a synth.Window."""
+        return cls(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, w.t0, w.tau)
+
+    @property
+    def M(self):
+        return self.W * self.H
+
+
+def validate(win, D_lo, D_hi):
+    return lib().or_validate(ctypes.byref(win.c), D_lo, D_hi)
+
+
+def warp_cells(win, D):
+    ux = np.zeros(win.x.size, np.int32)
+    uy = np.zeros(win.x.size, np.int32)
+    lib().or_warp_cells(ctypes.byref(win.c), D, ux.ctypes.data, uy.ctypes.data)
+    return ux, uy
+
+
+def fp64_disagreements(win, D):
+    return int(lib().or_fp64_disagreements(ctypes.byref(win.c), D))
+
+
+def scale(D, t_rel, tau):
+    """The binary32 warp scale s(D) = (1 - D t)/(1 - D tau) of Eq. (11)."""
+    return float(lib().or_scale(D, t_rel, tau))
+
+
+def scale_interval(D_lo, D_hi, t_rel, tau):
+    """The widened scale interval [s_a, s_b] the bound uses for one event."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    lib().or_scale_interval(D_lo, D_hi, t_rel, tau, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def contrast(win, D, want_iwe=False):
+    """(K, S, N_in, iwe-or-None) at hypothesis D."""
+    k, s, n = _I128(), ctypes.c_uint64(), ctypes.c_int64()
+    img = np.zeros(win.M, np.uint32) if want_iwe else None
+    _check(lib().or_contrast(ctypes.byref(win.c), D, ctypes.byref(k), ctypes.byref(s), ctypes.byref(n),
+                             img.ctypes.data if want_iwe else None))
+    return k.value(), int(s.value), int(n.value), (img.reshape(win.H, win.W) if want_iwe else None)
+
+
+def bound(win, D_lo, D_hi, want_iwe=False):
+    """(Kbar, Sbar, N_full, iwe-or-None) over [D_lo, D_hi]."""
+    k, s, n = _I128(), ctypes.c_uint64(), ctypes.c_int64()
+    img = np.zeros(win.M, np.uint32) if want_iwe else None
+    _check(lib().or_bound(ctypes.byref(win.c), D_lo, D_hi, ctypes.byref(k), ctypes.byref(s),
+                          ctypes.byref(n), img.ctypes.data if want_iwe else None))
+    return k.value(), int(s.value), int(n.value), (img.reshape(win.H, win.W) if want_iwe else None)
+
+
+def solve(win, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, K_pop=1, trace_cap=0):
+    r = _Res()
+    tr = (_Rec * trace_cap)() if trace_cap else None
+    tl = ctypes.c_int64(0)
+    _check(lib().or_solve(ctypes.byref(win.c), D_lo, D_hi, tol_D, gamma, K_pop, ctypes.byref(r),
+                          ctypes.cast(tr, ctypes.c_void_p) if tr is not None else None, trace_cap,
+                          ctypes.byref(tl)))
+    out = {f: getattr(r, f) for f, _ in _Res._fields_ if f not in ("K_hat", "gap_K")}
+    out["K_hat"] = r.K_hat.value()
+    out["gap_K"] = r.gap_K.value()
+    if tr is not None:
+        n = min(tl.value, trace_cap)
+        out["trace"] = [(tr[i].D_lo, tr[i].D_hi, tr[i].D_c, tr[i].leaf, tr[i].Kbar.value(), tr[i].K_c.value())
+                        for i in range(n)]
+        out["trace_len"] = tl.value
+    return out
+
+
+def grid_max(win, D_lo, D_hi, h):
+    k, d, n = _I128(), ctypes.c_float(), ctypes.c_int64()
+    _check(lib().or_grid_max(ctypes.byref(win.c), D_lo, D_hi, h, ctypes.byref(k), ctypes.byref(d),
+                             ctypes.byref(n)))
+    return k.value(), d.value, n.value
+
+
+def sweep_max(win, D_lo, D_hi):
+    k, d, n = _I128(), ctypes.c_float(), ctypes.c_int64()
+    _check(lib().or_sweep_max(ctypes.byref(win.c), D_lo, D_hi, ctypes.byref(k), ctypes.byref(d),
+                              ctypes.byref(n)))
+    return k.value(), d.value, n.value

@@ -1,0 +1,549 @@
+/*
+ * CPU oracle for exact contrast-maximisation divergence estimation
+ * (arXiv 2209.13168).  TEST INFRASTRUCTURE ONLY: see oracle.h.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC.
+ * Every float operation below is one IEEE-754 binary32 operation rounded to
+ * nearest (no contraction into FMA, no excess precision), in the order
+ * written.  The pixel a warped event falls in is an integer decided by
+ * floating point, so it is decided in binary32 here exactly as the kernels
+ * decide it.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+static or_i128 pack(i128 v) {
+    or_i128 r;
+    r.lo = (uint64_t)(u128)v;
+    r.hi = (int64_t)(uint64_t)((u128)v >> 64);
+    return r;
+}
+
+/* ---------------------------------------------------------------- domain */
+
+/* Reading of Sec. 4.1: nu in [-1/tau, 0] with Z0 = 1 becomes D = -nu; the
+ * singular end D = 1/tau (1 + nu tau = 0) is excluded.  The bound's widening
+ * (or_bound) is proven sufficient for D tau <= 3/4, so the domain is
+ * D tau in [-64, 3/4]. */
+static int d_ok(float D, float tau) {
+    if (!isfinite(D)) return 0;
+    double dt = (double)D * (double)tau;
+    return dt <= 0.75 && dt >= -64.0;
+}
+
+int or_validate(const or_window* w, float D_lo, float D_hi) {
+    if (!w || w->n < 0 || w->W < 1 || w->H < 1 || w->W > 4096 || w->H > 4096) return OR_ERR_ARG;
+    if (w->n > 0 && (!w->x || !w->y || !w->t)) return OR_ERR_ARG;
+    if (!isfinite(w->foe_x) || !isfinite(w->foe_y) || w->foe_x < 0.0f || w->foe_y < 0.0f ||
+        w->foe_x > (float)w->W || w->foe_y > (float)w->H) return OR_ERR_ARG;
+    if (!isfinite(w->tau) || !(w->tau > 0.0f) || !isfinite(w->t0)) return OR_ERR_ARG;
+    if (!d_ok(D_lo, w->tau) || !d_ok(D_hi, w->tau) || !(D_lo <= D_hi)) return OR_ERR_ARG;
+    for (int64_t i = 0; i < w->n; i++) {
+        float ti = w->t[i] - w->t0;
+        if (!isfinite(w->t[i]) || !(ti >= 0.0f) || !(ti <= w->tau)) return OR_ERR_ARG;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ warp */
+
+/* Eq. (11) with Z0 = 1 and nu = -D: the event keeps its direction from the
+ * FOE and its offset is scaled by s_i(D) = (1 - D t_i) / (1 - D tau).
+ * Evaluated as g = 1/(1 - D*tau) once per hypothesis, then
+ * s_i = (1 - D*t_i) * g. */
+static float warp_g(float D, float tau) {
+    float q = 1.0f - D * tau;
+    return 1.0f / q;
+}
+static float warp_s(float D, float ti, float g) {
+    float a = 1.0f - D * ti;
+    return a * g;
+}
+/* Eq. (12): "lies in pixel u".  Pixel u covers [u - 1/2, u + 1/2), so
+ * integer event coordinates are pixel centres (reading; the paper is silent). */
+static int32_t cell(float foe, float d, float s) {
+    float p = foe + d * s;
+    return (int32_t)floorf(p + 0.5f);
+}
+
+void or_warp_cells(const or_window* w, float D, int32_t* ux, int32_t* uy) {
+    float g = warp_g(D, w->tau);
+    for (int64_t i = 0; i < w->n; i++) {
+        float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
+        float s = warp_s(D, w->t[i] - w->t0, g);
+        ux[i] = cell(w->foe_x, dx, s);
+        uy[i] = cell(w->foe_y, dy, s);
+    }
+}
+
+/* The same warp in binary64 throughout; reports how many events land in a
+ * different pixel than the binary32 warp.  Diagnostic only. */
+int64_t or_fp64_disagreements(const or_window* w, float D) {
+    int64_t bad = 0;
+    float g = warp_g(D, w->tau);
+    double Dd = D, tau = w->tau;
+    for (int64_t i = 0; i < w->n; i++) {
+        float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
+        float s = warp_s(D, w->t[i] - w->t0, g);
+        double ti = (double)(w->t[i] - w->t0);
+        double sd = (1.0 - Dd * ti) / (1.0 - Dd * tau);
+        double X = (double)w->x[i] - (double)w->foe_x, Y = (double)w->y[i] - (double)w->foe_y;
+        int64_t ux = (int64_t)floor((double)w->foe_x + X * sd + 0.5);
+        int64_t uy = (int64_t)floor((double)w->foe_y + Y * sd + 0.5);
+        if (ux != cell(w->foe_x, dx, s) || uy != cell(w->foe_y, dy, s)) bad++;
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------- contrast */
+
+/* Eqs. (12)-(13).  C = (1/M) sum_u (H - mu)^2 = sum_u H^2 / M - mu^2 with
+ * mu = N_in / M (the rewrite used in the supplementary proof), so
+ *     M^2 C = M * S - N_in^2 =: K,  S = sum_u H(u)^2,  N_in = sum_u H(u),
+ * an exact integer.  Comparisons of contrast are comparisons of K. */
+static i128 key(int64_t M, uint64_t S, int64_t N) {
+    return (i128)M * (i128)S - (i128)N * (i128)N;
+}
+
+static void sums(const uint32_t* img, int64_t M, uint64_t* S, int64_t* N) {
+    uint64_t s = 0;
+    int64_t n = 0;
+    for (int64_t u = 0; u < M; u++) {
+        s += (uint64_t)img[u] * (uint64_t)img[u];
+        n += img[u];
+    }
+    *S = s;
+    *N = n;
+}
+
+static void iwe_point(const or_window* w, float D, uint32_t* img) {
+    int64_t M = (int64_t)w->W * w->H;
+    memset(img, 0, (size_t)M * sizeof(uint32_t));
+    float g = warp_g(D, w->tau);
+    for (int64_t i = 0; i < w->n; i++) {
+        float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
+        float s = warp_s(D, w->t[i] - w->t0, g);
+        int32_t ux = cell(w->foe_x, dx, s), uy = cell(w->foe_y, dy, s);
+        if (ux >= 0 && ux < w->W && uy >= 0 && uy < w->H) img[(int64_t)uy * w->W + ux] += 1;
+    }
+}
+
+static i128 eval_point(const or_window* w, float D, uint32_t* img, uint64_t* S, int64_t* N) {
+    iwe_point(w, D, img);
+    sums(img, (int64_t)w->W * w->H, S, N);
+    return key((int64_t)w->W * w->H, *S, *N);
+}
+
+int or_contrast(const or_window* w, float D, or_i128* K, uint64_t* S, int64_t* N_in, uint32_t* iwe) {
+    int rc = or_validate(w, D, D);
+    if (rc) return rc;
+    int64_t M = (int64_t)w->W * w->H;
+    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    if (!img) return OR_ERR_OOM;
+    uint64_t s;
+    int64_t n;
+    i128 k = eval_point(w, D, img, &s, &n);
+    if (!iwe) free(img);
+    if (K) *K = pack(k);
+    if (S) *S = s;
+    if (N_in) *N_in = n;
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------- bound */
+
+/* Relative widening of the scale interval.  For D tau <= 3/4 the binary32
+ * evaluation of s_i(D) has relative error below 10 * 2^-24 against the real
+ * s_i(D), and the real s_i is monotone in D (ds/dD = (tau - t)/(1 - D tau)^2
+ * >= 0), so every binary32 s_i(D) with D in [D_lo, D_hi] lies inside
+ * [min(s_lo, s_hi)(1 - 2^-19), max(s_lo, s_hi)(1 + 2^-19)].  The paper argues
+ * in real arithmetic (supplementary proof of Eq. (17)); this widening is the
+ * reading that keeps the bound valid for the binary32 warp. */
+static const float WIDEN_DN = 1.0f - 0x1p-19f;
+static const float WIDEN_UP = 1.0f + 0x1p-19f;
+/* Half a pixel plus a margin of 2^-8 pixel, which exceeds the rounding error
+ * of the binary32 cell computation for coordinates below 4096. */
+static const float HALF_PLUS = 0.50390625f;
+
+/* Eq. (16) for one event: every pixel the segment f_i(D_lo) <-> f_i(D_hi)
+ * passes through gets +1 (each pixel at most once per event).  The segment
+ * is radial, s in [s_a, s_b].  Walk the cells of the axis with the larger
+ * |offset| (ties: x); for major cell k, the widened s-range in which the
+ * major coordinate rounds to k gives the run of minor cells.  Returns
+ * whether both end cells lie in the frame (Eq. (19)); the frame is convex and
+ * each cell coordinate is monotone in s, so then the whole segment does. */
+/* The widened scale interval [s_a, s_b] of one event over [D_lo, D_hi]. */
+static void scale_interval(float D_lo, float D_hi, float ti, float tau, float* sa, float* sb) {
+    float sl = warp_s(D_lo, ti, warp_g(D_lo, tau)), sh = warp_s(D_hi, ti, warp_g(D_hi, tau));
+    *sa = (sl < sh ? sl : sh) * WIDEN_DN;
+    *sb = (sl < sh ? sh : sl) * WIDEN_UP;
+}
+
+float or_scale(float D, float ti, float tau) { return warp_s(D, ti, warp_g(D, tau)); }
+
+void or_scale_interval(float D_lo, float D_hi, float ti, float tau, float* sa, float* sb) {
+    scale_interval(D_lo, D_hi, ti, tau, sa, sb);
+}
+
+static int segment(const or_window* w, float dx, float dy, float sa, float sb, uint32_t* img) {
+    const int32_t W = w->W, H = w->H;
+    int32_t xa = cell(w->foe_x, dx, sa), ya = cell(w->foe_y, dy, sa);
+    int32_t xb = cell(w->foe_x, dx, sb), yb = cell(w->foe_y, dy, sb);
+    int full = xa >= 0 && xa < W && ya >= 0 && ya < H && xb >= 0 && xb < W && yb >= 0 && yb < H;
+    if (dx == 0.0f && dy == 0.0f) {          /* event on the FOE: one pixel for every D */
+        if (xa >= 0 && xa < W && ya >= 0 && ya < H) img[(int64_t)ya * W + xa] += 1;
+        return full;
+    }
+    int major_x = fabsf(dx) >= fabsf(dy);
+    float fm = major_x ? w->foe_x : w->foe_y, fn = major_x ? w->foe_y : w->foe_x;
+    float dm = major_x ? dx : dy, dn = major_x ? dy : dx;
+    int32_t ka = major_x ? xa : ya, kb = major_x ? xb : yb;
+    int32_t Wm = major_x ? W : H, Wn = major_x ? H : W;
+    int32_t k0 = ka < kb ? ka : kb, k1 = ka < kb ? kb : ka;
+    if (k0 < 0) k0 = 0;
+    if (k1 > Wm - 1) k1 = Wm - 1;
+    float rm = 1.0f / dm;
+    for (int32_t k = k0; k <= k1; k++) {
+        float e = (float)k - fm;
+        float b1 = (e - HALF_PLUS) * rm, b2 = (e + HALF_PLUS) * rm;
+        float lo = b1 < b2 ? b1 : b2, hi = b1 < b2 ? b2 : b1;
+        if (lo < sa) lo = sa;
+        if (hi > sb) hi = sb;
+        if (lo > hi) continue;
+        int32_t j1 = cell(fn, dn, lo), j2 = cell(fn, dn, hi);
+        int32_t j0 = j1 < j2 ? j1 : j2, jn = j1 < j2 ? j2 : j1;
+        if (j0 < 0) j0 = 0;
+        if (jn > Wn - 1) jn = Wn - 1;
+        for (int32_t j = j0; j <= jn; j++) {
+            int64_t u = major_x ? (int64_t)j * W + k : (int64_t)k * W + j;
+            img[u] += 1;
+        }
+    }
+    return full;
+}
+
+/* Eqs. (14)-(19): Kbar = M * Sbar - N_full^2 with Sbar = sum_u Hbar(u)^2
+ * (Eq. (18)) and N_full = M * mu_lower (Eq. (19)).  Since Sbar >= S(D) and
+ * 0 <= N_full <= N_in(D) for every D in the interval, Kbar >= K(D). */
+static i128 eval_bound(const or_window* w, float D_lo, float D_hi, uint32_t* img, uint64_t* Sb,
+                       int64_t* Nfull, int64_t* n_cells) {
+    int64_t M = (int64_t)w->W * w->H;
+    memset(img, 0, (size_t)M * sizeof(uint32_t));
+    int64_t nf = 0;
+    for (int64_t i = 0; i < w->n; i++) {
+        float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
+        float sa, sb;
+        scale_interval(D_lo, D_hi, w->t[i] - w->t0, w->tau, &sa, &sb);
+        nf += segment(w, dx, dy, sa, sb, img);
+    }
+    sums(img, M, Sb, n_cells);
+    *Nfull = nf;
+    return key(M, *Sb, nf);
+}
+
+int or_bound(const or_window* w, float D_lo, float D_hi, or_i128* Kbar, uint64_t* Sbar,
+             int64_t* N_full, uint32_t* iwe) {
+    int rc = or_validate(w, D_lo, D_hi);
+    if (rc) return rc;
+    int64_t M = (int64_t)w->W * w->H;
+    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    if (!img) return OR_ERR_OOM;
+    uint64_t s;
+    int64_t nf, nc;
+    i128 k = eval_bound(w, D_lo, D_hi, img, &s, &nf, &nc);
+    if (!iwe) free(img);
+    if (Kbar) *Kbar = pack(k);
+    if (Sbar) *Sbar = s;
+    if (N_full) *N_full = nf;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ BnB */
+
+typedef struct { float lo, hi; i128 kb; } node;
+
+typedef struct { node* a; int64_t n, cap; } queue;
+
+static int q_push(queue* q, node v) {
+    if (q->n == q->cap) {
+        int64_t nc = q->cap ? 2 * q->cap : 64;
+        node* na = (node*)realloc(q->a, (size_t)nc * sizeof(node));
+        if (!na) return OR_ERR_OOM;
+        q->a = na;
+        q->cap = nc;
+    }
+    q->a[q->n++] = v;
+    return OR_OK;
+}
+
+/* Index of the first item of the priority queue: largest Kbar; among equal
+ * Kbar, the smaller D_lo (tie rule: a reading, the paper is silent). */
+static int64_t q_top(const queue* q) {
+    int64_t b = 0;
+    for (int64_t i = 1; i < q->n; i++)
+        if (q->a[i].kb > q->a[b].kb || (q->a[i].kb == q->a[b].kb && q->a[i].lo < q->a[b].lo)) b = i;
+    return b;
+}
+
+static node q_take(queue* q, int64_t i) {
+    node v = q->a[i];
+    q->a[i] = q->a[q->n - 1];
+    q->n--;
+    return v;
+}
+
+static float centre(float lo, float hi) { return lo + 0.5f * (hi - lo); }
+
+/* Algorithm 1 over D = -nu, in rounds that dequeue up to K_pop intervals
+ * (K_pop = 1 is Algorithm 1 step for step):
+ *   line 1   incumbent = centre of the domain, K_hat = K(centre)
+ *   line 2   insert the domain with priority Kbar
+ *   line 4-5 dequeue the first item; stop if Kbar - K_hat <= gamma_K
+ *            (gamma in contrast units, gamma_K = floor(gamma * M^2)); in a
+ *            round, dequeuing stops at the first item that passes this test
+ *            against the incumbent at the start of the round, and that item
+ *            stays queued
+ *   line 6-7 evaluate every dequeued centre; in dequeue order, a centre with
+ *            K >= K_hat becomes the incumbent
+ *   line 8   bisect at the centre, unless the interval is no wider than tol_D
+ *            (a leaf: its Kbar is kept in leaf_max and it is not split; the
+ *            paper has no width rule, binary32 bounds need one)
+ *   line 10  evaluate both child bounds; insert children with Kbar >= K_hat,
+ *            K_hat being the incumbent at the end of the round.
+ * The certificate is gap_K = max(0, max(leaf_max, Kbar of the item that
+ * stopped the search) - K_hat). */
+int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
+             or_result* out, or_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
+    int rc = or_validate(w, D_lo, D_hi);
+    if (rc) return rc;
+    if (!out || K_pop < 1 || !(D_lo < D_hi) || !(tol_D >= 0.0f) || !isfinite(tol_D) || !(gamma >= 0.0) ||
+        !isfinite(gamma))
+        return OR_ERR_ARG;
+    const int64_t M = (int64_t)w->W * w->H;
+    const i128 gamma_K = (i128)floor(gamma * (double)M * (double)M);
+    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    node* pop = (node*)malloc((size_t)K_pop * sizeof(node));
+    i128* kc = (i128*)malloc((size_t)K_pop * sizeof(i128));
+    float* dc = (float*)malloc((size_t)K_pop * sizeof(float));
+    node* kids = (node*)malloc((size_t)2 * K_pop * sizeof(node));
+    if (!img || !pop || !kc || !dc || !kids) {
+        free(img); free(pop); free(kc); free(dc); free(kids);
+        return OR_ERR_OOM;
+    }
+    queue q = {0, 0, 0};
+    or_result r;
+    memset(&r, 0, sizeof(r));
+    int64_t tl = 0, cells = 0;
+    uint64_t S;
+    int64_t N;
+
+    float D_hat = centre(D_lo, D_hi);                         /* line 1 */
+    i128 K_hat = eval_point(w, D_hat, img, &S, &N);
+    r.point_evals = 1;
+    cells += N;
+    node root = {D_lo, D_hi, 0};                              /* line 2 */
+    int64_t nf, nc;
+    root.kb = eval_bound(w, D_lo, D_hi, img, &S, &nf, &nc);
+    r.bound_evals = 1;
+    cells += nc;
+    if ((rc = q_push(&q, root))) goto done;
+    r.max_queue = 1;
+
+    int have_leaf = 0, have_stop = 0;
+    i128 leaf_max = 0, stop_kb = 0;
+    while (q.n > 0) {                                          /* line 3 */
+        const i128 K0 = K_hat;
+        int np = 0;
+        while (np < K_pop && q.n > 0) {                        /* line 4 */
+            int64_t b = q_top(&q);
+            if (q.a[b].kb - K0 <= gamma_K) {                   /* line 5 */
+                if (np == 0) { have_stop = 1; stop_kb = q.a[b].kb; }
+                break;
+            }
+            pop[np++] = q_take(&q, b);
+        }
+        if (np == 0) break;
+        r.rounds++;
+        for (int j = 0; j < np; j++) {                         /* line 6 */
+            dc[j] = centre(pop[j].lo, pop[j].hi);
+            kc[j] = eval_point(w, dc[j], img, &S, &N);
+            cells += N;
+            r.point_evals++;
+            r.nodes_expanded++;
+        }
+        for (int j = 0; j < np; j++)                           /* line 7 */
+            if (kc[j] >= K_hat) { K_hat = kc[j]; D_hat = dc[j]; }
+        int nk = 0;
+        for (int j = 0; j < np; j++) {                         /* line 8-9 */
+            int leaf = !((pop[j].hi - pop[j].lo) > tol_D) || !(dc[j] > pop[j].lo) || !(dc[j] < pop[j].hi);
+            if (trace && tl < trace_cap) {
+                or_node_rec* t = &trace[tl];
+                t->D_lo = pop[j].lo; t->D_hi = pop[j].hi; t->D_c = dc[j]; t->leaf = leaf;
+                t->Kbar = pack(pop[j].kb); t->K_c = pack(kc[j]);
+            }
+            tl++;
+            if (leaf) {
+                if (!have_leaf || pop[j].kb > leaf_max) leaf_max = pop[j].kb;
+                have_leaf = 1;
+                continue;
+            }
+            node a = {pop[j].lo, dc[j], 0}, b = {dc[j], pop[j].hi, 0};
+            a.kb = eval_bound(w, a.lo, a.hi, img, &S, &nf, &nc);
+            cells += nc;
+            b.kb = eval_bound(w, b.lo, b.hi, img, &S, &nf, &nc);
+            cells += nc;
+            r.bound_evals += 2;
+            kids[nk++] = a;
+            kids[nk++] = b;
+        }
+        for (int j = 0; j < nk; j++)                           /* line 10 */
+            if (kids[j].kb >= K_hat)
+                if ((rc = q_push(&q, kids[j]))) goto done;
+        if (q.n > r.max_queue) r.max_queue = q.n;
+    }
+    {
+        i128 top = K_hat;
+        if (have_leaf && leaf_max > top) top = leaf_max;
+        if (have_stop && stop_kb > top) top = stop_kb;
+        i128 gap = top - K_hat;
+        r.D_star = D_hat;
+        r.D_end = (float)((double)D_hat / (1.0 - (double)D_hat * (double)w->tau));
+        r.K_hat = pack(K_hat);
+        r.gap_K = pack(gap);
+        r.contrast = (double)K_hat / ((double)M * (double)M);
+        r.bound_gap = (double)gap / ((double)M * (double)M);
+        r.event_warps = w->n * (r.point_evals + r.bound_evals);
+        r.cell_increments = cells;
+        r.status = OR_OK;
+        *out = r;
+        if (trace_len) *trace_len = tl;
+    }
+done:
+    free(q.a); free(img); free(pop); free(kc); free(dc); free(kids);
+    return rc;
+}
+
+/* ------------------------------------------------------- brute force */
+
+/* Dense grid: K at D_lo + j h (rounded to binary32), j = 0, 1, ... while the
+ * point stays <= D_hi, plus D_hi itself.  Returns the largest K and the
+ * smallest grid D attaining it. */
+int or_grid_max(const or_window* w, float D_lo, float D_hi, float h, or_i128* K_max, float* D_at,
+                int64_t* n_evals) {
+    int rc = or_validate(w, D_lo, D_hi);
+    if (rc) return rc;
+    if (!(h > 0.0f)) return OR_ERR_ARG;
+    int64_t M = (int64_t)w->W * w->H;
+    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    if (!img) return OR_ERR_OOM;
+    int64_t steps = (int64_t)floor(((double)D_hi - (double)D_lo) / (double)h);
+    i128 best = 0;
+    float bd = D_lo;
+    int64_t ne = 0;
+    for (int64_t j = 0; j <= steps + 1; j++) {
+        float D = j <= steps ? (float)((double)D_lo + (double)j * (double)h) : D_hi;
+        if (D > D_hi) D = D_hi;
+        uint64_t S;
+        int64_t N;
+        i128 k = eval_point(w, D, img, &S, &N);
+        ne++;
+        if (ne == 1 || k > best || (k == best && D < bd)) { best = k; bd = D; }
+    }
+    free(img);
+    *K_max = pack(best);
+    *D_at = bd;
+    if (n_evals) *n_evals = ne;
+    return OR_OK;
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : x > y;
+}
+
+static void add_bp(double** bp, int64_t* n, int64_t* cap, double v) {
+    if (*n == *cap) {
+        *cap = *cap ? 2 * *cap : 1024;
+        *bp = (double*)realloc(*bp, (size_t)*cap * sizeof(double));
+    }
+    (*bp)[(*n)++] = v;
+}
+
+/* Breakpoint sweep.  K(D) is piecewise constant: an event changes pixel only
+ * where a coordinate of its warp crosses a pixel border k + 1/2, i.e. where
+ * FOE + d (1 - D t)/(1 - D tau) = k + 1/2, so D = (d - c)/(d t - c tau) with
+ * c = k + 1/2 - FOE (binary64).  K is evaluated at the binary32 values
+ * within 4 ulps of each breakpoint and at the binary32 midpoint of each gap
+ * between neighbouring breakpoints, plus D_lo and D_hi; the binary32 warp
+ * can only change pixel within a few ulps of a real breakpoint.  Exhaustive
+ * for tiny windows only (cost ~ breakpoints x N). */
+int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, float* D_at,
+                 int64_t* n_evals) {
+    int rc = or_validate(w, D_lo, D_hi);
+    if (rc) return rc;
+    double* bp = NULL;
+    int64_t nb = 0, cap = 0;
+    double tau = w->tau;
+    for (int64_t i = 0; i < w->n; i++) {
+        double ti = (double)(w->t[i] - w->t0);
+        for (int ax = 0; ax < 2; ax++) {
+            double foe = ax ? w->foe_y : w->foe_x;
+            double d = (double)(ax ? w->y[i] : w->x[i]) - foe;
+            if (d == 0.0) continue;
+            double sl = (1.0 - D_lo * ti) / (1.0 - D_lo * tau), sh = (1.0 - D_hi * ti) / (1.0 - D_hi * tau);
+            double p1 = foe + d * sl, p2 = foe + d * sh;
+            double pmin = p1 < p2 ? p1 : p2, pmax = p1 < p2 ? p2 : p1;
+            for (int64_t k = (int64_t)floor(pmin - 0.5) - 1; k <= (int64_t)floor(pmax - 0.5) + 1; k++) {
+                double c = (double)k + 0.5 - foe;
+                double den = d * ti - c * tau;
+                if (den == 0.0) continue;
+                double D = (d - c) / den;
+                if (D >= D_lo && D <= D_hi) add_bp(&bp, &nb, &cap, D);
+            }
+        }
+    }
+    add_bp(&bp, &nb, &cap, D_lo);
+    add_bp(&bp, &nb, &cap, D_hi);
+    qsort(bp, (size_t)nb, sizeof(double), cmp_double);
+    int64_t M = (int64_t)w->W * w->H;
+    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    if (!img) { free(bp); return OR_ERR_OOM; }
+    i128 best = 0;
+    float bd = D_lo;
+    int64_t ne = 0;
+    for (int64_t b = 0; b < nb; b++) {
+        float cand[10];
+        int nc = 0;
+        float f = (float)bp[b];
+        float lo = f, hi = f;
+        cand[nc++] = f;
+        for (int u = 0; u < 4; u++) {
+            lo = nextafterf(lo, -INFINITY);
+            hi = nextafterf(hi, INFINITY);
+            cand[nc++] = lo;
+            cand[nc++] = hi;
+        }
+        if (b + 1 < nb) cand[nc++] = (float)(0.5 * (bp[b] + bp[b + 1]));
+        for (int c = 0; c < nc; c++) {
+            float D = cand[c];
+            if (!(D >= D_lo && D <= D_hi)) continue;
+            uint64_t S;
+            int64_t N;
+            i128 k = eval_point(w, D, img, &S, &N);
+            ne++;
+            if (ne == 1 || k > best || (k == best && D < bd)) { best = k; bd = D; }
+        }
+    }
+    free(img);
+    free(bp);
+    *K_max = pack(best);
+    *D_at = bd;
+    if (n_evals) *n_evals = ne;
+    return OR_OK;
+}
