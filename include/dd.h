@@ -1,0 +1,187 @@
+/*
+ * dd.h -- C ABI of the GB300 (sm_103a) exact divergence estimator.
+ *
+ * The estimator is the contrast-maximisation method of McLeod et al.,
+ * "Globally Optimal Event-Based Divergence Estimation for Ventral Landing"
+ * (arXiv 2209.13168): every event of a window is warped radially about the
+ * focus of expansion (FOE) to the end of the window (Eq. 11), counted into an
+ * image of warped events (IWE, Eq. 12), and the contrast of that image
+ * (Eq. 13) is maximised over the divergence by branch and bound
+ * (Algorithm 1) with the interval upper bound of Eqs. 14-19.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Search variable.  D is the divergence at the window start with Z0 = 1,
+ *   positive while approaching: D = -nu, where nu is the vertical velocity of
+ *   Sec. 4.1.  The warp of event i (pixel x_i, time t_i, relative to t0) is
+ *       x' = FOE + (x_i - FOE) * (1 - D t_i) / (1 - D tau),
+ *   evaluated in IEEE binary32 with one rounding per operation in the order
+ *       g = 1/(1 - D*tau);  s = (1 - D*t_i)*g;  x' = FOE + (x_i - FOE)*s,
+ *   and the pixel is floor(x' + 1/2) (pixel u covers [u - 1/2, u + 1/2)).
+ * - Domain.  Every D satisfies -64 <= D*tau <= 3/4 (the widening that keeps
+ *   the bound valid in binary32 is proven on that range; the paper's singular
+ *   end nu = -1/tau is excluded).
+ * - Contrast key.  Contrast is reported and compared as the exact integer
+ *       K = M * S - N_in^2 = M^2 * C,   S = sum_u H(u)^2,  N_in = sum_u H(u),
+ *   M = W*H, as a signed 128-bit value (dd_i128).
+ * - Status.  Every int-returning function returns DD_OK (0) or a negative
+ *   DD_ERR_* code; outputs are written only on DD_OK.  dd_strerror() names it.
+ * - Memory.  Host pointers are read (or written) during the call only and stay
+ *   owned by the caller.  With dd_events.device_ptrs = 1, x/y/t are device
+ *   pointers of the context's GPU, read in place and never retained.  The
+ *   context owns its device buffers (allocated by dd_create and grown on
+ *   demand), its CUDA stream and its BnB queue.
+ * - Threads.  A context is not thread-safe: use one context per host thread.
+ * - Events.  0 <= x < W, 0 <= y < H, t finite with 0 <= (t - t0) <= tau (the
+ *   difference taken in binary32).  Polarity is not read (Sec. 4.2).
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    DD_OK = 0,
+    DD_ERR_ARG = -1,            /* invalid argument or malformed events          */
+    DD_ERR_OOM = -2,            /* device or host allocation failed              */
+    DD_ERR_QUEUE_OVERFLOW = -3, /* the BnB queue exceeded its capacity           */
+    DD_ERR_TIMEOUT = -4,        /* the round limit was reached before the proof  */
+    DD_ERR_CUDA = -5,           /* a CUDA runtime call failed                    */
+    DD_ERR_NO_DEVICE = -6       /* no usable sm_103 device                       */
+};
+
+typedef struct dd_ctx dd_ctx;
+
+/* Signed 128-bit integer, two's complement, low word first. */
+typedef struct { uint64_t lo; int64_t hi; } dd_i128;
+
+/* Tuning knobs; pass NULL to dd_create for the defaults (0 = default). */
+typedef struct {
+    int32_t pop_k;          /* intervals dequeued per BnB round (default 1 = Algorithm 1) */
+    int32_t queue_capacity; /* BnB queue entries per window (default 8192)               */
+    int32_t band_rows;      /* rows of the shared-memory IWE tile (default: from W)      */
+    int32_t threads;        /* threads per block of the IWE kernels (default 512)        */
+    int32_t max_rounds;     /* BnB round limit, DD_ERR_TIMEOUT beyond (default 1<<20)    */
+    int32_t reserved[3];
+} dd_config;
+
+/* One window of events in structure-of-arrays form. */
+typedef struct {
+    const int16_t* x;       /* [n] pixel column                                    */
+    const int16_t* y;       /* [n] pixel row                                       */
+    const float* t;         /* [n] timestamp, in [t0, t0 + tau]                    */
+    int64_t n;              /* number of events, >= 0                              */
+    float t0;               /* window start                                        */
+    float tau;              /* window length, > 0                                  */
+    int32_t device_ptrs;    /* 0: host arrays (copied in); 1: device arrays        */
+} dd_events;
+
+/* Result of one exact solve (Algorithm 1). */
+typedef struct {
+    float D_star;           /* incumbent divergence (window start), Sec. 4.1       */
+    float D_end;            /* D_star/(1 - D_star tau): the paper's point estimate  */
+                            /* nu_s/(1 + nu_s tau) with nu_s = -D_star, sign       */
+                            /* flipped (positive while approaching), Sec. 4.1      */
+    double contrast;        /* K_hat / M^2 = C(D_star), Eq. 13                      */
+    double bound_gap;       /* gap_K / M^2: certified distance to the optimum       */
+    dd_i128 K_hat;          /* contrast key of D_star                               */
+    dd_i128 gap_K;          /* max(0, best open or leaf bound - K_hat)              */
+    int64_t nodes_expanded; /* intervals dequeued and evaluated                     */
+    int64_t point_evals;    /* contrast evaluations (root incumbent included)       */
+    int64_t bound_evals;    /* upper-bound evaluations                              */
+    int64_t event_warps;    /* n * (point_evals + bound_evals)                      */
+    int64_t cell_increments;/* IWE increments over all evaluations                  */
+    int64_t bound_increments;/* of which in bound images (Eq. 16)                   */
+    int64_t rounds;         /* BnB rounds (dequeue batches)                         */
+    int64_t max_queue;      /* largest queue length seen                            */
+    int32_t status;         /* DD_OK                                                */
+} dd_result;
+
+/* One expanded interval, in expansion order (dd_solve_trace). */
+typedef struct {
+    float D_lo, D_hi, D_c;
+    int32_t leaf;           /* 1: not split (width <= tol_D or unsplittable)        */
+    dd_i128 Kbar;           /* its bound key when dequeued                          */
+    dd_i128 K_c;            /* contrast key at its centre                           */
+} dd_node_rec;
+
+/* Create a context for W x H frames (1..4096 each) with the FOE at
+ * (foe_x, foe_y) in [0, W] x [0, H], on the current CUDA device (which must
+ * be sm_103).  Allocates the context's device buffers and stream.
+ * Errors: DD_ERR_ARG, DD_ERR_NO_DEVICE, DD_ERR_OOM, DD_ERR_CUDA. */
+int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* cfg, dd_ctx** out);
+
+/* Release everything the context owns.  NULL is ignored. */
+void dd_destroy(dd_ctx* ctx);
+
+/* Run the context's work on `stream` (a cudaStream_t of the context's
+ * device; NULL restores the context's own stream).  Every call still
+ * synchronises that stream before returning its host results. */
+int dd_set_stream(dd_ctx* ctx, void* stream);
+
+/* Eqs. 11-13: the contrast key at each of nD hypotheses D[j] (host array).
+ * Writes K[j] (required) and, where non-NULL, S[j], N_in[j], and the IWE of
+ * every hypothesis to iwe[j*M + y*W + x] (host, nD*M uint32).
+ * Errors: DD_ERR_ARG (bad events, D outside the domain, nD < 0), DD_ERR_OOM,
+ * DD_ERR_CUDA. */
+int dd_contrast(dd_ctx* ctx, const dd_events* ev, const float* D, int32_t nD, dd_i128* K,
+                uint64_t* S, int64_t* N_in, uint32_t* iwe);
+
+/* Eqs. 14-19: the bound key Kbar = M * Sbar - N_full^2 >= K(D) for every
+ * binary32 D in [D_lo[j], D_hi[j]], j < n (host arrays, D_lo[j] <= D_hi[j]).
+ * Hbar (Eq. 16) counts, per event, each pixel its segment
+ * f(D_lo) <-> f(D_hi) passes through; N_full (Eq. 19, times M) counts the
+ * events whose segment lies in the frame.  Optional outputs as dd_contrast.
+ * Errors: as dd_contrast. */
+int dd_bound(dd_ctx* ctx, const dd_events* ev, const float* D_lo, const float* D_hi, int32_t n,
+             dd_i128* Kbar, uint64_t* Sbar, int64_t* N_full, uint32_t* iwe);
+
+/* Algorithm 1: maximise the contrast over D in [D_lo, D_hi] (D_lo < D_hi).
+ * Intervals no wider than tol_D (>= 0) are not split; gamma >= 0 is the
+ * stopping gap of Algorithm 1 in contrast units.  The search runs on the
+ * GPU: bounds, contrasts, the priority queue (largest Kbar first, ties to the
+ * smaller D_lo), the incumbent update (a centre with K >= K_hat wins) and
+ * pruning.  With pop_k > 1 each round dequeues up to pop_k intervals.
+ * Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT,
+ * DD_ERR_CUDA. */
+int dd_solve(dd_ctx* ctx, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma,
+             dd_result* out);
+
+/* dd_solve that also records up to trace_cap expanded intervals (host
+ * array) and their total count in *trace_len. */
+int dd_solve_trace(dd_ctx* ctx, const dd_events* ev, float D_lo, float D_hi, float tol_D,
+                   double gamma, dd_result* out, dd_node_rec* trace, int64_t trace_cap,
+                   int64_t* trace_len);
+
+/* Counters of one context since dd_create or the last dd_reset_stats. */
+typedef struct {
+    int64_t kernel_launches;  /* kernels this library launched                      */
+    int64_t eval_launches;    /* of which IWE evaluation kernels                    */
+    int64_t h2d_bytes;        /* bytes copied host -> device                        */
+    int64_t d2h_bytes;        /* bytes copied device -> host                        */
+    int64_t host_syncs;       /* stream synchronisations                            */
+    int64_t timed_launches;   /* IWE kernel launches timed (dd_set_timing)          */
+    double eval_ms;           /* their summed device time, CUDA events on the        */
+                              /* context's stream                                   */
+} dd_stats;
+
+/* Read (and, with dd_reset_stats, clear) the counters.  No GPU work. */
+int dd_get_stats(dd_ctx* ctx, dd_stats* out);
+int dd_reset_stats(dd_ctx* ctx);
+
+/* enable != 0: bracket every IWE evaluation launch with CUDA events on the
+ * context's stream and add its duration to dd_stats.eval_ms (costs a few
+ * microseconds per launch; off by default). */
+int dd_set_timing(dd_ctx* ctx, int32_t enable);
+
+/* A static description of a status code. */
+const char* dd_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H */

@@ -61,7 +61,8 @@ class _Res(ctypes.Structure):
                 ("bound_gap", ctypes.c_double), ("K_hat", _I128), ("gap_K", _I128),
                 ("nodes_expanded", ctypes.c_int64), ("point_evals", ctypes.c_int64),
                 ("bound_evals", ctypes.c_int64), ("event_warps", ctypes.c_int64),
-                ("cell_increments", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("cell_increments", ctypes.c_int64), ("bound_increments", ctypes.c_int64),
+                ("rounds", ctypes.c_int64),
                 ("max_queue", ctypes.c_int64), ("status", ctypes.c_int32)]
 
 

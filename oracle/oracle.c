@@ -44,9 +44,11 @@ int or_validate(const or_window* w, float D_lo, float D_hi) {
         w->foe_x > (float)w->W || w->foe_y > (float)w->H) return OR_ERR_ARG;
     if (!isfinite(w->tau) || !(w->tau > 0.0f) || !isfinite(w->t0)) return OR_ERR_ARG;
     if (!d_ok(D_lo, w->tau) || !d_ok(D_hi, w->tau) || !(D_lo <= D_hi)) return OR_ERR_ARG;
+    /* Events come from a W x H sensor: pixel coordinates inside the frame. */
     for (int64_t i = 0; i < w->n; i++) {
         float ti = w->t[i] - w->t0;
         if (!isfinite(w->t[i]) || !(ti >= 0.0f) || !(ti <= w->tau)) return OR_ERR_ARG;
+        if (w->x[i] < 0 || w->x[i] >= w->W || w->y[i] < 0 || w->y[i] >= w->H) return OR_ERR_ARG;
     }
     return OR_OK;
 }
@@ -339,7 +341,7 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
     queue q = {0, 0, 0};
     or_result r;
     memset(&r, 0, sizeof(r));
-    int64_t tl = 0, cells = 0;
+    int64_t tl = 0, cells = 0, bcells = 0;
     uint64_t S;
     int64_t N;
 
@@ -352,6 +354,7 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
     root.kb = eval_bound(w, D_lo, D_hi, img, &S, &nf, &nc);
     r.bound_evals = 1;
     cells += nc;
+    bcells += nc;
     if ((rc = q_push(&q, root))) goto done;
     r.max_queue = 1;
 
@@ -396,8 +399,10 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
             node a = {pop[j].lo, dc[j], 0}, b = {dc[j], pop[j].hi, 0};
             a.kb = eval_bound(w, a.lo, a.hi, img, &S, &nf, &nc);
             cells += nc;
+            bcells += nc;
             b.kb = eval_bound(w, b.lo, b.hi, img, &S, &nf, &nc);
             cells += nc;
+            bcells += nc;
             r.bound_evals += 2;
             kids[nk++] = a;
             kids[nk++] = b;
@@ -420,6 +425,7 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
         r.bound_gap = (double)gap / ((double)M * (double)M);
         r.event_warps = w->n * (r.point_evals + r.bound_evals);
         r.cell_increments = cells;
+        r.bound_increments = bcells;
         r.status = OR_OK;
         *out = r;
         if (trace_len) *trace_len = tl;

@@ -42,7 +42,7 @@ typedef struct {
     double contrast, bound_gap;
     or_i128 K_hat, gap_K;
     int64_t nodes_expanded, point_evals, bound_evals, event_warps, cell_increments;
-    int64_t rounds, max_queue;
+    int64_t bound_increments, rounds, max_queue;
     int32_t status;
 } or_result;
 

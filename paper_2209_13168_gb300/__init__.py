@@ -1,0 +1,285 @@
+"""Python binding of libdd.so, the GB300 (sm_103a) exact divergence estimator.
+
+Argument marshalling only: every step of the estimator (event ingest, warp,
+IWE scatter, sums of squares, bounds, the branch-and-bound queue) runs in the
+CUDA kernels behind include/dd.h.  There is no CPU fallback: if libdd.so is
+missing or fails to load, every entry point raises.
+
+The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
+dd_solve_trace, dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing,
+dd_destroy, dd_strerror); ``Context`` wraps
+them for numpy arrays (host events) and torch CUDA tensors (device events).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdd.so")
+
+DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_NO_DEVICE = \
+    0, -1, -2, -3, -4, -5, -6
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, dd_strerror(status), status))
+
+
+class dd_i128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_int64)]
+
+    def value(self):
+        return (int(self.hi) << 64) | int(self.lo)
+
+
+class dd_config(ctypes.Structure):
+    _fields_ = [("pop_k", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("band_rows", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class dd_events(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("t0", ctypes.c_float), ("tau", ctypes.c_float), ("device_ptrs", ctypes.c_int32)]
+
+
+class dd_result(ctypes.Structure):
+    _fields_ = [("D_star", ctypes.c_float), ("D_end", ctypes.c_float), ("contrast", ctypes.c_double),
+                ("bound_gap", ctypes.c_double), ("K_hat", dd_i128), ("gap_K", dd_i128),
+                ("nodes_expanded", ctypes.c_int64), ("point_evals", ctypes.c_int64),
+                ("bound_evals", ctypes.c_int64), ("event_warps", ctypes.c_int64),
+                ("cell_increments", ctypes.c_int64), ("bound_increments", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("max_queue", ctypes.c_int64),
+                ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("K_hat", "gap_K")}
+        d["K_hat"] = self.K_hat.value()
+        d["gap_K"] = self.gap_K.value()
+        return d
+
+
+class dd_node_rec(ctypes.Structure):
+    _fields_ = [("D_lo", ctypes.c_float), ("D_hi", ctypes.c_float), ("D_c", ctypes.c_float),
+                ("leaf", ctypes.c_int32), ("Kbar", dd_i128), ("K_c", dd_i128)]
+
+
+class dd_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("eval_launches", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("host_syncs", ctypes.c_int64),
+                ("timed_launches", ctypes.c_int64), ("eval_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol include/dd.h declares, with its ctypes signature.
+_P = ctypes.POINTER
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "dd_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P(dd_config),
+                                 _P(_VP)]),
+    "dd_destroy": (None, [_VP]),
+    "dd_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "dd_contrast": (ctypes.c_int, [_VP, _P(dd_events), _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
+    "dd_bound": (ctypes.c_int, [_VP, _P(dd_events), _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
+    "dd_solve": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_double,
+                                _P(dd_result)]),
+    "dd_solve_trace": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_double, _P(dd_result), _VP, ctypes.c_int64, _P(ctypes.c_int64)]),
+    "dd_get_stats": (ctypes.c_int, [_VP, _P(dd_stats)]),
+    "dd_reset_stats": (ctypes.c_int, [_VP]),
+    "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load(path=None):
+    """Load libdd.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libdd.so not found at %s: build it with __graft_entry__.build() "
+                           "(the estimator has no CPU fallback)" % p)
+    L = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def dd_strerror(status):
+    return load().dd_strerror(int(status)).decode()
+
+
+def _check(rc, where):
+    if rc != DD_OK:
+        raise DDError(rc, where)
+
+
+def dd_create(W, H, foe_x, foe_y, cfg=None):
+    h = _VP()
+    _check(load().dd_create(W, H, foe_x, foe_y, ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
+           "dd_create")
+    return h
+
+
+def dd_destroy(h):
+    load().dd_destroy(h)
+
+
+def dd_set_stream(h, stream_ptr):
+    _check(load().dd_set_stream(h, _VP(stream_ptr) if stream_ptr else None), "dd_set_stream")
+
+
+def dd_get_stats(h):
+    s = dd_stats()
+    _check(load().dd_get_stats(h, ctypes.byref(s)), "dd_get_stats")
+    return s.as_dict()
+
+
+def dd_reset_stats(h):
+    _check(load().dd_reset_stats(h), "dd_reset_stats")
+
+
+def dd_set_timing(h, enable):
+    _check(load().dd_set_timing(h, 1 if enable else 0), "dd_set_timing")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Events:
+    """dd_events over numpy arrays (host) or torch CUDA tensors (device).
+
+    Holds references to the arrays so they outlive the call."""
+
+    def __init__(self, x, y, t, t0, tau):
+        dev = hasattr(x, "is_cuda") and x.is_cuda
+        if dev:
+            import torch
+            assert x.dtype == torch.int16 and y.dtype == torch.int16 and t.dtype == torch.float32
+            assert x.is_contiguous() and y.is_contiguous() and t.is_contiguous()
+        else:
+            x = np.ascontiguousarray(x, dtype=np.int16)
+            y = np.ascontiguousarray(y, dtype=np.int16)
+            t = np.ascontiguousarray(t, dtype=np.float32)
+        self.x, self.y, self.t = x, y, t
+        n = int(x.shape[0])
+        self.c = dd_events(_ptr(x) if n else None, _ptr(y) if n else None, _ptr(t) if n else None, n,
+                           float(t0), float(tau), 1 if dev else 0)
+
+    @classmethod
+    def of(cls, w, device=None):
+        """From a synth.Window; device='cuda' uploads the SoA as torch tensors."""
+        if device is None:
+            return cls(w.x, w.y, w.t, w.t0, w.tau)
+        import torch
+        return cls(torch.from_numpy(w.x).to(device), torch.from_numpy(w.y).to(device),
+                   torch.from_numpy(w.t).to(device), w.t0, w.tau)
+
+
+def dd_contrast(h, ev, D, want=("S", "N"), want_iwe=False, M=None):
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    n = D.size
+    K = (dd_i128 * max(n, 1))()
+    S = np.zeros(n, np.uint64)
+    N = np.zeros(n, np.int64)
+    img = np.zeros(n * M, np.uint32) if want_iwe else None
+    _check(load().dd_contrast(h, ctypes.byref(ev.c), D.ctypes.data, n, ctypes.cast(K, _VP), S.ctypes.data,
+                              N.ctypes.data, img.ctypes.data if want_iwe else None), "dd_contrast")
+    return [K[i].value() for i in range(n)], S, N, img
+
+
+def dd_bound(h, ev, D_lo, D_hi, want_iwe=False, M=None):
+    D_lo = np.ascontiguousarray(D_lo, dtype=np.float32)
+    D_hi = np.ascontiguousarray(D_hi, dtype=np.float32)
+    n = D_lo.size
+    K = (dd_i128 * max(n, 1))()
+    S = np.zeros(n, np.uint64)
+    N = np.zeros(n, np.int64)
+    img = np.zeros(n * M, np.uint32) if want_iwe else None
+    _check(load().dd_bound(h, ctypes.byref(ev.c), D_lo.ctypes.data, D_hi.ctypes.data, n, ctypes.cast(K, _VP),
+                           S.ctypes.data, N.ctypes.data, img.ctypes.data if want_iwe else None), "dd_bound")
+    return [K[i].value() for i in range(n)], S, N, img
+
+
+def dd_solve(h, ev, D_lo, D_hi, tol_D, gamma):
+    r = dd_result()
+    _check(load().dd_solve(h, ctypes.byref(ev.c), D_lo, D_hi, tol_D, gamma, ctypes.byref(r)), "dd_solve")
+    return r.as_dict()
+
+
+def dd_solve_trace(h, ev, D_lo, D_hi, tol_D, gamma, trace_cap):
+    r = dd_result()
+    tr = (dd_node_rec * max(trace_cap, 1))()
+    tl = ctypes.c_int64(0)
+    _check(load().dd_solve_trace(h, ctypes.byref(ev.c), D_lo, D_hi, tol_D, gamma, ctypes.byref(r),
+                                 ctypes.cast(tr, _VP), trace_cap, ctypes.byref(tl)), "dd_solve_trace")
+    d = r.as_dict()
+    d["trace"] = [(tr[i].D_lo, tr[i].D_hi, tr[i].D_c, tr[i].leaf, tr[i].Kbar.value(), tr[i].K_c.value())
+                  for i in range(min(tl.value, trace_cap))]
+    d["trace_len"] = tl.value
+    return d
+
+
+class Context:
+    """A dd_ctx for one frame geometry (W x H, FOE)."""
+
+    def __init__(self, W, H, foe_x, foe_y, pop_k=0, queue_capacity=0, band_rows=0, threads=0, max_rounds=0):
+        self.W, self.H = int(W), int(H)
+        self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds)
+        self.h = dd_create(self.W, self.H, float(foe_x), float(foe_y), self.cfg)
+
+    @property
+    def M(self):
+        return self.W * self.H
+
+    def close(self):
+        if self.h:
+            dd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        dd_set_stream(self.h, stream_ptr)
+
+    def stats(self):
+        return dd_get_stats(self.h)
+
+    def reset_stats(self):
+        dd_reset_stats(self.h)
+
+    def set_timing(self, enable):
+        dd_set_timing(self.h, enable)
+
+    def contrast(self, ev, D, want_iwe=False):
+        K, S, N, img = dd_contrast(self.h, ev, D, want_iwe=want_iwe, M=self.M)
+        return K, S, N, (img.reshape(-1, self.H, self.W) if want_iwe else None)
+
+    def bound(self, ev, D_lo, D_hi, want_iwe=False):
+        K, S, N, img = dd_bound(self.h, ev, D_lo, D_hi, want_iwe=want_iwe, M=self.M)
+        return K, S, N, (img.reshape(-1, self.H, self.W) if want_iwe else None)
+
+    def solve(self, ev, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, trace_cap=0):
+        if trace_cap:
+            return dd_solve_trace(self.h, ev, D_lo, D_hi, tol_D, gamma, trace_cap)
+        return dd_solve(self.h, ev, D_lo, D_hi, tol_D, gamma)

@@ -1,0 +1,96 @@
+// Internal types and launch interface shared by the kernels (dd_kernels.cu)
+// and the C-ABI host code (dd_api.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dd {
+
+typedef __int128 i128;
+
+// One event after ingest: pixel coordinates and the time since t0.
+struct __align__(8) Ev {
+    int16_t x, y;
+    float t;
+};
+
+enum TaskKind : int32_t { TASK_POINT = 0, TASK_BOUND = 1 };
+
+// One evaluation: the contrast at D_lo (TASK_POINT) or the bound over
+// [D_lo, D_hi] (TASK_BOUND).
+struct Task {
+    float D_lo, D_hi;
+    int32_t kind, pad;
+};
+
+// Per (task, tile) partial sums of one IWE tile.
+struct Partial {
+    unsigned long long S;      // sum of squared counts
+    unsigned long long cells;  // sum of counts (N_in for a point, increments for a bound)
+    unsigned long long full;   // events whose bound segment lies in the frame
+};
+
+struct __align__(16) Node {
+    float lo, hi;
+    int32_t pad0, pad1;
+    i128 kb;
+};
+
+struct __align__(16) Popped {
+    float lo, hi, c;
+    int32_t leaf;
+    i128 kb;
+    int32_t t_point, t_left, t_right, pad;
+};
+
+struct __align__(16) TraceRec {
+    float D_lo, D_hi, D_c;
+    int32_t leaf;
+    i128 Kbar, K_c;
+};
+
+enum Phase : int32_t { PH_INIT = 0, PH_RUN = 1, PH_DONE = 2 };
+
+constexpr int MAX_POP = 64;
+
+// Device-resident state of one BnB search (Algorithm 1).
+struct __align__(16) SolveState {
+    // parameters
+    i128 gamma_K;
+    int64_t M, max_rounds;
+    float D_lo, D_hi, tol, tau;
+    int32_t K_pop, qcap, trace_cap, pad0;
+    // search state
+    i128 K_hat, leaf_max, stop_kb;
+    float D_hat;
+    int32_t phase, status, n_tasks, n_pop, q_n, have_leaf, have_stop;
+    int64_t nodes_expanded, point_evals, bound_evals, cells, bcells, rounds, max_queue, trace_len;
+    Popped pop[MAX_POP];
+};
+
+// Geometry of a context.
+struct Geom {
+    int32_t W, H;
+    float fx, fy;
+    int32_t band_rows, n_tiles;
+};
+
+// Kernel launches (dd_kernels.cu).  All asynchronous on `s`.
+cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
+                          float t0, float tau, Ev* out, int32_t* row_count, int32_t* row_off,
+                          int32_t* cursor, int32_t* err, cudaStream_t s);
+cudaError_t launch_eval(const Geom& g, const Ev* ev, const int32_t* row_off, const Task* tasks,
+                        const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
+                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s);
+cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part,
+                        i128* key, unsigned long long* S, unsigned long long* cells,
+                        unsigned long long* full, cudaStream_t s);
+cudaError_t launch_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol,
+                        float tau, i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds,
+                        int32_t trace_cap, cudaStream_t s);
+cudaError_t launch_control(const Geom& g, SolveState* st, Node* queue, Task* tasks, const Partial* part,
+                           const int32_t* err, TraceRec* trace, cudaStream_t s);
+cudaError_t eval_smem_setup(const Geom& g);
+
+}  // namespace dd

@@ -362,6 +362,8 @@ def test_rejects_bad_arguments(oracle_lib):
     assert O.validate(O.Window(20, 20, 10.0, 10.0, [1], [2], [0.1], 0.2, 0.5), -1, 1) != 0  # t < t0
     assert O.validate(O.Window(20, 20, 10.0, 10.0, [1], [2], [0.1], 0.0, 0.0), -1, 1) != 0  # tau = 0
     assert O.validate(O.Window(20, 20, 30.0, 10.0, [1], [2], [0.1], 0.0, 0.5), -1, 1) != 0  # FOE out
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [20], [2], [0.1], 0.0, 0.5), -1, 1) != 0  # x = W
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [3], [-1], [0.1], 0.0, 0.5), -1, 1) != 0  # y < 0
     empty = O.Window(20, 20, 10.0, 10.0, [], [], [], 0.0, 0.5)
     assert O.contrast(empty, 0.3)[:3] == (0, 0, 0)
     r = O.solve(empty, -1.0, 1.0, 1e-4, 0.0, 1)
