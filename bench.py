@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: exact divergence solves per second on one GB300.
+
+A step is one exact solve (Algorithm 1 to its certificate) of the 640x480,
+100,000-event window (D = 0.35 s^-1, tau = 0.3 s, 30% noise; D searched in
+[-1, 1] s^-1, tolerance 1e-4, gamma = 0): ingest, every contrast and bound
+evaluation and the device branch and bound.  Events are resident in device
+memory when the timed region starts; L2 is flushed (a 256 MiB write) before
+every timed step.  Under torchrun each rank solves its own replica (windows
+are independent: replicas, weak scaling).
+
+--impl reference times the CPU oracle on the same window instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("640x480 frame, FOE (320,240), 100,000 events (70,000 signal from 2,000 scene points, "
+            "30,000 noise), D=0.35 1/s, tau=0.3 s; exact BnB over D in [-1,1], tol 1e-4, gamma 0")
+METRIC = "exact divergence solves/sec"
+UNIT = "solves/s"
+
+# Algorithmic ALU operations per unit of work of the IWE kernel (binary32 or
+# int32 lane operations; derivation in the design doc):
+OPS_POINT_WARP = 12      # s, two pixel coordinates, in-frame test, one increment
+OPS_BOUND_EVENT = 26     # two scales, widening, four end cells, full test
+OPS_BOUND_INCREMENT = 10  # major-cell s-range, minor cells, one increment
+SM_COUNT = 152
+LANES_PER_SM = 128
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class Clocks:
+    """nvidia-smi samples of one GPU during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.p, self.lines = gpu, None, []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel_hash):
+    """Per-launch DRAM bytes of the IWE kernel from the committed ncu summary,
+    only if it was taken on the kernel source as it is now."""
+    try:
+        p = json.load(open(os.path.join(ROOT, "profiles", "k_eval_config2.json")))
+    except (OSError, ValueError):
+        return None
+    if p.get("kernel_source_sha256") != kernel_hash:
+        return None
+    return p.get("dram_bytes_per_launch")
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dd_kernels.cu", "dd_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2209_13168_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def oracle_rate(w, budget_s, max_solves):
+    """Oracle solves of window w on one host thread for about budget_s."""
+    import oracle as O
+    O.build()
+    win = O.Window.of(w)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.solve(win, -1.0, 1.0, 1e-4, 0.0, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= max_solves:
+            return n, el
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from synth import window_config2
+    import oracle as O
+    O.build()
+    w = window_config2()
+    win = O.Window.of(w)
+    for _ in range(args.warmup):
+        O.solve(win, -1.0, 1.0, 1e-4, 0.0, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.solve(win, -1.0, 1.0, 1e-4, 0.0, 1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "solver": "CPU oracle, Algorithm 1 (pop 1), one host thread"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "%d full oracle solves of the window, one thread" % args.steps},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = env_int("WORLD_SIZE", 1), env_int("RANK", 0), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2209_13168_gb300 as dd
+    from synth import window_config2
+
+    w = window_config2()
+    stream = torch.cuda.Stream()
+    ctx = dd.Context(w.W, w.H, w.foe_x, w.foe_y, pop_k=args.pop_k)
+    ctx.set_stream(stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        ev = dd.Events.of(w, device="cuda")
+        flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
+    stream.synchronize()
+
+    for _ in range(args.warmup):
+        r = ctx.solve(ev)
+
+    # ---- timed region: device-resident inputs, L2 flushed before each step
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.reset_stats()
+    results = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            results.append(ctx.solve(ev))
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    r = results[-1]
+    assert all(x["K_hat"] == r["K_hat"] and x["D_star"] == r["D_star"] for x in results)
+    value = world * args.steps / total_s
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xs = torch.from_numpy(w.x).pin_memory().numpy()
+        ys = torch.from_numpy(w.y).pin_memory().numpy()
+        ts = torch.from_numpy(w.t).pin_memory().numpy()
+        hev = dd.Events(xs, ys, ts, w.t0, w.tau)
+        ctx.solve(hev)
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            rh = ctx.solve(hev)
+        el = time.perf_counter() - t0
+        sh = ctx.stats()
+        assert rh["K_hat"] == r["K_hat"]
+        if dist:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": sh["h2d_bytes"] // args.steps,
+               "d2h_bytes_per_step": sh["d2h_bytes"] // args.steps}
+
+    # ---- roofline of the dominant kernel (IWE evaluation), separate pass
+    ctx.set_timing(True)
+    ctx.reset_stats()
+    reps = 5
+    for _ in range(reps):
+        rr = ctx.solve(ev)
+    sr = ctx.stats()
+    ctx.set_timing(False)
+    eval_ms_per_solve = sr["eval_ms"] / reps
+    launches_per_solve = sr["timed_launches"] / reps
+    N = w.n
+    pe, be, bi = rr["point_evals"], rr["bound_evals"], rr["bound_increments"]
+    ops = OPS_POINT_WARP * N * pe + OPS_BOUND_EVENT * N * be + OPS_BOUND_INCREMENT * bi
+    achieved = ops / (eval_ms_per_solve / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
+    traffic = profile_traffic(kernel_hash())
+    roofline = {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "derived: %d SMs x %d lanes x %.0f MHz (max SM clock of measured peaks)"
+                               % (SM_COUNT, LANES_PER_SM, sm_max),
+                "ops_per_solve": ops, "eval_ms_per_solve": eval_ms_per_solve,
+                "eval_launches_per_solve": launches_per_solve,
+                "eval_share_of_step": eval_ms_per_solve / (sum(step_ms) / len(step_ms))}
+
+    # ---- secondary: Algorithm 1 one interval per round (pop 1)
+    plain = None
+    if not args.no_plain:
+        c1 = dd.Context(w.W, w.H, w.foe_x, w.foe_y, pop_k=1)
+        c1.set_stream(stream.cuda_stream)
+        c1.solve(ev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            rp = c1.solve(ev)
+        plain = {"value": 3 / (time.perf_counter() - t0), "unit": UNIT, "pop_k": 1,
+                 "nodes_expanded": rp["nodes_expanded"], "rounds": rp["rounds"]}
+        c1.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, el = oracle_rate(w, args.cpu_seconds, 5)
+        cpu = {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d full oracle solves of the same window (Algorithm 1, pop 1), one host thread, %.1f s"
+                         % (n, el)}
+
+    ms = sorted(step_ms)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "pop_k": args.pop_k, "events": N,
+                      "l2": "flushed before each timed step (%d MiB device write)" % args.flush_mb,
+                      "inputs": "device-resident SoA", "parallelism": "replicas" if world > 1 else "single GPU"},
+           "event_warps_per_s": world * r["event_warps"] * args.steps / total_s,
+           "cell_increments_per_s": world * r["cell_increments"] * args.steps / total_s,
+           "p50_ms": ms[len(ms) // 2], "p99_ms": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))],
+           "solve": {"D_star": r["D_star"], "contrast": r["contrast"], "bound_gap": r["bound_gap"],
+                     "nodes_expanded": r["nodes_expanded"], "rounds": r["rounds"],
+                     "point_evals": r["point_evals"], "bound_evals": r["bound_evals"]},
+           "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+           "clocks": clk, "plain_pop1": plain}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pop-k", type=int, default=16)
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
