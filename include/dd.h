@@ -51,7 +51,8 @@ enum {
     DD_ERR_QUEUE_OVERFLOW = -3, /* the BnB queue exceeded its capacity           */
     DD_ERR_TIMEOUT = -4,        /* the round limit was reached before the proof  */
     DD_ERR_CUDA = -5,           /* a CUDA runtime call failed                    */
-    DD_ERR_NO_DEVICE = -6       /* no usable sm_103 device                       */
+    DD_ERR_NO_DEVICE = -6,      /* no usable sm_103 device                       */
+    DD_ERR_CAPACITY = -7        /* input exceeds dd_contrast_noalloc's fixed scratch */
 };
 
 typedef struct dd_ctx dd_ctx;
@@ -177,6 +178,45 @@ int dd_reset_stats(dd_ctx* ctx);
  * context's stream and add its duration to dd_stats.eval_ms (costs a few
  * microseconds per launch; off by default). */
 int dd_set_timing(dd_ctx* ctx, int32_t enable);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free contrast evaluation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * time they evaluate contrasts -- flight or embedded software whose rules
+ * forbid any allocation after start-up (so no allocation can fail in the
+ * guidance loop), or a plugin inside a host process that owns all device
+ * memory through its own capped pool, where a cudaMalloc would bypass its
+ * accounting or fail.
+ *
+ * dd_contrast_noalloc computes exactly what dd_contrast computes (the keys
+ * K[j], Eqs. 11-13) without a context and without allocating: it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its working memory
+ * (sorted events, row tables, per-tile partial sums, keys) is one static
+ * device array of DD_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads
+ * this library holds until the process exits.
+ *
+ *   W, H, foe_x, foe_y  frame and FOE, as dd_create.
+ *   ev                  events in DEVICE memory (ev->device_ptrs must be 1),
+ *                       at most DD_NOALLOC_MAX_EVENTS of them.
+ *   D, nD               hypotheses (host array), as dd_contrast.
+ *   K                   host array of nD keys (unspecified after an error).
+ *   stream              cudaStream_t to run on (NULL: the legacy default
+ *                       stream); the call synchronises it before returning.
+ *
+ * Set-up: the first call on each device (made with that device current)
+ * looks up the device address of the static array and caches it; make that
+ * first call before any stream capture on the device.
+ * Sharing: every call on a device uses the same array and leaves the last
+ * call's contents in it (everything that must start at zero is cleared by the
+ * call itself).  Calls whose GPU work overlaps -- from several host threads
+ * or on several streams at once -- race on the array; serialise them.
+ * Errors: DD_ERR_CAPACITY if ev->n > DD_NOALLOC_MAX_EVENTS; DD_ERR_ARG as
+ * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
+ * DD_ERR_CUDA. */
+#define DD_NOALLOC_MAX_EVENTS (1 << 20)
+#define DD_NOALLOC_SCRATCH_BYTES 10014720
+int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
+                        int32_t nD, dd_i128* K, void* stream);
 
 /* A static description of a status code. */
 const char* dd_strerror(int status);

@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libdd.so")
 
 DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_NO_DEVICE = \
     0, -1, -2, -3, -4, -5, -6
+DD_ERR_CAPACITY = -7
+DD_NOALLOC_MAX_EVENTS = 1 << 20
 
 
 class DDError(RuntimeError):
@@ -92,6 +94,8 @@ SIGNATURES = {
     "dd_get_stats": (ctypes.c_int, [_VP, _P(dd_stats)]),
     "dd_reset_stats": (ctypes.c_int, [_VP]),
     "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "dd_contrast_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                           _P(dd_events), _VP, ctypes.c_int32, _VP, _VP]),
     "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -234,6 +238,18 @@ def dd_solve_trace(h, ev, D_lo, D_hi, tol_D, gamma, trace_cap):
                   for i in range(min(tl.value, trace_cap))]
     d["trace_len"] = tl.value
     return d
+
+
+def dd_contrast_noalloc(W, H, foe_x, foe_y, ev, D, stream_ptr=None):
+    """Keys K[j] of dd_contrast without a context and without allocating
+    device memory (events must be device tensors); see include/dd.h."""
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    n = D.size
+    K = (dd_i128 * max(n, 1))()
+    _check(load().dd_contrast_noalloc(W, H, foe_x, foe_y, ctypes.byref(ev.c), D.ctypes.data, n,
+                                      ctypes.cast(K, _VP), _VP(stream_ptr) if stream_ptr else None),
+           "dd_contrast_noalloc")
+    return [K[i].value() for i in range(n)]
 
 
 class Context:

@@ -318,6 +318,7 @@ const char* dd_strerror(int status) {
         case DD_ERR_TIMEOUT: return "branch-and-bound round limit reached";
         case DD_ERR_CUDA: return "CUDA runtime error";
         case DD_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+        case DD_ERR_CAPACITY: return "input exceeds the fixed scratch of the allocation-free entry point";
         default: return "unknown status";
     }
 }
