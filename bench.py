@@ -29,10 +29,16 @@ METRIC = "exact divergence solves/sec"
 UNIT = "solves/s"
 
 # Algorithmic ALU operations per unit of work of the IWE kernel (binary32 or
-# int32 lane operations; derivation in the design doc):
-OPS_POINT_WARP = 12      # s, two pixel coordinates, in-frame test, one increment
-OPS_BOUND_EVENT = 26     # two scales, widening, four end cells, full test
-OPS_BOUND_INCREMENT = 10  # major-cell s-range, minor cells, one increment
+# int32 lane operations):
+#   point event-warp  12: D*t, 1-., .*g; per axis d*s, +FOE, +1/2, floor; the
+#                         in-frame test; one increment
+#   bound event       26: two scales (6), two widenings (2), four end cells
+#                         (4 x 4), the full test (2)
+#   bound increment   10: the major cell's two s-boundaries (4), the minor
+#                         cells at its two ends (amortised, 5), one increment
+OPS_POINT_WARP = 12
+OPS_BOUND_EVENT = 26
+OPS_BOUND_INCREMENT = 10
 SM_COUNT = 152
 LANES_PER_SM = 128
 

@@ -304,20 +304,21 @@ static float centre(float lo, float hi) { return lo + 0.5f * (hi - lo); }
 
 /* Algorithm 1 over D = -nu, in rounds that dequeue up to K_pop intervals
  * (K_pop = 1 is Algorithm 1 step for step):
- *   line 1   incumbent = centre of the domain, K_hat = K(centre)
- *   line 2   insert the domain with priority Kbar
- *   line 4-5 dequeue the first item; stop if Kbar - K_hat <= gamma_K
- *            (gamma in contrast units, gamma_K = floor(gamma * M^2)); in a
- *            round, dequeuing stops at the first item that passes this test
- *            against the incumbent at the start of the round, and that item
- *            stays queued
- *   line 6-7 evaluate every dequeued centre; in dequeue order, a centre with
- *            K >= K_hat becomes the incumbent
- *   line 8   bisect at the centre, unless the interval is no wider than tol_D
- *            (a leaf: its Kbar is kept in leaf_max and it is not split; the
- *            paper has no width rule, binary32 bounds need one)
- *   line 10  evaluate both child bounds; insert children with Kbar >= K_hat,
- *            K_hat being the incumbent at the end of the round.
+ *   init       incumbent = centre of the domain, K_hat = K(centre); the
+ *              domain enters the queue with priority Kbar
+ *   dequeue    take the first item; stop if Kbar - K_hat <= gamma_K (gamma
+ *              in contrast units, gamma_K = floor(gamma * M^2)); in a round,
+ *              dequeuing stops at the first item that passes this test
+ *              against the incumbent at the start of the round, and that
+ *              item stays queued
+ *   incumbent  evaluate every dequeued centre; in dequeue order, a centre
+ *              with K >= K_hat becomes the incumbent
+ *   bisect     split at the centre, unless the interval is no wider than
+ *              tol_D (a leaf: its Kbar is kept in leaf_max and it is not
+ *              split; the paper has no width rule, binary32 bounds need one)
+ *   insert     evaluate both child bounds; insert children with
+ *              Kbar >= K_hat, K_hat being the incumbent at the end of the
+ *              round.
  * The certificate is gap_K = max(0, max(leaf_max, Kbar of the item that
  * stopped the search) - K_hat). */
 int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
@@ -345,11 +346,11 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
     uint64_t S;
     int64_t N;
 
-    float D_hat = centre(D_lo, D_hi);                         /* line 1 */
+    float D_hat = centre(D_lo, D_hi);                         /* init: incumbent */
     i128 K_hat = eval_point(w, D_hat, img, &S, &N);
     r.point_evals = 1;
     cells += N;
-    node root = {D_lo, D_hi, 0};                              /* line 2 */
+    node root = {D_lo, D_hi, 0};                              /* init: queue */
     int64_t nf, nc;
     root.kb = eval_bound(w, D_lo, D_hi, img, &S, &nf, &nc);
     r.bound_evals = 1;
@@ -360,12 +361,12 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
 
     int have_leaf = 0, have_stop = 0;
     i128 leaf_max = 0, stop_kb = 0;
-    while (q.n > 0) {                                          /* line 3 */
+    while (q.n > 0) {                                          /* while queue */
         const i128 K0 = K_hat;
         int np = 0;
-        while (np < K_pop && q.n > 0) {                        /* line 4 */
+        while (np < K_pop && q.n > 0) {                        /* dequeue */
             int64_t b = q_top(&q);
-            if (q.a[b].kb - K0 <= gamma_K) {                   /* line 5 */
+            if (q.a[b].kb - K0 <= gamma_K) {                   /* gap test */
                 if (np == 0) { have_stop = 1; stop_kb = q.a[b].kb; }
                 break;
             }
@@ -373,17 +374,17 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
         }
         if (np == 0) break;
         r.rounds++;
-        for (int j = 0; j < np; j++) {                         /* line 6 */
+        for (int j = 0; j < np; j++) {                         /* centres */
             dc[j] = centre(pop[j].lo, pop[j].hi);
             kc[j] = eval_point(w, dc[j], img, &S, &N);
             cells += N;
             r.point_evals++;
             r.nodes_expanded++;
         }
-        for (int j = 0; j < np; j++)                           /* line 7 */
+        for (int j = 0; j < np; j++)                           /* incumbent */
             if (kc[j] >= K_hat) { K_hat = kc[j]; D_hat = dc[j]; }
         int nk = 0;
-        for (int j = 0; j < np; j++) {                         /* line 8-9 */
+        for (int j = 0; j < np; j++) {                         /* bisect */  
             int leaf = !((pop[j].hi - pop[j].lo) > tol_D) || !(dc[j] > pop[j].lo) || !(dc[j] < pop[j].hi);
             if (trace && tl < trace_cap) {
                 or_node_rec* t = &trace[tl];
@@ -407,7 +408,7 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
             kids[nk++] = a;
             kids[nk++] = b;
         }
-        for (int j = 0; j < nk; j++)                           /* line 10 */
+        for (int j = 0; j < nk; j++)                           /* insert */ 
             if (kids[j].kb >= K_hat)
                 if ((rc = q_push(&q, kids[j]))) goto done;
         if (q.n > r.max_queue) r.max_queue = q.n;

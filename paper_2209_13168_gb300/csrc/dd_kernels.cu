@@ -427,7 +427,7 @@ __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float
     st->K_hat = 0;
     st->leaf_max = 0;
     st->stop_kb = 0;
-    st->D_hat = centre(D_lo, D_hi);               // line 1: incumbent = centre of the domain
+    st->D_hat = centre(D_lo, D_hi);               // incumbent = centre of the domain
     st->phase = PH_INIT;
     st->status = DD_OK;
     st->n_pop = 0;
@@ -440,7 +440,7 @@ __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float
     a.D_lo = a.D_hi = st->D_hat;
     a.kind = TASK_POINT;
     a.pad = 0;
-    b.D_lo = D_lo;                                // line 2: bound of the domain
+    b.D_lo = D_lo;                                // bound of the domain (queued first)
     b.D_hi = D_hi;
     b.kind = TASK_BOUND;
     b.pad = 0;
@@ -469,7 +469,8 @@ __device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
 }
 
 // One warp per search.  Consumes the keys of the round just evaluated
-// (Algorithm 1 lines 6-10), then dequeues the next batch (lines 3-5) and
+// (Algorithm 1: incumbent update, bisection, insertion), then dequeues the
+// next batch (dequeue and gap test) and
 // writes its tasks, or finishes.
 __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* queue, Task* tasks,
                                                 const Partial* part, const int32_t* err, TraceRec* trace) {
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
         } else {
             const int np = st->n_pop;
             i128 K_hat = st->K_hat;
-            for (int j = 0; j < np; j++) {            // lines 6-7 in dequeue order
+            for (int j = 0; j < np; j++) {            // incumbent update, dequeue order
                 const Popped& p = st->pop[j];
                 const i128 kc = key[p.t_point];
                 st->nodes_expanded++;
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
             }
             st->K_hat = K_hat;
             int qn = st->q_n;
-            for (int j = 0; j < np && !stop; j++) {   // lines 8-10
+            for (int j = 0; j < np && !stop; j++) {   // leaves, child bounds
                 const Popped& p = st->pop[j];
                 if (st->trace_len < st->trace_cap && trace) {
                     TraceRec r;
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
     stop = __shfl_sync(0xffffffffu, stop, 0);
     __syncwarp();
 
-    // lines 3-5: dequeue up to K_pop intervals
+    // dequeue up to K_pop intervals
     const i128 K0 = st->K_hat;
     const i128 gK = st->gamma_K;
     int np = 0;
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
         int brk = 0;
         if (lane == 0) {
             const Node nd = queue[bi];
-            if (nd.kb - K0 <= gK) {                   // line 5
+            if (nd.kb - K0 <= gK) {                   // gap test
                 if (np == 0) { st->have_stop = 1; st->stop_kb = nd.kb; }
                 brk = 1;
             } else {
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
         } else {
             st->rounds++;
             int nt = np;
-            for (int j = 0; j < np; j++) {            // lines 6 and 8: centre and bisection
+            for (int j = 0; j < np; j++) {            // centre and bisection
                 Popped& p = st->pop[j];
                 p.c = centre(p.lo, p.hi);
                 const float w = __fsub_rn(p.hi, p.lo);

@@ -304,7 +304,7 @@ def test_pop_k_keeps_the_optimum(oracle_lib):
 
 
 def test_gamma_stops_early(oracle_lib):
-    # Line 5 of Algorithm 1 with gamma > 0: the search stops once the best
+    # The stopping test of Algorithm 1 with gamma > 0: the search stops once the best
     # bound is within gamma (contrast units) of the incumbent.
     win = O.Window.of(window_config1())
     r0 = O.solve(win, -1.0, 1.0, 1e-4, 0.0, 1)
