@@ -67,7 +67,10 @@ typedef struct {
     int32_t band_rows;      /* rows of the shared-memory IWE tile (default: from W)      */
     int32_t threads;        /* threads per block of the IWE kernels (default 512)        */
     int32_t max_rounds;     /* BnB round limit, DD_ERR_TIMEOUT beyond (default 1<<20)    */
-    int32_t reserved[3];
+    int32_t host_loop;      /* 0: each solve's rounds run as one CUDA graph with a       */
+                            /*    conditional loop (no host round trips); 1: the host    */
+                            /*    launches the rounds in batches and polls for the end   */
+    int32_t reserved[2];
 } dd_config;
 
 /* One window of events in structure-of-arrays form. */

@@ -25,6 +25,8 @@ struct dd_ctx {
     float* in_t = nullptr;
     int64_t in_cap = 0;
     int32_t *row_count = nullptr, *row_off = nullptr, *cursor = nullptr, *err = nullptr;
+    int32_t* work = nullptr;      // IWE item counter of the persistent evaluation grid
+    int eval_blocks = 0;          // resident blocks of that grid
 
     dd::Task* tasks = nullptr;
     dd::Partial* part = nullptr;
@@ -34,7 +36,7 @@ struct dd_ctx {
     size_t iwe_cap = 0;
 
     dd::SolveState* st = nullptr;
-    dd::Node* queue = nullptr;
+    dd::Node* queue = nullptr;   // two buffers of queue_capacity nodes
     dd::TraceRec* trace = nullptr;
     int64_t trace_cap = 0;
 
@@ -43,6 +45,12 @@ struct dd_ctx {
     int timing = 0;
     std::vector<cudaEvent_t> t_ev;
     size_t t_used = 0;
+
+    // the rounds of a solve as one CUDA graph (a conditional while loop)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_ev = nullptr;
+    const void* g_trace = nullptr;
 
     // pinned host staging
     dd::SolveState* h_st = nullptr;
@@ -177,7 +185,7 @@ cudaError_t eval(dd_ctx* c, const int32_t* n_tasks_dev, int32_t n_tasks_max, flo
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = dd::launch_eval(c->g, c->ev, c->row_off, c->tasks, n_tasks_dev, n_tasks_max, tau, c->part, iwe,
-                                    st, c->threads, c->stream);
+                                    st, c->threads, c->stream, c->work, c->eval_blocks);
     if (e != cudaSuccess) return e;
     c->stats.kernel_launches++;
     c->stats.eval_launches++;
@@ -210,6 +218,7 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
             }
             iw = c->iwe;
         }
+        DD_TRY(cudaMemsetAsync(c->work, 0, sizeof(int32_t), c->stream));
         DD_TRY(eval(c, nullptr, m, ev->tau, iw, nullptr));
         DD_TRY(dd::launch_keys(c->g, c->tasks, m, c->part, c->keys, c->S, c->C, c->F, c->stream));
         c->stats.kernel_launches++;
@@ -233,6 +242,49 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
     return DD_OK;
 }
 
+void drop_graph(dd_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+// Build the solve graph: a while node whose body is one round (IWE
+// evaluation, then the control kernel, which clears the loop condition when
+// the search is over).  Kernel arguments are baked in, so the graph is
+// rebuilt when a buffer it points to is reallocated.
+int build_graph(dd_ctx* c, dd::TraceRec* trace) {
+    drop_graph(c);
+    DD_TRY(cudaGraphCreate(&c->graph, 0));
+    cudaGraphConditionalHandle h;
+    DD_TRY(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    DD_TRY(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    DD_TRY(cudaStreamBeginCaptureToGraph(c->own, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = dd::launch_eval(c->g, c->ev, c->row_off, c->tasks, &c->st->n_tasks, c->max_tasks, 0.0f,
+                                     c->part, nullptr, c->st, c->threads, c->own, c->work, c->eval_blocks);
+    cudaError_t e2 = dd::launch_control(c->g, c->st, c->queue, c->queue + c->cfg.queue_capacity, c->tasks,
+                                        c->part, c->err, trace, h, 1, c->work, c->own);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(c->own, &captured);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        drop_graph(c);
+        return DD_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&c->gexec, c->graph, 0) != cudaSuccess) {
+        drop_graph(c);
+        return DD_ERR_CUDA;
+    }
+    c->g_ev = c->ev;
+    c->g_trace = trace;
+    return DD_OK;
+}
+
 int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma, dd_result* out,
                dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
     if (!c || !out) return DD_ERR_ARG;
@@ -253,26 +305,42 @@ int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol
     const int64_t M = (int64_t)c->g.W * c->g.H;
     const i128 gamma_K = (i128)std::floor(gamma * (double)M * (double)M);
     DD_TRY(dd::launch_init(c->st, c->tasks, M, D_lo, D_hi, tol_D, ev->tau, gamma_K, c->cfg.pop_k,
-                           c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap, c->stream));
+                           c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap, c->work, c->stream));
     c->stats.kernel_launches++;
-    int batch = 2;
-    for (;;) {
-        for (int b = 0; b < batch; b++) {
-            DD_TRY(eval(c, &c->st->n_tasks, c->max_tasks, ev->tau, nullptr, c->st));
-            DD_TRY(dd::launch_control(c->g, c->st, c->queue, c->tasks, c->part, c->err,
-                                      trace_cap > 0 ? c->trace : nullptr, c->stream));
-            c->stats.kernel_launches++;
+    dd::TraceRec* tr_dev = trace_cap > 0 ? c->trace : nullptr;
+    const bool graph = !c->cfg.host_loop && !c->timing;
+    if (graph) {
+        // One graph launch runs every round on the device.
+        if (!c->gexec || c->g_ev != (const void*)c->ev || c->g_trace != (const void*)tr_dev) {
+            rc = build_graph(c, tr_dev);
+            if (rc) return rc;
         }
-        DD_TRY(copy(c, c->h_flag, &c->st->phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        DD_TRY(sync(c));
-        if (*c->h_flag == dd::PH_DONE) break;
-        if (batch < 64) batch *= 2;
+        DD_TRY(cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+        // Host-driven rounds: launch batches, poll for the end.
+        int batch = 2;
+        for (;;) {
+            for (int b = 0; b < batch; b++) {
+                DD_TRY(eval(c, &c->st->n_tasks, c->max_tasks, ev->tau, nullptr, c->st));
+                DD_TRY(dd::launch_control(c->g, c->st, c->queue, c->queue + c->cfg.queue_capacity, c->tasks,
+                                          c->part, c->err, tr_dev, 0, 0, c->work, c->stream));
+                c->stats.kernel_launches++;
+            }
+            DD_TRY(copy(c, c->h_flag, &c->st->phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            DD_TRY(sync(c));
+            if (*c->h_flag == dd::PH_DONE) break;
+            if (batch < 64) batch *= 2;
+        }
     }
     DD_TRY(copy(c, c->h_st, c->st, sizeof(dd::SolveState), cudaMemcpyDeviceToHost));
     std::vector<dd::TraceRec> tr((size_t)trace_cap);
     if (trace_cap > 0) DD_TRY(copy(c, tr.data(), c->trace, sizeof(dd::TraceRec) * trace_cap, cudaMemcpyDeviceToHost));
     DD_TRY(sync(c));
     const dd::SolveState& s = *c->h_st;
+    if (graph) {                                  // the loop ran rounds + 1 times
+        c->stats.kernel_launches += 2 * (s.rounds + 1);
+        c->stats.eval_launches += s.rounds + 1;
+    }
     if (s.status != DD_OK) return s.status;
     // Sec. 4.1 retrieval and reporting (double precision, from the exact keys).
     dd_result r;
@@ -333,6 +401,7 @@ void dd_destroy(dd_ctx* c) {
     cudaFree(c->row_off);
     cudaFree(c->cursor);
     cudaFree(c->err);
+    cudaFree(c->work);
     cudaFree(c->tasks);
     cudaFree(c->part);
     cudaFree(c->keys);
@@ -347,6 +416,7 @@ void dd_destroy(dd_ctx* c) {
     cudaFreeHost(c->h_tasks);
     cudaFreeHost(c->h_flag);
     for (cudaEvent_t e : c->t_ev) cudaEventDestroy(e);
+    drop_graph(c);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }
@@ -380,8 +450,9 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     c->g.H = H;
     c->g.fx = foe_x;
     c->g.fy = foe_y;
-    // Default band: about 96 KB of uint32 counts, two blocks per SM.
-    int rows = k.band_rows ? k.band_rows : (int)(96 * 1024 / (4 * W));
+    // Default band: about 40 KB of uint32 counts (16 rows at 640 px), so
+    // that heavy tasks spread over many blocks and several blocks share an SM.
+    int rows = k.band_rows ? k.band_rows : (int)(40 * 1024 / (4 * W));
     if (rows < 1) rows = 1;
     if (rows > H) rows = H;
     if ((size_t)rows * W * 4 > 200 * 1024) rows = (int)(200 * 1024 / (4 * W));
@@ -392,6 +463,8 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     c->g.band_rows = rows;
     c->g.n_tiles = (H + rows - 1) / rows;
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
+    c->cfg.threads = c->threads;
+    c->cfg.band_rows = rows;
 
     int rc = DD_OK;
     auto A = [&](void** p, size_t bytes) {
@@ -401,6 +474,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     A((void**)&c->row_off, sizeof(int32_t) * (H + 1));
     A((void**)&c->cursor, sizeof(int32_t) * H);
     A((void**)&c->err, sizeof(int32_t));
+    A((void**)&c->work, sizeof(int32_t));
     A((void**)&c->tasks, sizeof(dd::Task) * c->max_tasks);
     A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles);
     A((void**)&c->keys, sizeof(i128) * c->max_tasks);
@@ -408,13 +482,14 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     A((void**)&c->C, sizeof(unsigned long long) * c->max_tasks);
     A((void**)&c->F, sizeof(unsigned long long) * c->max_tasks);
     A((void**)&c->st, sizeof(dd::SolveState));
-    A((void**)&c->queue, sizeof(dd::Node) * (size_t)k.queue_capacity);
+    A((void**)&c->queue, sizeof(dd::Node) * 2 * (size_t)k.queue_capacity);
     if (rc == DD_OK && cudaMallocHost((void**)&c->h_st, sizeof(dd::SolveState)) != cudaSuccess) rc = DD_ERR_OOM;
     if (rc == DD_OK && cudaMallocHost((void**)&c->h_tasks, sizeof(dd::Task) * c->max_tasks) != cudaSuccess)
         rc = DD_ERR_OOM;
     if (rc == DD_OK && cudaMallocHost((void**)&c->h_flag, sizeof(int32_t)) != cudaSuccess) rc = DD_ERR_OOM;
     if (rc == DD_OK && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && dd::eval_smem_setup(c->g) != cudaSuccess) rc = DD_ERR_CUDA;
+    if (rc == DD_OK && (c->eval_blocks = dd::eval_resident_blocks(c->g, c->threads)) <= 0) rc = DD_ERR_CUDA;
     if (rc != DD_OK) {
         dd_destroy(c);
         return rc;

@@ -64,7 +64,7 @@ struct __align__(16) SolveState {
     // search state
     i128 K_hat, leaf_max, stop_kb;
     float D_hat;
-    int32_t phase, status, n_tasks, n_pop, q_n, have_leaf, have_stop;
+    int32_t phase, status, n_tasks, n_pop, q_n, q_start, q_cur, have_leaf, have_stop;
     int64_t nodes_expanded, point_evals, bound_evals, cells, bcells, rounds, max_queue, trace_len;
     Popped pop[MAX_POP];
 };
@@ -80,17 +80,22 @@ struct Geom {
 cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
                           float t0, float tau, Ev* out, int32_t* row_count, int32_t* row_off,
                           int32_t* cursor, int32_t* err, cudaStream_t s);
+// work: an item counter that is zero at launch (the kernel then runs a
+// persistent grid of grid_blocks blocks), or nullptr (one block per item).
 cudaError_t launch_eval(const Geom& g, const Ev* ev, const int32_t* row_off, const Task* tasks,
                         const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
-                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s);
+                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s,
+                        int32_t* work = nullptr, int grid_blocks = 0);
+int eval_resident_blocks(const Geom& g, int threads);
 cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part,
                         i128* key, unsigned long long* S, unsigned long long* cells,
                         unsigned long long* full, cudaStream_t s);
 cudaError_t launch_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol,
                         float tau, i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds,
-                        int32_t trace_cap, cudaStream_t s);
-cudaError_t launch_control(const Geom& g, SolveState* st, Node* queue, Task* tasks, const Partial* part,
-                           const int32_t* err, TraceRec* trace, cudaStream_t s);
+                        int32_t trace_cap, int32_t* work, cudaStream_t s);
+cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,
+                           const int32_t* err, TraceRec* trace, cudaGraphConditionalHandle loop, int32_t use_loop,
+                           int32_t* work, cudaStream_t s);
 cudaError_t eval_smem_setup(const Geom& g);
 
 }  // namespace dd

@@ -252,24 +252,14 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-// One block = one (task, tile).  Blocks past the live task count, or of a
-// finished search, return at once.
-__global__ void __launch_bounds__(1024) k_eval(Geom g, const Ev* __restrict__ ev,
-                                               const int32_t* __restrict__ row_off,
-                                               const Task* __restrict__ tasks, const int32_t* n_tasks_dev,
-                                               int32_t n_tasks_host, float tau, Partial* __restrict__ part,
-                                               uint32_t* __restrict__ iwe_out, const SolveState* st) {
-    extern __shared__ uint32_t tile[];
-    __shared__ unsigned long long red[3][32];
-    __shared__ int erange[2];
-    if (st && st->phase == PH_DONE) return;
-    const int n_tasks = n_tasks_dev ? *n_tasks_dev : n_tasks_host;
-    const int task = blockIdx.x / g.n_tiles;
-    if (task >= n_tasks) return;
-    const int ti = blockIdx.x - task * g.n_tiles;
+// One (task, tile) item: zero the tile, scatter the events that can reach its
+// rows, reduce.  Writes part[task * n_tiles + tile].
+__device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ ev,
+                                          const int32_t* __restrict__ row_off, const Task& tk, int task, int ti,
+                                          float tau, Partial* __restrict__ part, uint32_t* __restrict__ iwe_out,
+                                          uint32_t* tile, unsigned long long (*red)[32], int* erange) {
     const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
     const int W = g.W, cnt = (y1 - y0) * W;
-    const Task tk = tasks[task];
 
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) tile[i] = 0u;
     if (threadIdx.x == 0) {
@@ -339,9 +329,54 @@ __global__ void __launch_bounds__(1024) k_eval(Geom g, const Ev* __restrict__ ev
             p.S = S;
             p.cells = C;
             p.full = full;
-            part[blockIdx.x] = p;
+            part[task * g.n_tiles + ti] = p;
         }
     }
+}
+
+// IWE evaluation of a task list.  With `work` (an item counter that is zero
+// at launch), a grid of resident blocks takes (task, tile) items in turn,
+// the tasks queued last (a round's bound tasks) first.  Without it, block b
+// evaluates item b.  A finished search launches nothing.
+__global__ void __launch_bounds__(1024) k_eval(Geom g, const Ev* __restrict__ ev,
+                                               const int32_t* __restrict__ row_off,
+                                               const Task* __restrict__ tasks, const int32_t* n_tasks_dev,
+                                               int32_t n_tasks_host, float tau, Partial* __restrict__ part,
+                                               uint32_t* __restrict__ iwe_out, const SolveState* st,
+                                               int32_t* work) {
+    extern __shared__ uint32_t tile[];
+    __shared__ unsigned long long red[3][32];
+    __shared__ int erange[2];
+    __shared__ int s_item;
+    if (st && st->phase == PH_DONE) return;
+    const int n_tasks = n_tasks_dev ? *n_tasks_dev : n_tasks_host;
+    if (st) tau = st->tau;                       // a solve keeps its tau in the state
+    const int n_items = n_tasks * g.n_tiles;
+    if (!work) {
+        const int task = blockIdx.x / g.n_tiles;
+        if (task >= n_tasks) return;
+        eval_item(g, ev, row_off, tasks[task], task, blockIdx.x - task * g.n_tiles, tau, part, iwe_out, tile, red,
+                  erange);
+        return;
+    }
+    for (;;) {
+        __syncthreads();                          // the previous item's readers are done
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int task = n_tasks - 1 - item / g.n_tiles;
+        eval_item(g, ev, row_off, tasks[task], task, item % g.n_tiles, tau, part, iwe_out, tile, red, erange);
+    }
+}
+
+int eval_resident_blocks(const Geom& g, int threads) {
+    int per_sm = 0, dev = 0, sms = 0;
+    size_t smem = (size_t)g.band_rows * g.W * sizeof(uint32_t);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval, threads, smem) != cudaSuccess) return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return per_sm * sms;
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by all
@@ -357,11 +392,14 @@ cudaError_t eval_smem_setup(const Geom& g) {
 
 cudaError_t launch_eval(const Geom& g, const Ev* ev, const int32_t* row_off, const Task* tasks,
                         const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
-                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s) {
+                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s, int32_t* work,
+                        int grid_blocks) {
     if (n_tasks_max <= 0) return cudaSuccess;
     size_t smem = (size_t)g.band_rows * g.W * sizeof(uint32_t);
-    k_eval<<<n_tasks_max * g.n_tiles, threads, smem, s>>>(g, ev, row_off, tasks, n_tasks_dev, n_tasks_max, tau,
-                                                          part, iwe_out, st);
+    int items = n_tasks_max * g.n_tiles;
+    int grid = work && grid_blocks > 0 && grid_blocks < items ? grid_blocks : items;
+    k_eval<<<grid, threads, smem, s>>>(g, ev, row_off, tasks, n_tasks_dev, n_tasks_max, tau, part, iwe_out, st,
+                                       work);
     return cudaGetLastError();
 }
 
@@ -412,8 +450,10 @@ __device__ __forceinline__ float centre(float lo, float hi) {
 }
 
 __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
-                       i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap) {
+                       i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
+                       int32_t* work) {
     if (threadIdx.x != 0) return;
+    *work = 0;
     st->gamma_K = gamma_K;
     st->M = M;
     st->max_rounds = max_rounds;
@@ -432,6 +472,8 @@ __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float
     st->status = DD_OK;
     st->n_pop = 0;
     st->q_n = 0;
+    st->q_start = 0;
+    st->q_cur = 0;
     st->have_leaf = 0;
     st->have_stop = 0;
     st->nodes_expanded = st->point_evals = st->bound_evals = st->cells = st->bcells = 0;
@@ -451,37 +493,55 @@ __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float
 
 cudaError_t launch_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
                         i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
-                        cudaStream_t s) {
-    k_init<<<1, 32, 0, s>>>(st, tasks, M, D_lo, D_hi, tol, tau, gamma_K, K_pop, qcap, max_rounds, trace_cap);
+                        int32_t* work, cudaStream_t s) {
+    k_init<<<1, 32, 0, s>>>(st, tasks, M, D_lo, D_hi, tol, tau, gamma_K, K_pop, qcap, max_rounds, trace_cap, work);
     return cudaGetLastError();
 }
 
 // Priority order of the queue: larger Kbar first, ties to the smaller D_lo.
-__device__ __forceinline__ bool better(i128 ka, float la, i128 kb, float lb) {
-    return ka > kb || (ka == kb && la < lb);
+// Distinct queued intervals have distinct D_lo, so the order is total.
+__device__ __forceinline__ bool better(const Node& a, const Node& b) {
+    return a.kb > b.kb || (a.kb == b.kb && a.lo < b.lo);
 }
 
-__device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
-    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-    lo = __shfl_sync(0xffffffffu, lo, src);
-    hi = __shfl_sync(0xffffffffu, hi, src);
-    return (i128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+// Number of entries of the sorted array q[0..n) that come before e.
+__device__ __forceinline__ int rank_in(const Node* q, int n, const Node& e) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (better(q[mid], e)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
-// One warp per search.  Consumes the keys of the round just evaluated
-// (Algorithm 1: incumbent update, bisection, insertion), then dequeues the
-// next batch (dequeue and gap test) and
-// writes its tasks, or finishes.
-__global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* queue, Task* tasks,
-                                                const Partial* part, const int32_t* err, TraceRec* trace) {
+constexpr int CTL_THREADS = 256;
+
+// One block per search.  Consumes the keys of the round just evaluated
+// (Algorithm 1: incumbent update, leaves, child bounds and their insertion),
+// then dequeues the next batch (dequeue and gap test) and writes its tasks,
+// or finishes.  The queue is kept sorted in priority order in one of two
+// buffers: insertion is a parallel merge into the other buffer, a dequeue
+// takes a prefix.
+__global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st, Node* qa, Node* qb, Task* tasks,
+                                                        const Partial* part, const int32_t* err, TraceRec* trace,
+                                                        cudaGraphConditionalHandle loop, int32_t use_loop,
+                                                        int32_t* work) {
     __shared__ i128 key[3 * MAX_POP];
     __shared__ unsigned long long cells[3 * MAX_POP];
-    const int lane = threadIdx.x;
-    if (st->phase == PH_DONE) return;
+    __shared__ Node kids[2 * MAX_POP + 1];
+    __shared__ Node sorted_kids[2 * MAX_POP + 1];
+    __shared__ int s_nk, s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (st->phase == PH_DONE) {
+        if (use_loop && tid == 0) cudaGraphSetConditional(loop, 0);
+        return;
+    }
+    if (tid == 0) *work = 0;                      // the next evaluation starts at item 0
     const int64_t M = st->M;
     const int n_tasks = st->n_tasks;
 
-    for (int t = 0; t < n_tasks; t++) {
+    for (int t = wid; t < n_tasks; t += nw) {
         unsigned long long S = 0, C = 0, F = 0;
         for (int i = lane; i < g.n_tiles; i += 32) {
             const Partial p = part[t * g.n_tiles + i];
@@ -497,10 +557,10 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
             cells[t] = C;
         }
     }
-    __syncwarp();
+    __syncthreads();
 
-    int stop = 0;
-    if (lane == 0) {
+    if (tid == 0) {
+        int stop = 0, nk = 0;
         if (*err) {
             st->status = DD_ERR_ARG;
             stop = 1;
@@ -515,14 +575,12 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
             root.hi = st->D_hi;
             root.pad0 = root.pad1 = 0;
             root.kb = key[1];
-            queue[0] = root;
-            st->q_n = 1;
-            st->max_queue = 1;
+            kids[nk++] = root;                    // the domain is queued unconditionally
             st->phase = PH_RUN;
         } else {
             const int np = st->n_pop;
             i128 K_hat = st->K_hat;
-            for (int j = 0; j < np; j++) {            // incumbent update, dequeue order
+            for (int j = 0; j < np; j++) {        // incumbent update, dequeue order
                 const Popped& p = st->pop[j];
                 const i128 kc = key[p.t_point];
                 st->nodes_expanded++;
@@ -534,8 +592,7 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
                 }
             }
             st->K_hat = K_hat;
-            int qn = st->q_n;
-            for (int j = 0; j < np && !stop; j++) {   // leaves, child bounds
+            for (int j = 0; j < np; j++) {        // leaves and child bounds
                 const Popped& p = st->pop[j];
                 if (st->trace_len < st->trace_cap && trace) {
                     TraceRec r;
@@ -556,88 +613,94 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
                 st->bound_evals += 2;
                 st->cells += (int64_t)(cells[p.t_left] + cells[p.t_right]);
                 st->bcells += (int64_t)(cells[p.t_left] + cells[p.t_right]);
-            }
-            for (int j = 0; j < np && !stop; j++) {
-                const Popped& p = st->pop[j];
-                if (p.leaf) continue;
                 for (int side = 0; side < 2; side++) {
                     const i128 kb = key[side ? p.t_right : p.t_left];
-                    if (kb >= K_hat) {
-                        if (qn >= st->qcap) {
-                            st->status = DD_ERR_QUEUE_OVERFLOW;
-                            stop = 1;
-                            break;
-                        }
+                    if (kb >= K_hat) {            // insertion test, end-of-round incumbent
                         Node nd;
                         nd.lo = side ? p.c : p.lo;
                         nd.hi = side ? p.hi : p.c;
                         nd.pad0 = nd.pad1 = 0;
                         nd.kb = kb;
-                        queue[qn++] = nd;
+                        kids[nk++] = nd;
                     }
                 }
             }
-            st->q_n = qn;
-            if (qn > st->max_queue) st->max_queue = qn;
         }
+        if (!stop && st->q_n + nk > st->qcap) {
+            st->status = DD_ERR_QUEUE_OVERFLOW;
+            stop = 1;
+        }
+        s_nk = nk;
+        s_stop = stop;
     }
-    stop = __shfl_sync(0xffffffffu, stop, 0);
-    __syncwarp();
+    __syncthreads();
+    const int nk = s_nk;
+    int stop = s_stop;
 
-    // dequeue up to K_pop intervals
-    const i128 K0 = st->K_hat;
-    const i128 gK = st->gamma_K;
-    int np = 0;
-    while (!stop && np < st->K_pop) {
-        const int qn = st->q_n;
-        if (qn == 0) break;
-        int bi = -1;
-        i128 bk = 0;
-        float bl = 0.0f;
-        for (int i = lane; i < qn; i += 32) {
-            const Node nd = queue[i];
-            if (bi < 0 || better(nd.kb, nd.lo, bk, bl)) { bi = i; bk = nd.kb; bl = nd.lo; }
+    if (!stop) {
+        // sort the new children, then merge them with the queued intervals
+        for (int i = tid; i < nk; i += blockDim.x) {
+            int r = 0;
+            for (int j = 0; j < nk; j++) r += better(kids[j], kids[i]);
+            sorted_kids[r] = kids[i];
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            const i128 ok = shfl_i128(bk, lane + o < 32 ? lane + o : lane);
-            const float ol = __shfl_down_sync(0xffffffffu, bl, o);
-            if (lane + o < 32 && oi >= 0 && (bi < 0 || better(ok, ol, bk, bl))) { bi = oi; bk = ok; bl = ol; }
+        __syncthreads();
+        const Node* src = (st->q_cur ? qb : qa) + st->q_start;
+        Node* dst = st->q_cur ? qa : qb;
+        const int a = st->q_n;
+        for (int i = tid; i < a; i += blockDim.x) {
+            const Node e = src[i];
+            dst[i + rank_in(sorted_kids, nk, e)] = e;
         }
-        int brk = 0;
-        if (lane == 0) {
-            const Node nd = queue[bi];
-            if (nd.kb - K0 <= gK) {                   // gap test
-                if (np == 0) { st->have_stop = 1; st->stop_kb = nd.kb; }
-                brk = 1;
-            } else {
+        for (int j = tid; j < nk; j += blockDim.x) {
+            const Node e = sorted_kids[j];
+            dst[j + rank_in(src, a, e)] = e;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            st->q_cur ^= 1;
+            st->q_start = 0;
+            st->q_n = a + nk;
+            if (st->q_n > st->max_queue) st->max_queue = st->q_n;
+        }
+        __syncthreads();
+    }
+
+    if (tid == 0) {
+        const Node* q = st->q_cur ? qb : qa;
+        int np = 0;
+        if (!stop) {                              // dequeue up to K_pop intervals
+            const i128 K0 = st->K_hat, gK = st->gamma_K;
+            while (np < st->K_pop && np < st->q_n) {
+                const Node nd = q[np];
+                if (nd.kb - K0 <= gK) {           // gap test
+                    if (np == 0) {
+                        st->have_stop = 1;
+                        st->stop_kb = nd.kb;
+                    }
+                    break;
+                }
                 Popped& p = st->pop[np];
                 p.lo = nd.lo;
                 p.hi = nd.hi;
                 p.kb = nd.kb;
-                queue[bi] = queue[qn - 1];
-                st->q_n = qn - 1;
+                np++;
             }
+            st->q_start = np;
+            st->q_n -= np;
         }
-        brk = __shfl_sync(0xffffffffu, brk, 0);
-        __syncwarp();
-        if (brk) break;
-        np++;
-    }
-
-    if (lane == 0) {
         if (stop || np == 0) {
             i128 top = st->K_hat;
             if (st->have_leaf && st->leaf_max > top) top = st->leaf_max;
             if (st->have_stop && st->stop_kb > top) top = st->stop_kb;
-            st->stop_kb = top - st->K_hat;            // the certificate gap_K
+            st->stop_kb = top - st->K_hat;        // the certificate gap_K
             st->n_pop = 0;
             st->n_tasks = 0;
             st->phase = PH_DONE;
         } else {
             st->rounds++;
             int nt = np;
-            for (int j = 0; j < np; j++) {            // centre and bisection
+            for (int j = 0; j < np; j++) {        // centre and bisection
                 Popped& p = st->pop[j];
                 p.c = centre(p.lo, p.hi);
                 const float w = __fsub_rn(p.hi, p.lo);
@@ -676,12 +739,14 @@ __global__ void __launch_bounds__(32) k_control(Geom g, SolveState* st, Node* qu
                 st->phase = PH_DONE;
             }
         }
+        if (use_loop) cudaGraphSetConditional(loop, st->phase == PH_DONE ? 0u : 1u);
     }
 }
 
-cudaError_t launch_control(const Geom& g, SolveState* st, Node* queue, Task* tasks, const Partial* part,
-                           const int32_t* err, TraceRec* trace, cudaStream_t s) {
-    k_control<<<1, 32, 0, s>>>(g, st, queue, tasks, part, err, trace);
+cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,
+                           const int32_t* err, TraceRec* trace, cudaGraphConditionalHandle loop, int32_t use_loop,
+                           int32_t* work, cudaStream_t s) {
+    k_control<<<1, CTL_THREADS, 0, s>>>(g, st, qa, qb, tasks, part, err, trace, loop, use_loop, work);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ def ctx_for(w, **kw):
 
 
 def check_contrast(w, Ds, want_iwe, **kw):
+    kw.pop("host_loop", None)
     ctx = ctx_for(w, **kw)
     win = O.Window.of(w)
     for dev in (None, "cuda"):
@@ -50,6 +51,7 @@ def check_contrast(w, Ds, want_iwe, **kw):
 
 
 def check_bound(w, lo, hi, want_iwe, **kw):
+    kw.pop("host_loop", None)
     ctx = ctx_for(w, **kw)
     win = O.Window.of(w)
     ev = dd.Events.of(w, device="cuda")
@@ -121,8 +123,9 @@ def test_bound_keys_config2(c2):
 # ------------------------------------------------------------------- solve
 
 @pytest.mark.parametrize("pop_k", [1, 4, 16])
-def test_solve_config1(c1, pop_k):
-    check_solve(c1, pop_k)
+@pytest.mark.parametrize("host_loop", [0, 1])
+def test_solve_config1(c1, pop_k, host_loop):
+    check_solve(c1, pop_k, host_loop=host_loop)
 
 
 @pytest.mark.parametrize("pop_k", [1, 16])
@@ -136,12 +139,24 @@ def test_solve_with_gamma_and_narrow_range(c1):
     check_solve(c1, 2, D_lo=0.15, D_hi=0.25, tol=1e-5)
 
 
-def test_solve_repeat_is_identical(c1):
+def test_solve_repeat_is_identical(c1, c2):
+    # The same context across windows of different sizes (buffers regrow and
+    # the solve graph is rebuilt) and with and without a trace.
     ctx = ctx_for(c1, pop_k=4)
-    ev = dd.Events.of(c1, device="cuda")
-    a = ctx.solve(ev)
-    b = ctx.solve(ev)
-    assert a == b
+    ev1 = dd.Events.of(c1, device="cuda")
+    a = ctx.solve(ev1)
+    b = ctx.solve(ev1, trace_cap=10)
+    c = ctx.solve(ev1)
+    for k in a:
+        assert a[k] == b[k] == c[k], k
+    ctx.close()
+    ctx = ctx_for(c2, pop_k=8)
+    small = make_window(640, 480, 320.0, 240.0, 7000, 200, 3000, 0.35, 0.3, seed=21)
+    r_small = ctx.solve(dd.Events.of(small, device="cuda"))
+    r_big = ctx.solve(dd.Events.of(c2, device="cuda"))
+    r_small2 = ctx.solve(dd.Events.of(small, device="cuda"))
+    assert r_small == r_small2
+    assert r_big["K_hat"] == O.solve(O.Window.of(c2), -1.0, 1.0, 1e-4, 0.0, 8)["K_hat"]
     ctx.close()
 
 
@@ -152,7 +167,8 @@ def test_ragged_tiles_and_thread_counts():
     rng = np.random.default_rng(1)
     Ds = rng.uniform(-1, 1, 20).astype(np.float32)
     lo, hi = intervals(rng, 12, w.tau)
-    for kw in ({}, {"band_rows": 1}, {"band_rows": 7, "threads": 64}, {"band_rows": 61, "threads": 1024}):
+    for kw in ({}, {"band_rows": 1}, {"band_rows": 7, "threads": 64}, {"band_rows": 61, "threads": 1024},
+               {"band_rows": 5, "threads": 96, "host_loop": 1}):
         check_contrast(w, Ds, want_iwe=True, **kw)
         check_bound(w, lo, hi, want_iwe=True, **kw)
         check_solve(w, 3, trace=True, **kw)
