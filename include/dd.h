@@ -70,7 +70,8 @@ typedef struct {
     int32_t host_loop;      /* 0: each solve's rounds run as one CUDA graph with a       */
                             /*    conditional loop (no host round trips); 1: the host    */
                             /*    launches the rounds in batches and polls for the end   */
-    int32_t reserved[2];
+    int32_t max_splits;     /* most blocks that share one row band of a bound (default 16) */
+    int32_t reserved[1];
 } dd_config;
 
 /* One window of events in structure-of-arrays form. */
@@ -217,7 +218,7 @@ int dd_set_timing(dd_ctx* ctx, int32_t enable);
  * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
  * DD_ERR_CUDA. */
 #define DD_NOALLOC_MAX_EVENTS (1 << 20)
-#define DD_NOALLOC_SCRATCH_BYTES 10014720
+#define DD_NOALLOC_SCRATCH_BYTES 18403328
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
                         int32_t nD, dd_i128* K, void* stream);
 

@@ -21,11 +21,16 @@ struct dd_ctx {
 
     dd::Ev* ev = nullptr;
     int64_t ev_cap = 0;
+    float2* rcp = nullptr;        // per sorted event: 1/(x - FOE_x), 1/(y - FOE_y)
+    int64_t rcp_cap = 0;
     int16_t *in_x = nullptr, *in_y = nullptr;
     float* in_t = nullptr;
     int64_t in_cap = 0;
     int32_t *row_count = nullptr, *row_off = nullptr, *cursor = nullptr, *err = nullptr;
-    int32_t* work = nullptr;      // IWE item counter of the persistent evaluation grid
+    int32_t* work = nullptr;      // IWE unit counter of the persistent evaluation grid
+    uint32_t* macc = nullptr;     // merge buffers of split IWE items (zero between uses)
+    int32_t* mdone = nullptr;
+    unsigned long long* mfull = nullptr;
     int eval_blocks = 0;          // resident blocks of that grid
 
     dd::Task* tasks = nullptr;
@@ -112,6 +117,8 @@ cudaError_t copy(dd_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpy
 int ingest(dd_ctx* c, const dd_events* ev) {
     int rc = grow(&c->ev, &c->ev_cap, ev->n);
     if (rc) return rc;
+    rc = grow(&c->rcp, &c->rcp_cap, ev->n);
+    if (rc) return rc;
     const int16_t *x = ev->x, *y = ev->y;
     const float* t = ev->t;
     if (!ev->device_ptrs && ev->n > 0) {
@@ -135,7 +142,7 @@ int ingest(dd_ctx* c, const dd_events* ev) {
         y = c->in_y;
         t = c->in_t;
     }
-    DD_TRY(dd::launch_ingest(c->g, x, y, t, ev->n, ev->t0, ev->tau, c->ev, c->row_count, c->row_off, c->cursor,
+    DD_TRY(dd::launch_ingest(c->g, x, y, t, ev->n, ev->t0, ev->tau, c->ev, c->rcp, c->row_count, c->row_off, c->cursor,
                              c->err, c->stream));
     c->stats.kernel_launches += ev->n > 0 ? 3 : 1;
     return DD_OK;
@@ -184,8 +191,9 @@ cudaError_t eval(dd_ctx* c, const int32_t* n_tasks_dev, int32_t n_tasks_max, flo
         cudaError_t e = record(c);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = dd::launch_eval(c->g, c->ev, c->row_off, c->tasks, n_tasks_dev, n_tasks_max, tau, c->part, iwe,
-                                    st, c->threads, c->stream, c->work, c->eval_blocks);
+    cudaError_t e = dd::launch_eval(c->g, c->ev, c->rcp, c->row_off, c->tasks, n_tasks_dev, n_tasks_max, tau, c->part, iwe,
+                                    st, c->threads, c->stream, c->work, c->eval_blocks, c->macc, c->mdone,
+                                    c->mfull);
     if (e != cudaSuccess) return e;
     c->stats.kernel_launches++;
     c->stats.eval_launches++;
@@ -203,7 +211,8 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
             c->h_tasks[j].D_lo = A[j0 + j];
             c->h_tasks[j].D_hi = B[j0 + j];
             c->h_tasks[j].kind = kind;
-            c->h_tasks[j].pad = 0;
+            c->h_tasks[j].splits =
+                kind == dd::TASK_BOUND ? dd::bound_splits(c->g, A[j0 + j], B[j0 + j], ev->tau) : 1;
         }
         DD_TRY(copy(c, c->tasks, c->h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice));
         uint32_t* iw = nullptr;
@@ -266,8 +275,9 @@ int build_graph(dd_ctx* c, dd::TraceRec* trace) {
     DD_TRY(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
     DD_TRY(cudaStreamBeginCaptureToGraph(c->own, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = dd::launch_eval(c->g, c->ev, c->row_off, c->tasks, &c->st->n_tasks, c->max_tasks, 0.0f,
-                                     c->part, nullptr, c->st, c->threads, c->own, c->work, c->eval_blocks);
+    cudaError_t e1 = dd::launch_eval(c->g, c->ev, c->rcp, c->row_off, c->tasks, &c->st->n_tasks, c->max_tasks, 0.0f,
+                                     c->part, nullptr, c->st, c->threads, c->own, c->work, c->eval_blocks, c->macc,
+                                     c->mdone, c->mfull);
     cudaError_t e2 = dd::launch_control(c->g, c->st, c->queue, c->queue + c->cfg.queue_capacity, c->tasks,
                                         c->part, c->err, trace, h, 1, c->work, c->own);
     cudaGraph_t captured = nullptr;
@@ -304,7 +314,7 @@ int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol
     if (rc) return rc;
     const int64_t M = (int64_t)c->g.W * c->g.H;
     const i128 gamma_K = (i128)std::floor(gamma * (double)M * (double)M);
-    DD_TRY(dd::launch_init(c->st, c->tasks, M, D_lo, D_hi, tol_D, ev->tau, gamma_K, c->cfg.pop_k,
+    DD_TRY(dd::launch_init(c->g, c->st, c->tasks, M, D_lo, D_hi, tol_D, ev->tau, gamma_K, c->cfg.pop_k,
                            c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap, c->work, c->stream));
     c->stats.kernel_launches++;
     dd::TraceRec* tr_dev = trace_cap > 0 ? c->trace : nullptr;
@@ -394,6 +404,7 @@ const char* dd_strerror(int status) {
 void dd_destroy(dd_ctx* c) {
     if (!c) return;
     cudaFree(c->ev);
+    cudaFree(c->rcp);
     cudaFree(c->in_x);
     cudaFree(c->in_y);
     cudaFree(c->in_t);
@@ -402,6 +413,9 @@ void dd_destroy(dd_ctx* c) {
     cudaFree(c->cursor);
     cudaFree(c->err);
     cudaFree(c->work);
+    cudaFree(c->macc);
+    cudaFree(c->mdone);
+    cudaFree(c->mfull);
     cudaFree(c->tasks);
     cudaFree(c->part);
     cudaFree(c->keys);
@@ -432,6 +446,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
         k.max_rounds < 0)
         return DD_ERR_ARG;
     if (k.threads && (k.threads % 32 || k.threads > 1024)) return DD_ERR_ARG;
+    if (k.max_splits < 0 || k.max_splits > 64 || k.host_loop < 0) return DD_ERR_ARG;
     if (!k.pop_k) k.pop_k = 1;
     if (!k.queue_capacity) k.queue_capacity = 8192;
     if (!k.max_rounds) k.max_rounds = 1 << 20;
@@ -455,13 +470,15 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     int rows = k.band_rows ? k.band_rows : (int)(40 * 1024 / (4 * W));
     if (rows < 1) rows = 1;
     if (rows > H) rows = H;
-    if ((size_t)rows * W * 4 > 200 * 1024) rows = (int)(200 * 1024 / (4 * W));
+    if ((size_t)rows * (W | 1) * 4 > 200 * 1024) rows = (int)(200 * 1024 / (4 * (W | 1)));
     if (rows < 1) {
         delete c;
         return DD_ERR_ARG;
     }
     c->g.band_rows = rows;
     c->g.n_tiles = (H + rows - 1) / rows;
+    c->g.n_tb = dd::time_buckets(H);
+    c->g.max_splits = k.max_splits ? k.max_splits : 16;
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
     c->cfg.threads = c->threads;
     c->cfg.band_rows = rows;
@@ -470,11 +487,20 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     auto A = [&](void** p, size_t bytes) {
         if (rc == DD_OK && cudaMalloc(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
     };
-    A((void**)&c->row_count, sizeof(int32_t) * H);
-    A((void**)&c->row_off, sizeof(int32_t) * (H + 1));
-    A((void**)&c->cursor, sizeof(int32_t) * H);
+    const int bins = c->g.n_tb * H;
+    A((void**)&c->row_count, sizeof(int32_t) * bins);
+    A((void**)&c->row_off, sizeof(int32_t) * (bins + 1));
+    A((void**)&c->cursor, sizeof(int32_t) * bins);
     A((void**)&c->err, sizeof(int32_t));
     A((void**)&c->work, sizeof(int32_t));
+    A((void**)&c->macc, sizeof(uint32_t) * (size_t)c->max_tasks * W * H);
+    A((void**)&c->mdone, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles);
+    A((void**)&c->mfull, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles);
+    if (rc == DD_OK && (cudaMemset(c->macc, 0, sizeof(uint32_t) * (size_t)c->max_tasks * W * H) != cudaSuccess ||
+                        cudaMemset(c->mdone, 0, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles) != cudaSuccess ||
+                        cudaMemset(c->mfull, 0, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles) !=
+                            cudaSuccess))
+        rc = DD_ERR_CUDA;
     A((void**)&c->tasks, sizeof(dd::Task) * c->max_tasks);
     A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles);
     A((void**)&c->keys, sizeof(i128) * c->max_tasks);

@@ -18,11 +18,13 @@ struct __align__(8) Ev {
 enum TaskKind : int32_t { TASK_POINT = 0, TASK_BOUND = 1 };
 
 // One evaluation: the contrast at D_lo (TASK_POINT) or the bound over
-// [D_lo, D_hi] (TASK_BOUND).
+// [D_lo, D_hi] (TASK_BOUND).  `splits` (>= 1) is how many blocks share each
+// of its row bands; it changes the schedule only, never the result.
 struct Task {
     float D_lo, D_hi;
-    int32_t kind, pad;
+    int32_t kind, splits;
 };
+
 
 // Per (task, tile) partial sums of one IWE tile.
 struct Partial {
@@ -53,6 +55,7 @@ struct __align__(16) TraceRec {
 enum Phase : int32_t { PH_INIT = 0, PH_RUN = 1, PH_DONE = 2 };
 
 constexpr int MAX_POP = 64;
+constexpr int MAX_TASKS = 3 * MAX_POP;   // tasks of one evaluation launch
 
 // Device-resident state of one BnB search (Algorithm 1).
 struct __align__(16) SolveState {
@@ -69,28 +72,51 @@ struct __align__(16) SolveState {
     Popped pop[MAX_POP];
 };
 
-// Geometry of a context.
+// Geometry of a context.  Events are sorted by (time bucket, row): n_tb
+// buckets of equal length over [0, tau], n_tb * H <= 4096 bins, n_tb <= 8.
 struct Geom {
     int32_t W, H;
     float fx, fy;
-    int32_t band_rows, n_tiles;
+    int32_t band_rows, n_tiles, n_tb, max_splits;
 };
+
+// Row pitch of a shared-memory IWE tile: odd, so that the cells of one
+// column in consecutive rows fall in different shared-memory banks.
+__host__ __device__ inline int32_t tile_pitch(const Geom& g) { return g.W | 1; }
+
+// Blocks per row band for a bound task: about one per four estimated cells
+// per event.  An event's segment spans about |s(D_hi) - s(D_lo)| * |offset|
+// pixels; at t = 0 the scale change is |g(D_hi) - g(D_lo)|, g = 1/(1 - D tau),
+// and a typical offset is (W + H)/4.  A schedule heuristic only.
+__host__ __device__ inline int32_t bound_splits(const Geom& g, float D_lo, float D_hi, float tau) {
+    const float gl = 1.0f / (1.0f - D_lo * tau), gh = 1.0f / (1.0f - D_hi * tau);
+    const float ds = gh > gl ? gh - gl : gl - gh;
+    const float cells = 1.0f + ds * 0.25f * (float)(g.W + g.H);
+    const int32_t s = (int32_t)(cells * 0.25f);
+    return s < 1 ? 1 : (s > g.max_splits ? g.max_splits : s);
+}
 
 // Kernel launches (dd_kernels.cu).  All asynchronous on `s`.
 cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
-                          float t0, float tau, Ev* out, int32_t* row_count, int32_t* row_off,
+                          float t0, float tau, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
                           int32_t* cursor, int32_t* err, cudaStream_t s);
 // work: an item counter that is zero at launch (the kernel then runs a
 // persistent grid of grid_blocks blocks), or nullptr (one block per item).
-cudaError_t launch_eval(const Geom& g, const Ev* ev, const int32_t* row_off, const Task* tasks,
+cudaError_t launch_eval(const Geom& g, const Ev* ev, const float2* rcp, const int32_t* row_off, const Task* tasks,
                         const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
                         uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s,
-                        int32_t* work = nullptr, int grid_blocks = 0);
+                        int32_t* work = nullptr, int grid_blocks = 0, uint32_t* merge_acc = nullptr,
+                        int32_t* merge_done = nullptr, unsigned long long* merge_full = nullptr);
 int eval_resident_blocks(const Geom& g, int threads);
+// Time buckets for a frame of H rows: as many as fit 4096 bins, at most 8.
+inline int32_t time_buckets(int32_t H) {
+    int32_t b = 4096 / H;
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
 cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part,
                         i128* key, unsigned long long* S, unsigned long long* cells,
                         unsigned long long* full, cudaStream_t s);
-cudaError_t launch_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol,
+cudaError_t launch_init(const Geom& g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol,
                         float tau, i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds,
                         int32_t trace_cap, int32_t* work, cudaStream_t s);
 cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,

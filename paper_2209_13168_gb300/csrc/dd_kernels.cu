@@ -51,39 +51,48 @@ __device__ __forceinline__ bool event_ok(int xi, int yi, float ti, float tr, flo
     return isfinite(ti) && tr >= 0.0f && tr <= tau && xi >= 0 && xi < W && yi >= 0 && yi < H;
 }
 
-__global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(const int16_t* __restrict__ x,
+// Sort key of an event: (time bucket, row).  Bucket b holds the events with
+// t*scale in [b, b+1) (binary32 product), scale = n_tb/tau.
+__device__ __forceinline__ int event_key(const Geom& g, int yi, float tr, float bscale) {
+    int b = __float2int_rd(__fmul_rn(tr, bscale));
+    b = min(max(b, 0), g.n_tb - 1);
+    return b * g.H + yi;
+}
+
+__global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const int16_t* __restrict__ x,
                                                              const int16_t* __restrict__ y,
                                                              const float* __restrict__ t, int64_t n,
-                                                             float t0, float tau, int W, int H,
-                                                             int32_t* row_count, int32_t* err) {
+                                                             float t0, float tau, int32_t* row_count, int32_t* err) {
     __shared__ int32_t h[MAX_ROWS];
-    for (int r = threadIdx.x; r < H; r += blockDim.x) h[r] = 0;
+    const int bins = g.n_tb * g.H;
+    const float bscale = __fdiv_rn((float)g.n_tb, tau);
+    for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int xi = x[i], yi = y[i];
         float ti = t[i];
         float tr = __fsub_rn(ti, t0);
-        if (!event_ok(xi, yi, ti, tr, tau, W, H)) { bad = 1; continue; }
-        atomicAdd(&h[yi], 1);
+        if (!event_ok(xi, yi, ti, tr, tau, g.W, g.H)) { bad = 1; continue; }
+        atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
     }
     if (bad) atomicOr(err, 1);
     __syncthreads();
-    for (int r = threadIdx.x; r < H; r += blockDim.x)
+    for (int r = threadIdx.x; r < bins; r += blockDim.x)
         if (h[r]) atomicAdd(&row_count[r], h[r]);
 }
 
-// Exclusive scan of the row counts (H <= 4096) by one block.
-__global__ void __launch_bounds__(1024) k_row_scan(const int32_t* row_count, int H, int32_t* row_off,
+// Exclusive scan of the bin counts (at most 4096 bins) by one block.
+__global__ void __launch_bounds__(1024) k_row_scan(const int32_t* row_count, int bins, int32_t* row_off,
                                                    int32_t* cursor) {
     __shared__ int32_t wsum[32];
-    const int per = (H + 1023) / 1024;
+    const int per = (bins + 1023) / 1024;
     int base = threadIdx.x * per;
     int local[4];
     int tot = 0;
     for (int k = 0; k < per; k++) {
         int r = base + k;
-        local[k] = r < H ? row_count[r] : 0;
+        local[k] = r < bins ? row_count[r] : 0;
         tot += local[k];
     }
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -106,32 +115,36 @@ __global__ void __launch_bounds__(1024) k_row_scan(const int32_t* row_count, int
     int excl = v - tot + (wid ? wsum[wid - 1] : 0);
     for (int k = 0; k < per; k++) {
         int r = base + k;
-        if (r < H) { row_off[r] = excl; cursor[r] = excl; }
+        if (r < bins) { row_off[r] = excl; cursor[r] = excl; }
         excl += local[k];
     }
-    if (threadIdx.x == 1023) row_off[H] = excl;
+    if (threadIdx.x == 1023) row_off[bins] = excl;
 }
 
-// Scatter each valid event to its row segment; a block reserves one range
-// per row, so the global atomics are per (block, row).
-__global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(const int16_t* __restrict__ x,
+// Scatter each valid event to its bin; a block reserves one range per bin,
+// so the global atomics are per (block, bin).  Also stores the reciprocals
+// of the event's offsets from the FOE (used by the bound's cell walk).
+__global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const int16_t* __restrict__ x,
                                                                 const int16_t* __restrict__ y,
                                                                 const float* __restrict__ t, int64_t n,
-                                                                float t0, float tau, int W, int H,
-                                                                int32_t* cursor, Ev* __restrict__ out,
+                                                                float t0, float tau, int32_t* cursor,
+                                                                Ev* __restrict__ out, float2* __restrict__ rcp,
                                                                 int64_t chunk) {
     __shared__ int32_t h[MAX_ROWS];
     __shared__ int32_t base[MAX_ROWS];
+    const int bins = g.n_tb * g.H;
+    const float bscale = __fdiv_rn((float)g.n_tb, tau);
     int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-    for (int r = threadIdx.x; r < H; r += blockDim.x) h[r] = 0;
+    for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         int xi = x[i], yi = y[i];
         float ti = t[i];
-        if (event_ok(xi, yi, ti, __fsub_rn(ti, t0), tau, W, H)) atomicAdd(&h[yi], 1);
+        float tr = __fsub_rn(ti, t0);
+        if (event_ok(xi, yi, ti, tr, tau, g.W, g.H)) atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < H; r += blockDim.x) {
+    for (int r = threadIdx.x; r < bins; r += blockDim.x) {
         base[r] = h[r] ? atomicAdd(&cursor[r], h[r]) : 0;
         h[r] = 0;
     }
@@ -140,111 +153,176 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(const int16_t* _
         int xi = x[i], yi = y[i];
         float ti = t[i];
         float tr = __fsub_rn(ti, t0);
-        if (!event_ok(xi, yi, ti, tr, tau, W, H)) continue;
-        int pos = base[yi] + atomicAdd(&h[yi], 1);
+        if (!event_ok(xi, yi, ti, tr, tau, g.W, g.H)) continue;
+        const int key = event_key(g, yi, tr, bscale);
+        int pos = base[key] + atomicAdd(&h[key], 1);
         Ev e;
         e.x = (int16_t)xi;
         e.y = (int16_t)yi;
         e.t = tr;
         out[pos] = e;
+        rcp[pos] = make_float2(__frcp_rn(__fsub_rn((float)xi, g.fx)), __frcp_rn(__fsub_rn((float)yi, g.fy)));
     }
 }
 
 cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
-                          float t0, float tau, Ev* out, int32_t* row_count, int32_t* row_off,
+                          float t0, float tau, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
                           int32_t* cursor, int32_t* err, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(row_count, 0, sizeof(int32_t) * g.H, s);
+    const int bins = g.n_tb * g.H;
+    cudaError_t e = cudaMemsetAsync(row_count, 0, sizeof(int32_t) * bins, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     if (n > 0) {
         int64_t nb = (n + INGEST_THREADS - 1) / INGEST_THREADS;
         int blocks = (int)(nb < 304 ? nb : 304);
-        k_row_hist<<<blocks, INGEST_THREADS, 0, s>>>(x, y, t, n, t0, tau, g.W, g.H, row_count, err);
+        k_row_hist<<<blocks, INGEST_THREADS, 0, s>>>(g, x, y, t, n, t0, tau, row_count, err);
     }
-    k_row_scan<<<1, 1024, 0, s>>>(row_count, g.H, row_off, cursor);
+    k_row_scan<<<1, 1024, 0, s>>>(row_count, bins, row_off, cursor);
     if (n > 0) {
         int64_t chunk = 8192;
         int blocks = (int)((n + chunk - 1) / chunk);
-        k_row_scatter<<<blocks, INGEST_THREADS, 0, s>>>(x, y, t, n, t0, tau, g.W, g.H, cursor, out, chunk);
+        k_row_scatter<<<blocks, INGEST_THREADS, 0, s>>>(g, x, y, t, n, t0, tau, cursor, out, rcp, chunk);
     }
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- eval
 
-// Rows of events that can reach tile rows [y0, y1) for any scale in
-// [smin, smax] (a superset; binary64 with margins).
-__device__ void tile_event_range(const Geom& g, const int32_t* row_off, double smin, double smax, int y0,
-                                 int y1, int& e0, int& e1) {
-    double A = (double)y0 - 0.5625 - (double)g.fy;
-    double B = (double)(y1 - 1) + 0.5625 - (double)g.fy;
-    double dylo = A >= 0.0 ? A / smax : A / smin;
-    double dyhi = B >= 0.0 ? B / smin : B / smax;
-    double rl = floor((double)g.fy + dylo) - 1.0, rh = ceil((double)g.fy + dyhi) + 1.0;
-    int rlo = rl < 0.0 ? 0 : (rl > g.H - 1 ? g.H - 1 : (int)rl);
-    int rhi = rh < 0.0 ? 0 : (rh > g.H - 1 ? g.H - 1 : (int)rh);
-    e0 = row_off[rlo];
-    e1 = row_off[rhi + 1];
-}
-
-// Eq. (16) for one event restricted to tile rows [y0, y1): walk the cells of
-// the major axis (larger |offset|, ties to x); for major cell k the widened
-// s-range where the major coordinate rounds to k gives the run of minor
-// cells.  Identical per-cell arithmetic to a whole-frame walk; the tile only
-// skips major cells whose runs cannot reach its rows.
-__device__ __forceinline__ void segment_tile(const Geom& g, float dx, float dy, float sa, float sb, int xa,
-                                             int ya, int xb, int yb, int y0, int y1, uint32_t* tile) {
-    const int W = g.W, H = g.H;
-    if (dx == 0.0f && dy == 0.0f) {
-        if (xa >= 0 && xa < W && ya >= y0 && ya < y1) atomicAdd(&tile[(ya - y0) * W + xa], 1u);
+// Events of time bucket b that can reach tile rows [y0, y1) for D in
+// [Dl, Dh]: the scale s(D, t) = (1 - D t)/(1 - D tau) is monotone in D and in
+// t, so over the bucket's time range its extremes are at the four corners.
+// An event at row y can reach the rows only if (y - FOE_y) s meets them for
+// some s in that range; the rows that can are a contiguous range of the
+// bucket's row-sorted events.  Binary32 with margins far above its rounding
+// error (1e-4 relative on s, 1e-3 of a bucket in t, one row): a superset.
+__device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float Dl, float Dh, float tau,
+                                   float bscale, int b, int y0, int y1, int& e0, int& e1) {
+    const float tl = fmaxf(0.0f, __fdividef((float)b - 1e-3f, bscale));
+    const float th = fminf(tau, __fdividef((float)b + 1.001f, bscale));
+    float smin = 3.0e38f, smax = -3.0e38f;
+    for (int i = 0; i < 4; i++) {
+        const float D = (i & 1) ? Dh : Dl, t = (i & 2) ? th : tl;
+        const float s = __fdividef(1.0f - D * t, 1.0f - D * tau);
+        smin = fminf(smin, s);
+        smax = fmaxf(smax, s);
+    }
+    smin *= 1.0f - 1e-4f;
+    smax *= 1.0f + 1e-4f;
+    const float A = (float)y0 - 0.5625f - g.fy;
+    const float B = (float)(y1 - 1) + 0.5625f - g.fy;
+    const float dylo = __fdividef(A, A >= 0.0f ? smax : smin);
+    const float dyhi = __fdividef(B, B >= 0.0f ? smin : smax);
+    const float rl = floorf(g.fy + dylo) - 1.0f, rh = ceilf(g.fy + dyhi) + 1.0f;
+    if (rh < 0.0f || rl > (float)(g.H - 1)) {
+        e0 = e1 = 0;
         return;
     }
+    const int rlo = rl < 0.0f ? 0 : (int)rl;
+    const int rhi = rh > (float)(g.H - 1) ? g.H - 1 : (int)rh;
+    e0 = row_off[b * g.H + rlo];
+    e1 = row_off[b * g.H + rhi + 1];
+}
+
+// Eq. (16) for one event restricted to tile rows [y0, y1).  The segment is
+// walked along its major axis (larger |offset| from the FOE, ties to x): for
+// major cell k, the s-range where the major coordinate rounds to k (widened
+// by 2^-8 px, clipped to [s_a, s_b]) gives a run of minor cells.  The walk is
+// split into a set-up (seg_range: which major cells can reach the tile) and
+// the per-major-cell work (seg_cell), so that a warp can spread the major
+// cells of its events over its lanes.  The per-cell arithmetic is that of a
+// whole-frame walk; the tile only skips major cells whose runs cannot reach
+// its rows.
+enum SegMode : int { SEG_NONE = 0, SEG_ONE = 1, SEG_X = 2, SEG_Y = 3 };
+
+struct Seg {
+    int mode, k0, count, addr;   // addr: the tile cell of SEG_ONE
+    float dn, rm, sa, sb;        // minor offset, 1/major offset, scale range
+};
+
+__device__ __forceinline__ Seg seg_range(const Geom& g, float dx, float dy, float rdx, float rdy, float sa,
+                                         float sb, int xa, int ya, int xb, int yb, int y0, int y1) {
+    Seg s;
+    s.mode = SEG_NONE;
+    s.k0 = s.count = s.addr = 0;
+    s.dn = s.rm = 0.0f;
+    s.sa = sa;
+    s.sb = sb;
+    const int W = g.W, H = g.H;
+    if (dx == 0.0f && dy == 0.0f) {               // on the FOE: one pixel for every D
+        if (xa >= 0 && xa < W && ya >= y0 && ya < y1) {
+            s.mode = SEG_ONE;
+            s.count = 1;
+            s.addr = (ya - y0) * tile_pitch(g) + xa;
+        }
+        return s;
+    }
     if (fabsf(dx) >= fabsf(dy)) {
-        int k0 = min(xa, xb), k1 = max(xa, xb);
-        k0 = max(k0, 0);
-        k1 = min(k1, W - 1);
+        int k0 = max(min(xa, xb), 0), k1 = min(max(xa, xb), W - 1);
         if (dy == 0.0f) {
-            if (ya < y0 || ya >= y1) return;
+            if (ya < y0 || ya >= y1) return s;
         } else {
-            float r = __frcp_rn(dy);
-            float e0 = __fsub_rn(__fsub_rn((float)y0, g.fy), HALF_PLUS);
-            float e1 = __fadd_rn(__fsub_rn((float)(y1 - 1), g.fy), HALF_PLUS);
-            float b0 = __fmul_rn(e0, r), b1 = __fmul_rn(e1, r);
-            float lo = fmax_t(fmin_t(b0, b1), sa), hi = fmin_t(fmax_t(b0, b1), sb);
-            if (lo > hi) return;
-            int c0 = cell_of(g.fx, dx, lo), c1 = cell_of(g.fx, dx, hi);
+            const float r = rdy;
+            const float e0 = __fsub_rn(__fsub_rn((float)y0, g.fy), HALF_PLUS);
+            const float e1 = __fadd_rn(__fsub_rn((float)(y1 - 1), g.fy), HALF_PLUS);
+            const float b0 = __fmul_rn(e0, r), b1 = __fmul_rn(e1, r);
+            const float lo = fmax_t(fmin_t(b0, b1), sa), hi = fmin_t(fmax_t(b0, b1), sb);
+            if (lo > hi) return s;
+            const int c0 = cell_of(g.fx, dx, lo), c1 = cell_of(g.fx, dx, hi);
             k0 = max(k0, min(c0, c1) - 2);
             k1 = min(k1, max(c0, c1) + 2);
         }
-        float rm = __frcp_rn(dx);
-        for (int k = k0; k <= k1; k++) {
-            float e = __fsub_rn((float)k, g.fx);
-            float b1 = __fmul_rn(__fsub_rn(e, HALF_PLUS), rm), b2 = __fmul_rn(__fadd_rn(e, HALF_PLUS), rm);
-            float lo = b1 < b2 ? b1 : b2, hi = b1 < b2 ? b2 : b1;
-            if (lo < sa) lo = sa;
-            if (hi > sb) hi = sb;
-            if (lo > hi) continue;
-            int j1 = cell_of(g.fy, dy, lo), j2 = cell_of(g.fy, dy, hi);
-            int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), H - 1), y1 - 1);
-            for (int j = j0; j <= jn; j++) atomicAdd(&tile[(j - y0) * W + k], 1u);
-        }
+        if (k1 < k0) return s;
+        s.mode = SEG_X;
+        s.k0 = k0;
+        s.count = k1 - k0 + 1;
+        s.dn = dy;
+        s.rm = rdx;
     } else {
-        int k0 = max(max(min(ya, yb), 0), y0), k1 = min(min(max(ya, yb), H - 1), y1 - 1);
-        float rm = __frcp_rn(dy);
-        for (int k = k0; k <= k1; k++) {
-            float e = __fsub_rn((float)k, g.fy);
-            float b1 = __fmul_rn(__fsub_rn(e, HALF_PLUS), rm), b2 = __fmul_rn(__fadd_rn(e, HALF_PLUS), rm);
-            float lo = b1 < b2 ? b1 : b2, hi = b1 < b2 ? b2 : b1;
-            if (lo < sa) lo = sa;
-            if (hi > sb) hi = sb;
-            if (lo > hi) continue;
-            int j1 = cell_of(g.fx, dx, lo), j2 = cell_of(g.fx, dx, hi);
-            int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), W - 1);
-            uint32_t* row = tile + (k - y0) * W;
-            for (int j = j0; j <= jn; j++) atomicAdd(&row[j], 1u);
-        }
+        const int k0 = max(max(min(ya, yb), 0), y0), k1 = min(min(max(ya, yb), H - 1), y1 - 1);
+        if (k1 < k0) return s;
+        s.mode = SEG_Y;
+        s.k0 = k0;
+        s.count = k1 - k0 + 1;
+        s.dn = dx;
+        s.rm = rdy;
     }
+    return s;
+}
+
+__device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float dn, float rm, float sa, float sb,
+                                         int addr, int y0, int y1, uint32_t* tile) {
+    if (mode == SEG_ONE) {
+        atomicAdd(&tile[addr], 1u);
+        return;
+    }
+    const bool major_x = mode == SEG_X;
+    const float fm = major_x ? g.fx : g.fy, fn = major_x ? g.fy : g.fx;
+    const float e = __fsub_rn((float)k, fm);
+    const float b1 = __fmul_rn(__fsub_rn(e, HALF_PLUS), rm), b2 = __fmul_rn(__fadd_rn(e, HALF_PLUS), rm);
+    float lo = b1 < b2 ? b1 : b2, hi = b1 < b2 ? b2 : b1;
+    if (lo < sa) lo = sa;
+    if (hi > sb) hi = sb;
+    if (lo > hi) return;
+    const int j1 = cell_of(fn, dn, lo), j2 = cell_of(fn, dn, hi);
+    if (major_x) {
+        const int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), g.H - 1), y1 - 1);
+        for (int j = j0; j <= jn; j++) atomicAdd(&tile[(j - y0) * tile_pitch(g) + k], 1u);
+    } else {
+        const int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), g.W - 1);
+        uint32_t* row = tile + (k - y0) * tile_pitch(g);
+        for (int j = j0; j <= jn; j++) atomicAdd(&row[j], 1u);
+    }
+}
+
+// Inclusive prefix sum over the warp.
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -252,69 +330,201 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-// One (task, tile) item: zero the tile, scatter the events that can reach its
-// rows, reduce.  Writes part[task * n_tiles + tile].
-__device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ ev,
-                                          const int32_t* __restrict__ row_off, const Task& tk, int task, int ti,
-                                          float tau, Partial* __restrict__ part, uint32_t* __restrict__ iwe_out,
-                                          uint32_t* tile, unsigned long long (*red)[32], int* erange) {
-    const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
-    const int W = g.W, cnt = (y1 - y0) * W;
+constexpr int MAX_TB = 8;    // time buckets of the event sort
 
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) tile[i] = 0u;
-    if (threadIdx.x == 0) {
-        double gl = 1.0 / (1.0 - (double)tk.D_lo * (double)tau);
-        double gh = 1.0 / (1.0 - (double)tk.D_hi * (double)tau);
-        double smin = fmin(fmin(gl, gh), 1.0) * (1.0 - 1e-5), smax = fmax(fmax(gl, gh), 1.0) * (1.0 + 1e-5);
-        int e0, e1;
-        tile_event_range(g, row_off, smin, smax, y0, y1, e0, e1);
-        erange[0] = e0;
-        erange[1] = e1;
+// Buffers that merge the tiles of an item split over several blocks.
+struct Merge {
+    uint32_t* acc;                 // [task][M] counts, zero between uses
+    int32_t* done;                 // [task][tile] finished splits, zero between uses
+    unsigned long long* full;      // [task][tile] N_full sums, zero between uses
+};
+
+// One unit: split `split` of `splits` of the (task, tile) item.  The block
+// scatters its share of the events that can reach the tile's rows into the
+// shared tile.  An unsplit item reduces the tile itself; a split item adds
+// its tile into the L2 accumulator, and the last of its blocks to finish
+// reduces the accumulated tile.  Writes part[task * n_tiles + tile].
+__device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ ev, const float2* __restrict__ rcp,
+                                          const int32_t* __restrict__ row_off, const Task& tk, int task, int ti,
+                                          int split, int splits, const Merge& mg, float tau,
+                                          Partial* __restrict__ part, uint32_t* __restrict__ iwe_out,
+                                          uint32_t* tile, unsigned long long (*red)[32], int* erange, int* s_last) {
+    const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
+    const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+    // The tile arrives zeroed (the previous item's reduce clears what it read).
+    // erange[b] = first event of bucket b's candidate run; erange[MAX_TB + b] =
+    // the run's offset in the concatenation of all runs (MAX_TB + n_tb: total).
+    if (threadIdx.x < 32) {
+        int e0 = 0, e1 = 0;
+        if (lane < g.n_tb)
+            bucket_event_range(g, row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
+                               e1);
+        const int len = e1 - e0, incl = warp_incl_scan(len);
+        if (lane < g.n_tb) {
+            erange[lane] = e0;
+            erange[MAX_TB + lane] = incl - len;
+        }
+        if (lane == g.n_tb - 1) erange[MAX_TB + g.n_tb] = incl;
     }
     __syncthreads();
-    const int e0 = erange[0], e1 = erange[1];
     unsigned long long full = 0;
+    const int all = erange[MAX_TB + g.n_tb];
+    const int f_begin = (int)((long long)all * split / splits);
+    const int total = (int)((long long)all * (split + 1) / splits);
+    // Event index of position f of the concatenated runs.
+    auto event_at = [&](int f) {
+        int b = 0;
+#pragma unroll
+        for (int q = 1; q < MAX_TB; q++)
+            if (q < g.n_tb && f >= erange[MAX_TB + q]) b = q;
+        return erange[b] + (f - erange[MAX_TB + b]);
+    };
 
     if (tk.kind == TASK_POINT) {
         const float D = tk.D_lo, gg = warp_g(D, tau);
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const Ev v = ev[e];
-            const float dx = __fsub_rn((float)v.x, g.fx), dy = __fsub_rn((float)v.y, g.fy);
+#pragma unroll 4
+        for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
+            const Ev v = ev[event_at(f)];
             const float s = warp_s(D, v.t, gg);
-            const int ux = cell_of(g.fx, dx, s), uy = cell_of(g.fy, dy, s);
-            if ((unsigned)ux < (unsigned)W && uy >= y0 && uy < y1) atomicAdd(&tile[(uy - y0) * W + ux], 1u);
+            const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
+            if (uy < y0 || uy >= y1) continue;
+            const int ux = cell_of(g.fx, __fsub_rn((float)v.x, g.fx), s);
+            if ((unsigned)ux < (unsigned)W) atomicAdd(&tile[(uy - y0) * P + ux], 1u);
         }
     } else {
         const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const Ev v = ev[e];
-            const float dx = __fsub_rn((float)v.x, g.fx), dy = __fsub_rn((float)v.y, g.fy);
-            const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-            const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-            const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-            const int xa = cell_of(g.fx, dx, sa), ya = cell_of(g.fy, dy, sa);
-            const int xb = cell_of(g.fx, dx, sb), yb = cell_of(g.fy, dy, sb);
-            // Eq. (19): both end cells in the frame; counted by the tile of row ya.
-            if (xa >= 0 && xa < W && ya >= 0 && ya < g.H && xb >= 0 && xb < W && yb >= 0 && yb < g.H &&
-                ya >= y0 && ya < y1)
-                full++;
-            segment_tile(g, dx, dy, sa, sb, xa, ya, xb, yb, y0, y1, tile);
+        {
+            // Warps take 32 positions at a time, one event per lane.
+            for (int base = f_begin + (threadIdx.x >> 5) * 32; base < total; base += nw * 32) {
+                const int f = base + lane;
+                Seg sg;
+                sg.mode = SEG_NONE;
+                sg.k0 = sg.count = sg.addr = 0;
+                sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
+                if (f < total) {
+                    const int e = event_at(f);
+                    const Ev v = ev[e];
+                    const float dy = __fsub_rn((float)v.y, g.fy);
+                    const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+                    const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+                    const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+                    const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
+                    // Every covered cell lies between the rows of the two end
+                    // cells (each cell coordinate is monotone in s).
+                    if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                        const float dx = __fsub_rn((float)v.x, g.fx);
+                        const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
+                        // Eq. (19): both end cells in the frame; counted by the tile of row ya.
+                        if (xa >= 0 && xa < W && ya >= 0 && ya < g.H && xb >= 0 && xb < W && yb >= 0 &&
+                            yb < g.H && ya >= y0 && ya < y1)
+                            full++;
+                        if (xa == xb && ya == yb) {
+                            // Both ends in one pixel: each cell coordinate is
+                            // monotone in s, so the segment covers that pixel only.
+                            if (xa >= 0 && xa < W && ya >= y0 && ya < y1) {
+                                sg.mode = SEG_ONE;
+                                sg.count = 1;
+                                sg.addr = (ya - y0) * P + xa;
+                            }
+                        } else {
+                            const float2 r = rcp[e];
+                            sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+                        }
+                    }
+                }
+                const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
+                if (cmax == 0) continue;
+                if (cmax <= 2) {                  // short runs: each lane walks its own
+                    for (int i = 0; i < sg.count; i++)
+                        seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile);
+                    continue;
+                }
+                // Long runs: spread the (event, major cell) pairs over the lanes.
+                const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int c0 = 0; c0 < total; c0 += 32) {
+                    const int gi = c0 + lane;
+                    int o = 0;                    // owner: first lane whose inclusive sum exceeds gi
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int probe = __shfl_sync(0xffffffffu, incl, o + step - 1);
+                        if (probe <= gi) o += step;
+                    }
+                    const int om = __shfl_sync(0xffffffffu, sg.mode, o);
+                    const int ok = __shfl_sync(0xffffffffu, sg.k0 - excl, o);
+                    const int oa = __shfl_sync(0xffffffffu, sg.addr, o);
+                    const float odn = __shfl_sync(0xffffffffu, sg.dn, o);
+                    const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
+                    const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
+                    const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
+                    if (gi < total) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile);
+                }
+            }
         }
     }
     __syncthreads();
 
-    unsigned long long S = 0, C = 0;
     uint32_t* out = iwe_out ? iwe_out + (size_t)task * W * g.H + (size_t)y0 * W : nullptr;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const unsigned long long v = tile[i];
-        S += v * v;
-        C += v;
-        if (out) out[i] = (uint32_t)v;
+    const int item = task * g.n_tiles + ti;
+    unsigned long long S = 0, C = 0;
+    // Tile rows have pitch P (odd), frame rows have pitch W: warps take rows,
+    // lanes take columns.
+    if (splits == 1) {
+        for (int r = wid; r < rows; r += nw)
+            for (int c = lane; c < W; c += 32) {
+                const unsigned long long v = tile[r * P + c];
+                tile[r * P + c] = 0u;
+                S += v * v;
+                C += v;
+                if (out) out[r * W + c] = (uint32_t)v;
+            }
+    } else {
+        uint32_t* acc = mg.acc + (size_t)task * W * g.H + (size_t)y0 * W;
+        // Splits of one item finish together: each starts its pass at its own
+        // row so that they add into different words at a time.
+        const int rot = (int)((long long)rows * split / splits);
+        for (int q = wid; q < rows; q += nw) {
+            const int r = q + rot < rows ? q + rot : q + rot - rows;
+            for (int c = lane; c < W; c += 32) {
+                const uint32_t v = tile[r * P + c];
+                if (v) {
+                    tile[r * P + c] = 0u;
+                    atomicAdd(&acc[r * W + c], v);
+                }
+            }
+        }
+        __threadfence();                          // this thread's additions, before the count below
+        full = warp_sum(full);
+        if (lane == 0) red[2][wid] = full;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long f = 0;
+            for (int w = 0; w < nw; w++) f += red[2][w];
+            if (f) atomicAdd(&mg.full[item], f);
+            __threadfence();
+            *s_last = atomicAdd(&mg.done[item], 1) == splits - 1;
+        }
+        __syncthreads();
+        if (!*s_last) return;                     // another split finishes the item
+        __threadfence();                          // every split's additions are visible now
+        for (int i = threadIdx.x; i < rows * W; i += blockDim.x) {
+            const unsigned long long v = __ldcg(&acc[i]);
+            if (v) acc[i] = 0u;
+            S += v * v;
+            C += v;
+            if (out) out[i] = (uint32_t)v;
+        }
+        full = 0;
+        if (threadIdx.x == 0) {
+            full = atomicExch(&mg.full[item], 0ull);
+            mg.done[item] = 0;
+        }
     }
     S = warp_sum(S);
     C = warp_sum(C);
     full = warp_sum(full);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
     if (lane == 0) { red[0][wid] = S; red[1][wid] = C; red[2][wid] = full; }
     __syncthreads();
     if (wid == 0) {
@@ -329,77 +539,101 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
             p.S = S;
             p.cells = C;
             p.full = full;
-            part[task * g.n_tiles + ti] = p;
+            part[item] = p;
         }
     }
 }
 
-// IWE evaluation of a task list.  With `work` (an item counter that is zero
-// at launch), a grid of resident blocks takes (task, tile) items in turn,
-// the tasks queued last (a round's bound tasks) first.  Without it, block b
-// evaluates item b.  A finished search launches nothing.
+// IWE evaluation of a task list.  With `work` (a unit counter that is zero
+// at launch), a grid of resident blocks takes units in turn: a task of
+// `splits` splits has n_tiles * splits units, and the tasks queued last (a
+// round's bound tasks) come first.  Without it, block b evaluates (task,
+// tile) item b unsplit.  A finished search launches nothing.
 __global__ void __launch_bounds__(1024) k_eval(Geom g, const Ev* __restrict__ ev,
+                                               const float2* __restrict__ rcp,
                                                const int32_t* __restrict__ row_off,
                                                const Task* __restrict__ tasks, const int32_t* n_tasks_dev,
                                                int32_t n_tasks_host, float tau, Partial* __restrict__ part,
                                                uint32_t* __restrict__ iwe_out, const SolveState* st,
-                                               int32_t* work) {
+                                               int32_t* work, Merge mg) {
     extern __shared__ uint32_t tile[];
     __shared__ unsigned long long red[3][32];
-    __shared__ int erange[2];
-    __shared__ int s_item;
+    __shared__ int erange[2 * MAX_TB + 1];
+    __shared__ int ustart[MAX_TASKS + 1];
+    __shared__ int s_item, s_last;
     if (st && st->phase == PH_DONE) return;
     const int n_tasks = n_tasks_dev ? *n_tasks_dev : n_tasks_host;
     if (st) tau = st->tau;                       // a solve keeps its tau in the state
-    const int n_items = n_tasks * g.n_tiles;
+    const int tile_words = g.band_rows * tile_pitch(g);
     if (!work) {
         const int task = blockIdx.x / g.n_tiles;
         if (task >= n_tasks) return;
-        eval_item(g, ev, row_off, tasks[task], task, blockIdx.x - task * g.n_tiles, tau, part, iwe_out, tile, red,
-                  erange);
+        for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
+        eval_item(g, ev, rcp, row_off, tasks[task], task, blockIdx.x - task * g.n_tiles, 0, 1, mg, tau, part,
+                  iwe_out, tile, red, erange, &s_last);
         return;
     }
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+    if (threadIdx.x < 32) {                       // unit offsets, tasks in processing order
+        int run = 0;
+        for (int base = 0; base < n_tasks; base += 32) {
+            const int p = base + threadIdx.x;
+            const int c = p < n_tasks ? g.n_tiles * max(1, tasks[n_tasks - 1 - p].splits) : 0;
+            const int incl = warp_incl_scan(c);
+            if (p < n_tasks) ustart[p] = run + incl - c;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (threadIdx.x == 0) ustart[n_tasks] = run;
+    }
+    for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
+    __syncthreads();
+    const int n_units = ustart[n_tasks];
     for (;;) {
-        __syncthreads();                          // the previous item's readers are done
-        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= n_items) break;
-        const int task = n_tasks - 1 - item / g.n_tiles;
-        eval_item(g, ev, row_off, tasks[task], task, item % g.n_tiles, tau, part, iwe_out, tile, red, erange);
+        const int u = s_item;
+        if (u >= n_units) break;
+        __syncthreads();                          // every thread has read s_item
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);   // the next unit, fetched early
+        int lo = 0, hi = n_tasks - 1;             // last p with ustart[p] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ustart[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const int task = n_tasks - 1 - lo;
+        const Task tk = tasks[task];
+        const int splits = max(1, tk.splits), r = u - ustart[lo];
+        eval_item(g, ev, rcp, row_off, tk, task, r / splits, r % splits, splits, mg, tau, part, iwe_out, tile, red,
+                  erange, &s_last);
+        __syncthreads();                          // the unit's readers are done; s_item is set
     }
 }
 
 int eval_resident_blocks(const Geom& g, int threads) {
     int per_sm = 0, dev = 0, sms = 0;
-    size_t smem = (size_t)g.band_rows * g.W * sizeof(uint32_t);
+    size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval, threads, smem) != cudaSuccess) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     return per_sm * sms;
 }
 
-// The dynamic shared-memory limit is a per-function attribute shared by all
-// contexts: only ever raise it.
-cudaError_t eval_smem_setup(const Geom& g) {
-    static int current = 0;
-    int bytes = g.band_rows * g.W * (int)sizeof(uint32_t);
-    if (bytes <= current) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) current = bytes;
-    return e;
-}
-
-cudaError_t launch_eval(const Geom& g, const Ev* ev, const int32_t* row_off, const Task* tasks,
+cudaError_t launch_eval(const Geom& g, const Ev* ev, const float2* rcp, const int32_t* row_off, const Task* tasks,
                         const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
                         uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s, int32_t* work,
-                        int grid_blocks) {
+                        int grid_blocks, uint32_t* merge_acc, int32_t* merge_done, unsigned long long* merge_full) {
+    if (work && (!merge_acc || !merge_done || !merge_full)) return cudaErrorInvalidValue;
+    Merge mg;
+    mg.acc = merge_acc;
+    mg.done = merge_done;
+    mg.full = merge_full;
     if (n_tasks_max <= 0) return cudaSuccess;
-    size_t smem = (size_t)g.band_rows * g.W * sizeof(uint32_t);
-    int items = n_tasks_max * g.n_tiles;
-    int grid = work && grid_blocks > 0 && grid_blocks < items ? grid_blocks : items;
-    k_eval<<<grid, threads, smem, s>>>(g, ev, row_off, tasks, n_tasks_dev, n_tasks_max, tau, part, iwe_out, st,
-                                       work);
+    size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
+    // Split units: up to max_splits per (task, tile) item when a work counter
+    // schedules them.
+    const long long units = (long long)n_tasks_max * g.n_tiles * (work ? g.max_splits : 1);
+    const int grid = work && grid_blocks > 0 && grid_blocks < units ? grid_blocks : (int)units;
+    k_eval<<<grid, threads, smem, s>>>(g, ev, rcp, row_off, tasks, n_tasks_dev, n_tasks_max, tau, part, iwe_out,
+                                       st, work, mg);
     return cudaGetLastError();
 }
 
@@ -449,7 +683,7 @@ __device__ __forceinline__ float centre(float lo, float hi) {
     return __fadd_rn(lo, __fmul_rn(0.5f, __fsub_rn(hi, lo)));
 }
 
-__global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
+__global__ void k_init(Geom g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
                        i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
                        int32_t* work) {
     if (threadIdx.x != 0) return;
@@ -481,20 +715,20 @@ __global__ void k_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float
     Task a, b;
     a.D_lo = a.D_hi = st->D_hat;
     a.kind = TASK_POINT;
-    a.pad = 0;
+    a.splits = 1;
     b.D_lo = D_lo;                                // bound of the domain (queued first)
     b.D_hi = D_hi;
     b.kind = TASK_BOUND;
-    b.pad = 0;
+    b.splits = bound_splits(g, D_lo, D_hi, tau);
     tasks[0] = a;
     tasks[1] = b;
     st->n_tasks = 2;
 }
 
-cudaError_t launch_init(SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
+cudaError_t launch_init(const Geom& g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
                         i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
                         int32_t* work, cudaStream_t s) {
-    k_init<<<1, 32, 0, s>>>(st, tasks, M, D_lo, D_hi, tol, tau, gamma_K, K_pop, qcap, max_rounds, trace_cap, work);
+    k_init<<<1, 32, 0, s>>>(g, st, tasks, M, D_lo, D_hi, tol, tau, gamma_K, K_pop, qcap, max_rounds, trace_cap, work);
     return cudaGetLastError();
 }
 
@@ -517,29 +751,50 @@ __device__ __forceinline__ int rank_in(const Node* q, int n, const Node& e) {
 
 constexpr int CTL_THREADS = 256;
 
+__device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    lo = __shfl_sync(0xffffffffu, lo, src);
+    hi = __shfl_sync(0xffffffffu, hi, src);
+    return (i128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+
+__device__ __forceinline__ i128 warp_max_i128(i128 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const i128 w = shfl_i128(v, threadIdx.x ^ o);
+        if (w > v) v = w;
+    }
+    return v;
+}
+
 // One block per search.  Consumes the keys of the round just evaluated
 // (Algorithm 1: incumbent update, leaves, child bounds and their insertion),
 // then dequeues the next batch (dequeue and gap test) and writes its tasks,
-// or finishes.  The queue is kept sorted in priority order in one of two
-// buffers: insertion is a parallel merge into the other buffer, a dequeue
-// takes a prefix.
+// or finishes.  The search state is staged in shared memory; per-interval
+// work runs one interval per lane of warp 0.  The queue is kept sorted in
+// priority order in one of two buffers: insertion is a parallel merge into
+// the other buffer, a dequeue takes a prefix.
 __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st, Node* qa, Node* qb, Task* tasks,
                                                         const Partial* part, const int32_t* err, TraceRec* trace,
                                                         cudaGraphConditionalHandle loop, int32_t use_loop,
                                                         int32_t* work) {
+    __shared__ SolveState s;
     __shared__ i128 key[3 * MAX_POP];
     __shared__ unsigned long long cells[3 * MAX_POP];
     __shared__ Node kids[2 * MAX_POP + 1];
     __shared__ Node sorted_kids[2 * MAX_POP + 1];
     __shared__ int s_nk, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    if (st->phase == PH_DONE) {
+    static_assert(sizeof(SolveState) % 16 == 0, "state is copied as int4");
+    for (int i = tid; i < (int)(sizeof(SolveState) / 16); i += blockDim.x)
+        reinterpret_cast<int4*>(&s)[i] = reinterpret_cast<const int4*>(st)[i];
+    __syncthreads();
+    if (s.phase == PH_DONE) {
         if (use_loop && tid == 0) cudaGraphSetConditional(loop, 0);
         return;
     }
     if (tid == 0) *work = 0;                      // the next evaluation starts at item 0
-    const int64_t M = st->M;
-    const int n_tasks = st->n_tasks;
+    const int64_t M = s.M;
+    const int n_tasks = s.n_tasks;
 
     for (int t = wid; t < n_tasks; t += nw) {
         unsigned long long S = 0, C = 0, F = 0;
@@ -559,42 +814,60 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
     }
     __syncthreads();
 
-    if (tid == 0) {
+    if (wid == 0) {
         int stop = 0, nk = 0;
         if (*err) {
-            st->status = DD_ERR_ARG;
+            if (lane == 0) s.status = DD_ERR_ARG;
             stop = 1;
-        } else if (st->phase == PH_INIT) {
-            st->K_hat = key[0];
-            st->point_evals = 1;
-            st->bound_evals = 1;
-            st->cells = (int64_t)(cells[0] + cells[1]);
-            st->bcells = (int64_t)cells[1];
-            Node root;
-            root.lo = st->D_lo;
-            root.hi = st->D_hi;
-            root.pad0 = root.pad1 = 0;
-            root.kb = key[1];
-            kids[nk++] = root;                    // the domain is queued unconditionally
-            st->phase = PH_RUN;
+        } else if (s.phase == PH_INIT) {
+            if (lane == 0) {
+                s.K_hat = key[0];
+                s.point_evals = 1;
+                s.bound_evals = 1;
+                s.cells = (int64_t)(cells[0] + cells[1]);
+                s.bcells = (int64_t)cells[1];
+                Node root;
+                root.lo = s.D_lo;
+                root.hi = s.D_hi;
+                root.pad0 = root.pad1 = 0;
+                root.kb = key[1];
+                kids[0] = root;                   // the domain is queued unconditionally
+                s.phase = PH_RUN;
+            }
+            nk = 1;
         } else {
-            const int np = st->n_pop;
-            i128 K_hat = st->K_hat;
-            for (int j = 0; j < np; j++) {        // incumbent update, dequeue order
-                const Popped& p = st->pop[j];
-                const i128 kc = key[p.t_point];
-                st->nodes_expanded++;
-                st->point_evals++;
-                st->cells += (int64_t)cells[p.t_point];
-                if (kc >= K_hat) {
-                    K_hat = kc;
-                    st->D_hat = p.c;
+            const int np = s.n_pop;
+            // Incumbent update in dequeue order (a centre with K >= K_hat wins):
+            // per chunk of 32, the chunk maximum wins if it reaches the running
+            // incumbent, at the last lane attaining it.
+            i128 K_hat = s.K_hat;
+            float D_hat = s.D_hat;
+            unsigned long long pc = 0;
+            for (int base = 0; base < np; base += 32) {
+                const int j = base + lane;
+                const bool v = j < np;
+                const i128 kc = v ? key[s.pop[j].t_point] : (i128)(-1);
+                if (v) pc += cells[s.pop[j].t_point];
+                const i128 m = warp_max_i128(kc);
+                if (m >= K_hat) {
+                    const unsigned at = __ballot_sync(0xffffffffu, v && kc == m);
+                    const int last = 31 - __clz(at);
+                    K_hat = m;
+                    D_hat = __shfl_sync(0xffffffffu, v ? s.pop[j].c : 0.0f, last);
                 }
             }
-            st->K_hat = K_hat;
-            for (int j = 0; j < np; j++) {        // leaves and child bounds
-                const Popped& p = st->pop[j];
-                if (st->trace_len < st->trace_cap && trace) {
+            pc = warp_sum(pc);
+            // Leaves, traces, child bounds, children inserted against the
+            // end-of-round incumbent.
+            int nonleaf = 0, has_leaf = 0;
+            i128 lmax = (i128)(-1);
+            unsigned long long bc = 0;
+            for (int base = 0; base < np; base += 32) {
+                const int j = base + lane;
+                const bool v = j < np;
+                Popped p;
+                if (v) p = s.pop[j];
+                if (v && trace && s.trace_len + j < s.trace_cap) {
                     TraceRec r;
                     r.D_lo = p.lo;
                     r.D_hi = p.hi;
@@ -602,40 +875,71 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
                     r.leaf = p.leaf;
                     r.Kbar = p.kb;
                     r.K_c = key[p.t_point];
-                    trace[st->trace_len] = r;
+                    trace[s.trace_len + j] = r;
                 }
-                st->trace_len++;
-                if (p.leaf) {
-                    if (!st->have_leaf || p.kb > st->leaf_max) st->leaf_max = p.kb;
-                    st->have_leaf = 1;
-                    continue;
+                const bool leaf = v && p.leaf, split = v && !p.leaf;
+                if (leaf && (!has_leaf || p.kb > lmax)) lmax = p.kb;
+                has_leaf |= leaf;
+                i128 kl = 0, kr = 0;
+                int c = 0;
+                if (split) {
+                    kl = key[p.t_left];
+                    kr = key[p.t_right];
+                    bc += cells[p.t_left] + cells[p.t_right];
+                    c = (kl >= K_hat) + (kr >= K_hat);
                 }
-                st->bound_evals += 2;
-                st->cells += (int64_t)(cells[p.t_left] + cells[p.t_right]);
-                st->bcells += (int64_t)(cells[p.t_left] + cells[p.t_right]);
-                for (int side = 0; side < 2; side++) {
-                    const i128 kb = key[side ? p.t_right : p.t_left];
-                    if (kb >= K_hat) {            // insertion test, end-of-round incumbent
+                nonleaf += __popc(__ballot_sync(0xffffffffu, split));
+                const int incl = warp_incl_scan(c);
+                const int at = nk + incl - c;
+                if (split) {
+                    int o = at;
+                    if (kl >= K_hat) {
                         Node nd;
-                        nd.lo = side ? p.c : p.lo;
-                        nd.hi = side ? p.hi : p.c;
+                        nd.lo = p.lo;
+                        nd.hi = p.c;
                         nd.pad0 = nd.pad1 = 0;
-                        nd.kb = kb;
-                        kids[nk++] = nd;
+                        nd.kb = kl;
+                        kids[o++] = nd;
+                    }
+                    if (kr >= K_hat) {
+                        Node nd;
+                        nd.lo = p.c;
+                        nd.hi = p.hi;
+                        nd.pad0 = nd.pad1 = 0;
+                        nd.kb = kr;
+                        kids[o] = nd;
                     }
                 }
+                nk += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            bc = warp_sum(bc);
+            has_leaf = __any_sync(0xffffffffu, has_leaf);
+            lmax = warp_max_i128(lmax);
+            if (lane == 0) {
+                s.K_hat = K_hat;
+                s.D_hat = D_hat;
+                s.nodes_expanded += np;
+                s.point_evals += np;
+                s.bound_evals += 2 * nonleaf;
+                s.cells += (int64_t)(pc + bc);
+                s.bcells += (int64_t)bc;
+                if (has_leaf && (!s.have_leaf || lmax > s.leaf_max)) s.leaf_max = lmax;
+                s.have_leaf |= has_leaf;
+                s.trace_len += np;
             }
         }
-        if (!stop && st->q_n + nk > st->qcap) {
-            st->status = DD_ERR_QUEUE_OVERFLOW;
+        if (!stop && s.q_n + nk > s.qcap) {
+            if (lane == 0) s.status = DD_ERR_QUEUE_OVERFLOW;
             stop = 1;
         }
-        s_nk = nk;
-        s_stop = stop;
+        if (lane == 0) {
+            s_nk = nk;
+            s_stop = stop;
+        }
     }
     __syncthreads();
     const int nk = s_nk;
-    int stop = s_stop;
+    const int stop = s_stop;
 
     if (!stop) {
         // sort the new children, then merge them with the queued intervals
@@ -645,9 +949,9 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
             sorted_kids[r] = kids[i];
         }
         __syncthreads();
-        const Node* src = (st->q_cur ? qb : qa) + st->q_start;
-        Node* dst = st->q_cur ? qa : qb;
-        const int a = st->q_n;
+        const Node* src = (s.q_cur ? qb : qa) + s.q_start;
+        Node* dst = s.q_cur ? qa : qb;
+        const int a = s.q_n;
         for (int i = tid; i < a; i += blockDim.x) {
             const Node e = src[i];
             dst[i + rank_in(sorted_kids, nk, e)] = e;
@@ -658,89 +962,120 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
         }
         __syncthreads();
         if (tid == 0) {
-            st->q_cur ^= 1;
-            st->q_start = 0;
-            st->q_n = a + nk;
-            if (st->q_n > st->max_queue) st->max_queue = st->q_n;
+            s.q_cur ^= 1;
+            s.q_start = 0;
+            s.q_n = a + nk;
+            if (s.q_n > s.max_queue) s.max_queue = s.q_n;
         }
         __syncthreads();
     }
 
-    if (tid == 0) {
-        const Node* q = st->q_cur ? qb : qa;
+    if (wid == 0) {
+        const Node* q = s.q_cur ? qb : qa;
         int np = 0;
         if (!stop) {                              // dequeue up to K_pop intervals
-            const i128 K0 = st->K_hat, gK = st->gamma_K;
-            while (np < st->K_pop && np < st->q_n) {
-                const Node nd = q[np];
-                if (nd.kb - K0 <= gK) {           // gap test
-                    if (np == 0) {
-                        st->have_stop = 1;
-                        st->stop_kb = nd.kb;
+            const i128 K0 = s.K_hat, gK = s.gamma_K;
+            const int lim = min(s.K_pop, s.q_n);
+            for (int base = 0; base < lim; base += 32) {
+                const int j = base + lane;
+                const bool v = j < lim;
+                Node nd;
+                if (v) nd = q[j];
+                const bool pass = v && (nd.kb - K0 > gK);   // gap test
+                const unsigned fail = __ballot_sync(0xffffffffu, v && !pass);
+                const int first = fail ? __ffs(fail) - 1 : 32;
+                if (v && lane < first) {
+                    s.pop[j].lo = nd.lo;
+                    s.pop[j].hi = nd.hi;
+                    s.pop[j].kb = nd.kb;
+                }
+                if (fail) {
+                    if (base + first == 0 && lane == 0) {
+                        s.have_stop = 1;
+                        s.stop_kb = nd.kb;
                     }
+                    np = base + first;
                     break;
                 }
-                Popped& p = st->pop[np];
-                p.lo = nd.lo;
-                p.hi = nd.hi;
-                p.kb = nd.kb;
-                np++;
+                np = min(lim, base + 32);
             }
-            st->q_start = np;
-            st->q_n -= np;
+            if (lane == 0) {
+                s.q_start = np;
+                s.q_n -= np;
+            }
         }
+        __syncwarp();
         if (stop || np == 0) {
-            i128 top = st->K_hat;
-            if (st->have_leaf && st->leaf_max > top) top = st->leaf_max;
-            if (st->have_stop && st->stop_kb > top) top = st->stop_kb;
-            st->stop_kb = top - st->K_hat;        // the certificate gap_K
-            st->n_pop = 0;
-            st->n_tasks = 0;
-            st->phase = PH_DONE;
+            if (lane == 0) {
+                i128 top = s.K_hat;
+                if (s.have_leaf && s.leaf_max > top) top = s.leaf_max;
+                if (s.have_stop && s.stop_kb > top) top = s.stop_kb;
+                s.stop_kb = top - s.K_hat;        // the certificate gap_K
+                s.n_pop = 0;
+                s.n_tasks = 0;
+                s.phase = PH_DONE;
+            }
         } else {
-            st->rounds++;
-            int nt = np;
-            for (int j = 0; j < np; j++) {        // centre and bisection
-                Popped& p = st->pop[j];
-                p.c = centre(p.lo, p.hi);
-                const float w = __fsub_rn(p.hi, p.lo);
-                p.leaf = !(w > st->tol) || !(p.c > p.lo) || !(p.c < p.hi);
-                p.t_point = j;
-                Task a;
-                a.D_lo = a.D_hi = p.c;
-                a.kind = TASK_POINT;
-                a.pad = 0;
-                tasks[j] = a;
-                if (!p.leaf) {
-                    p.t_left = nt;
-                    p.t_right = nt + 1;
-                    Task l, r;
-                    l.D_lo = p.lo;
-                    l.D_hi = p.c;
-                    l.kind = TASK_BOUND;
-                    l.pad = 0;
-                    r.D_lo = p.c;
-                    r.D_hi = p.hi;
-                    r.kind = TASK_BOUND;
-                    r.pad = 0;
-                    tasks[nt] = l;
-                    tasks[nt + 1] = r;
-                    nt += 2;
-                } else {
-                    p.t_left = p.t_right = -1;
+            int nl_before = 0;
+            for (int base = 0; base < np; base += 32) {   // centre and bisection
+                const int j = base + lane;
+                const bool v = j < np;
+                bool split = false;
+                if (v) {
+                    Popped& p = s.pop[j];
+                    p.c = centre(p.lo, p.hi);
+                    const float w = __fsub_rn(p.hi, p.lo);
+                    p.leaf = !(w > s.tol) || !(p.c > p.lo) || !(p.c < p.hi);
+                    split = !p.leaf;
+                }
+                const unsigned sb = __ballot_sync(0xffffffffu, split);
+                if (v) {
+                    Popped& p = s.pop[j];
+                    p.t_point = j;
+                    Task a;
+                    a.D_lo = a.D_hi = p.c;
+                    a.kind = TASK_POINT;
+                    a.splits = 1;
+                    tasks[j] = a;
+                    if (split) {
+                        const int t = np + 2 * (nl_before + __popc(sb & ((1u << lane) - 1u)));
+                        p.t_left = t;
+                        p.t_right = t + 1;
+                        Task l, r;
+                        l.D_lo = p.lo;
+                        l.D_hi = p.c;
+                        l.kind = TASK_BOUND;
+                        l.splits = bound_splits(g, p.lo, p.c, s.tau);
+                        r.D_lo = p.c;
+                        r.D_hi = p.hi;
+                        r.kind = TASK_BOUND;
+                        r.splits = bound_splits(g, p.c, p.hi, s.tau);
+                        tasks[t] = l;
+                        tasks[t + 1] = r;
+                    } else {
+                        p.t_left = p.t_right = -1;
+                    }
+                }
+                nl_before += __popc(sb);
+            }
+            if (lane == 0) {
+                s.rounds++;
+                s.n_pop = np;
+                s.n_tasks = np + 2 * nl_before;
+                if (s.rounds > s.max_rounds) {
+                    s.status = DD_ERR_TIMEOUT;
+                    s.stop_kb = 0;
+                    s.n_tasks = 0;
+                    s.phase = PH_DONE;
                 }
             }
-            st->n_pop = np;
-            st->n_tasks = nt;
-            if (st->rounds > st->max_rounds) {
-                st->status = DD_ERR_TIMEOUT;
-                st->stop_kb = 0;
-                st->n_tasks = 0;
-                st->phase = PH_DONE;
-            }
         }
-        if (use_loop) cudaGraphSetConditional(loop, st->phase == PH_DONE ? 0u : 1u);
+        __syncwarp();
+        if (use_loop && lane == 0) cudaGraphSetConditional(loop, s.phase == PH_DONE ? 0u : 1u);
     }
+    __syncthreads();
+    for (int i = tid; i < (int)(sizeof(SolveState) / 16); i += blockDim.x)
+        reinterpret_cast<int4*>(st)[i] = reinterpret_cast<const int4*>(&s)[i];
 }
 
 cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,
@@ -748,6 +1083,31 @@ cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Ta
                            int32_t* work, cudaStream_t s) {
     k_control<<<1, CTL_THREADS, 0, s>>>(g, st, qa, qb, tasks, part, err, trace, loop, use_loop, work);
     return cudaGetLastError();
+}
+
+// The dynamic shared-memory limit is a per-function attribute shared by all
+// contexts: only ever raise it.
+cudaError_t eval_smem_setup(const Geom& g) {
+    static bool carveout = false;
+    if (!carveout) {
+        // One shared-memory carveout for every kernel of the library, so that
+        // consecutive launches never wait for an L1 / shared reconfiguration.
+        const void* fns[] = {(const void*)k_eval, (const void*)k_control, (const void*)k_init,
+                             (const void*)k_keys, (const void*)k_row_hist, (const void*)k_row_scan,
+                             (const void*)k_row_scatter};
+        for (const void* f : fns) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
+        }
+        carveout = true;
+    }
+    static int current = 0;
+    int bytes = g.band_rows * tile_pitch(g) * (int)sizeof(uint32_t);
+    if (bytes <= current) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) current = bytes;
+    return e;
 }
 
 }  // namespace dd

@@ -12,14 +12,15 @@
 namespace {
 
 constexpr int64_t NA_MAX_EVENTS = DD_NOALLOC_MAX_EVENTS;
-constexpr int NA_MAX_ROWS = 4096;
+constexpr int NA_MAX_ROWS = 4096;   // sort bins: time buckets x rows
 constexpr int NA_MAX_TASKS = 64;     // hypotheses per kernel launch (calls are chunked)
 constexpr int NA_MAX_TILES = 1024;   // row bands of one frame (at most 683 for 4096 x 4096)
 
 // Byte offsets of the sub-buffers inside the static array (each 256-aligned).
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t OFF_EV = 0;
-constexpr size_t OFF_ROW_COUNT = align256(OFF_EV + sizeof(dd::Ev) * NA_MAX_EVENTS);
+constexpr size_t OFF_RCP = align256(OFF_EV + sizeof(dd::Ev) * NA_MAX_EVENTS);
+constexpr size_t OFF_ROW_COUNT = align256(OFF_RCP + sizeof(float2) * NA_MAX_EVENTS);
 constexpr size_t OFF_ROW_OFF = align256(OFF_ROW_COUNT + sizeof(int32_t) * NA_MAX_ROWS);
 constexpr size_t OFF_CURSOR = align256(OFF_ROW_OFF + sizeof(int32_t) * (NA_MAX_ROWS + 1));
 constexpr size_t OFF_ERR = align256(OFF_CURSOR + sizeof(int32_t) * NA_MAX_ROWS);
@@ -96,11 +97,14 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     if (rows > H) rows = H;
     g.band_rows = rows;
     g.n_tiles = (H + rows - 1) / rows;
+    g.n_tb = dd::time_buckets(H);
+    g.max_splits = 1;
     if (g.n_tiles > NA_MAX_TILES) return DD_ERR_CAPACITY;
     if (dd::eval_smem_setup(g) != cudaSuccess) return DD_ERR_CUDA;
 
     cudaStream_t s = (cudaStream_t)stream;
     dd::Ev* ev_sorted = (dd::Ev*)(base + OFF_EV);
+    float2* rcp = (float2*)(base + OFF_RCP);
     int32_t* row_count = (int32_t*)(base + OFF_ROW_COUNT);
     int32_t* row_off = (int32_t*)(base + OFF_ROW_OFF);
     int32_t* cursor = (int32_t*)(base + OFF_CURSOR);
@@ -114,7 +118,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
 
     // row_count and err are cleared by the ingest before use; every live
     // (task, tile) block overwrites its partial, so nothing else needs zeroing.
-    if (dd::launch_ingest(g, ev->x, ev->y, ev->t, ev->n, ev->t0, ev->tau, ev_sorted, row_count, row_off, cursor,
+    if (dd::launch_ingest(g, ev->x, ev->y, ev->t, ev->n, ev->t0, ev->tau, ev_sorted, rcp, row_count, row_off, cursor,
                           err, s) != cudaSuccess)
         return DD_ERR_CUDA;
     dd::Task h_tasks[NA_MAX_TASKS];
@@ -126,11 +130,11 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
             for (int32_t j = 0; j < m; j++) {
                 h_tasks[j].D_lo = h_tasks[j].D_hi = D[j0 + j];
                 h_tasks[j].kind = dd::TASK_POINT;
-                h_tasks[j].pad = 0;
+                h_tasks[j].splits = 1;
             }
             if (cudaMemcpyAsync(tasks, h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
                 return DD_ERR_CUDA;
-            if (dd::launch_eval(g, ev_sorted, row_off, tasks, nullptr, m, ev->tau, part, nullptr, nullptr, 512, s) !=
+            if (dd::launch_eval(g, ev_sorted, rcp, row_off, tasks, nullptr, m, ev->tau, part, nullptr, nullptr, 512, s) !=
                 cudaSuccess)
                 return DD_ERR_CUDA;
             if (dd::launch_keys(g, tasks, m, part, keys, S, C, F, s) != cudaSuccess) return DD_ERR_CUDA;
