@@ -106,6 +106,14 @@ typedef struct {
     int32_t status;         /* DD_OK                                                */
 } dd_result;
 
+/* Search parameters of one window of dd_solve_batch. */
+typedef struct {
+    float D_lo, D_hi;       /* search range, D_lo < D_hi, both in the domain        */
+    float tol_D;            /* leaf width (>= 0)                                     */
+    int32_t reserved;       /* 0                                                     */
+    double gamma;           /* stopping gap of Algorithm 1, contrast units (>= 0)    */
+} dd_window_params;
+
 /* One expanded interval, in expansion order (dd_solve_trace). */
 typedef struct {
     float D_lo, D_hi, D_c;
@@ -155,6 +163,20 @@ int dd_bound(dd_ctx* ctx, const dd_events* ev, const float* D_lo, const float* D
  * DD_ERR_CUDA. */
 int dd_solve(dd_ctx* ctx, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma,
              dd_result* out);
+
+/* Algorithm 1 for n_windows independent windows at once (all of the
+ * context's frame geometry): every round evaluates the pending intervals of
+ * all windows in one launch and runs one control block per window; each
+ * window keeps its own device-resident queue and incumbent, and a window that
+ * has finished simply stops contributing work.  The rounds run as one CUDA
+ * graph (or host-driven batches with dd_config.host_loop).  windows[w] and
+ * params[w] (host arrays) describe window w; out[w] receives its result,
+ * identical to dd_solve on that window alone with the same pop_k.
+ * Returns DD_OK when every window succeeded; otherwise the first failing
+ * window's status, with each out[w].status set (results of failed windows
+ * are unspecified).  Errors: as dd_solve; DD_ERR_ARG if n_windows < 1. */
+int dd_solve_batch(dd_ctx* ctx, const dd_events* windows, int32_t n_windows, const dd_window_params* params,
+                   dd_result* out);
 
 /* dd_solve that also records up to trace_cap expanded intervals (host
  * array) and their total count in *trace_len. */
@@ -218,7 +240,7 @@ int dd_set_timing(dd_ctx* ctx, int32_t enable);
  * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
  * DD_ERR_CUDA. */
 #define DD_NOALLOC_MAX_EVENTS (1 << 20)
-#define DD_NOALLOC_SCRATCH_BYTES 18403328
+#define DD_NOALLOC_SCRATCH_BYTES 18406400
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
                         int32_t nD, dd_i128* K, void* stream);
 

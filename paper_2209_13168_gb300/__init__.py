@@ -6,7 +6,7 @@ CUDA kernels behind include/dd.h.  There is no CPU fallback: if libdd.so is
 missing or fails to load, every entry point raises.
 
 The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
-dd_solve_trace, dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing,
+dd_solve_trace, dd_solve_batch, dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing,
 dd_destroy, dd_strerror); ``Context`` wraps
 them for numpy arrays (host events) and torch CUDA tensors (device events).
 """
@@ -64,6 +64,11 @@ class dd_result(ctypes.Structure):
         return d
 
 
+class dd_window_params(ctypes.Structure):
+    _fields_ = [("D_lo", ctypes.c_float), ("D_hi", ctypes.c_float), ("tol_D", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double)]
+
+
 class dd_node_rec(ctypes.Structure):
     _fields_ = [("D_lo", ctypes.c_float), ("D_hi", ctypes.c_float), ("D_c", ctypes.c_float),
                 ("leaf", ctypes.c_int32), ("Kbar", dd_i128), ("K_c", dd_i128)]
@@ -92,6 +97,7 @@ SIGNATURES = {
                                 _P(dd_result)]),
     "dd_solve_trace": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_double, _P(dd_result), _VP, ctypes.c_int64, _P(ctypes.c_int64)]),
+    "dd_solve_batch": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, _P(dd_window_params), _P(dd_result)]),
     "dd_get_stats": (ctypes.c_int, [_VP, _P(dd_stats)]),
     "dd_reset_stats": (ctypes.c_int, [_VP]),
     "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -228,6 +234,21 @@ def dd_solve(h, ev, D_lo, D_hi, tol_D, gamma):
     return r.as_dict()
 
 
+def dd_solve_batch(h, evs, params):
+    """evs: list of Events; params: list of (D_lo, D_hi, tol_D, gamma).
+    Returns (status, [result dicts]) when the windows ran (each result has its
+    own status); raises when the call itself failed."""
+    n = len(evs)
+    E = (dd_events * n)(*[e.c for e in evs])
+    P = (dd_window_params * n)(*[dd_window_params(a, b, t, 0, g) for (a, b, t, g) in params])
+    R = (dd_result * n)()
+    rc = load().dd_solve_batch(h, E, n, P, R)
+    res = [R[i].as_dict() for i in range(n)]
+    if rc != DD_OK and all(r["status"] == DD_OK for r in res):
+        raise DDError(rc, "dd_solve_batch")      # the call itself failed
+    return rc, res
+
+
 def dd_solve_trace(h, ev, D_lo, D_hi, tol_D, gamma, trace_cap):
     r = dd_result()
     tr = (dd_node_rec * max(trace_cap, 1))()
@@ -296,6 +317,12 @@ class Context:
     def bound(self, ev, D_lo, D_hi, want_iwe=False):
         K, S, N, img = dd_bound(self.h, ev, D_lo, D_hi, want_iwe=want_iwe, M=self.M)
         return K, S, N, (img.reshape(-1, self.H, self.W) if want_iwe else None)
+
+    def solve_batch(self, evs, params=None):
+        """Solve several windows at once; params defaults to [-1, 1], 1e-4, 0."""
+        if params is None:
+            params = [(-1.0, 1.0, 1e-4, 0.0)] * len(evs)
+        return dd_solve_batch(self.h, evs, params)
 
     def solve(self, ev, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, trace_cap=0):
         if trace_cap:

@@ -16,34 +16,49 @@ struct dd_ctx {
     dd::Geom g{};
     dd_config cfg{};
     int threads = 512;
-    int max_tasks = 0;
+    int max_tasks = 0;            // task slots per window
+    int eval_blocks = 0;          // resident blocks of the evaluation grid
     cudaStream_t own = nullptr, stream = nullptr;
 
+    // events: sorted and reciprocals for all windows of a call
     dd::Ev* ev = nullptr;
+    float2* rcp = nullptr;
     int64_t ev_cap = 0;
-    float2* rcp = nullptr;        // per sorted event: 1/(x - FOE_x), 1/(y - FOE_y)
-    int64_t rcp_cap = 0;
-    int16_t *in_x = nullptr, *in_y = nullptr;
+    int16_t *in_x = nullptr, *in_y = nullptr;   // staging of host-array inputs
     float* in_t = nullptr;
     int64_t in_cap = 0;
-    int32_t *row_count = nullptr, *row_off = nullptr, *cursor = nullptr, *err = nullptr;
-    int32_t* work = nullptr;      // IWE unit counter of the persistent evaluation grid
-    uint32_t* macc = nullptr;     // merge buffers of split IWE items (zero between uses)
-    int32_t* mdone = nullptr;
-    unsigned long long* mfull = nullptr;
-    int eval_blocks = 0;          // resident blocks of that grid
 
+    // per-window buffers, sized for win_cap windows
+    int win_cap = 0;
+    int32_t *row_count = nullptr, *row_off = nullptr, *cursor = nullptr, *err = nullptr;
+    dd::WinIn* wins = nullptr;
+    dd::WinParams* params = nullptr;
+    dd::SolveState* st = nullptr;
+    dd::Node* queues = nullptr;   // per window: two buffers of queue_capacity nodes
     dd::Task* tasks = nullptr;
     dd::Partial* part = nullptr;
+    dd::Job* jobs = nullptr;      // two lists of job_stride jobs
+    int job_stride = 0;
+    int32_t* chunk_win = nullptr;
+    int64_t chunk_cap = 0;
+    dd::Sched* sch = nullptr;
+
+    // single-window extras
+    uint32_t* macc = nullptr;     // merge buffers of split jobs (zero between uses)
+    int32_t* mdone = nullptr;
+    unsigned long long* mfull = nullptr;
     i128* keys = nullptr;
     unsigned long long *S = nullptr, *C = nullptr, *F = nullptr;
     uint32_t* iwe = nullptr;
     size_t iwe_cap = 0;
-
-    dd::SolveState* st = nullptr;
-    dd::Node* queue = nullptr;   // two buffers of queue_capacity nodes
     dd::TraceRec* trace = nullptr;
     int64_t trace_cap = 0;
+
+    // the rounds of a solve as one CUDA graph (a conditional while loop)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_nw = 0;
+    const void* g_key[3] = {nullptr, nullptr, nullptr};
 
     // telemetry (dd_stats) and optional per-launch timing of the IWE kernel
     dd_stats stats{};
@@ -51,16 +66,15 @@ struct dd_ctx {
     std::vector<cudaEvent_t> t_ev;
     size_t t_used = 0;
 
-    // the rounds of a solve as one CUDA graph (a conditional while loop)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    const void* g_ev = nullptr;
-    const void* g_trace = nullptr;
-
     // pinned host staging
     dd::SolveState* h_st = nullptr;
     dd::Task* h_tasks = nullptr;
-    int32_t* h_flag = nullptr;
+    dd::Job* h_jobs = nullptr;
+    dd::Sched* h_sch = nullptr;
+    dd::WinIn* h_wins = nullptr;
+    dd::WinParams* h_params = nullptr;
+    int32_t* h_chunks = nullptr;
+    int32_t* h_err = nullptr;
 };
 
 namespace {
@@ -82,77 +96,25 @@ bool d_ok(float D, float tau) {
     return dt <= 0.75 && dt >= -64.0;
 }
 
-// Host check of a window's arguments (events are checked on the host when
-// they are host arrays, and by the ingest kernel when they are device arrays).
-int check_events(const dd_ctx* c, const dd_events* ev) {
+// Host checks of a window descriptor.  Event contents (coordinates in the
+// frame, times in the window) are checked by the ingest kernels, which flag
+// the window; the call then fails with DD_ERR_ARG.
+int check_events(const dd_events* ev) {
     if (!ev || ev->n < 0 || ev->n > INT32_MAX / 2) return DD_ERR_ARG;
     if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
     if (ev->n > 0 && (!ev->x || !ev->y || !ev->t)) return DD_ERR_ARG;
-    if (!ev->device_ptrs) {
-        for (int64_t i = 0; i < ev->n; i++) {
-            float tr = ev->t[i] - ev->t0;
-            if (!std::isfinite(ev->t[i]) || !(tr >= 0.0f) || !(tr <= ev->tau)) return DD_ERR_ARG;
-            if (ev->x[i] < 0 || ev->x[i] >= c->g.W || ev->y[i] < 0 || ev->y[i] >= c->g.H) return DD_ERR_ARG;
-        }
-    }
     return DD_OK;
 }
 
 template <class T>
-int grow(T** p, int64_t* cap, int64_t need) {
-    if (need <= *cap) return DD_OK;
-    int64_t nc = need < 1024 ? 1024 : need + need / 4;
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    DD_TRY(cudaMalloc((void**)p, sizeof(T) * (size_t)nc));
-    *cap = nc;
-    return DD_OK;
+void release(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
 }
-
-cudaError_t copy(dd_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);
-
-// Upload (host arrays) or alias (device arrays) the events, then sort them by
-// row into ctx->ev.  Sets ctx->err on malformed device events.
-int ingest(dd_ctx* c, const dd_events* ev) {
-    int rc = grow(&c->ev, &c->ev_cap, ev->n);
-    if (rc) return rc;
-    rc = grow(&c->rcp, &c->rcp_cap, ev->n);
-    if (rc) return rc;
-    const int16_t *x = ev->x, *y = ev->y;
-    const float* t = ev->t;
-    if (!ev->device_ptrs && ev->n > 0) {
-        if (ev->n > c->in_cap) {
-            cudaFree(c->in_x);
-            cudaFree(c->in_y);
-            cudaFree(c->in_t);
-            c->in_x = c->in_y = nullptr;
-            c->in_t = nullptr;
-            c->in_cap = 0;
-            int64_t nc = ev->n + ev->n / 4;
-            DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
-            DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
-            DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
-            c->in_cap = nc;
-        }
-        DD_TRY(copy(c, c->in_x, ev->x, sizeof(int16_t) * ev->n, cudaMemcpyHostToDevice));
-        DD_TRY(copy(c, c->in_y, ev->y, sizeof(int16_t) * ev->n, cudaMemcpyHostToDevice));
-        DD_TRY(copy(c, c->in_t, ev->t, sizeof(float) * ev->n, cudaMemcpyHostToDevice));
-        x = c->in_x;
-        y = c->in_y;
-        t = c->in_t;
-    }
-    DD_TRY(dd::launch_ingest(c->g, x, y, t, ev->n, ev->t0, ev->tau, c->ev, c->rcp, c->row_count, c->row_off, c->cursor,
-                             c->err, c->stream));
-    c->stats.kernel_launches += ev->n > 0 ? 3 : 1;
-    return DD_OK;
-}
-
-dd_i128 from_i128(i128 v) {
-    dd_i128 r;
-    r.lo = (uint64_t)(unsigned __int128)v;
-    r.hi = (int64_t)(uint64_t)((unsigned __int128)v >> 64);
-    return r;
+template <class T>
+void release_host(T*& p) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
 }
 
 cudaError_t copy(dd_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
@@ -185,15 +147,39 @@ cudaError_t record(dd_ctx* c) {
     return cudaEventRecord(c->t_ev[c->t_used++], c->stream);
 }
 
-cudaError_t eval(dd_ctx* c, const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, uint32_t* iwe,
-                 const dd::SolveState* st) {
+void drop_graph(dd_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->g_nw = 0;
+}
+
+dd::EvalArgs eval_args(dd_ctx* c, uint32_t* iwe_out, bool single) {
+    dd::EvalArgs a;
+    a.ev = c->ev;
+    a.rcp = c->rcp;
+    a.row_off = c->row_off;
+    a.wins = c->wins;
+    a.tasks = c->tasks;
+    a.task_stride = c->max_tasks;
+    a.jobs = c->jobs;
+    a.job_stride = c->job_stride;
+    a.sch = c->sch;
+    a.part = c->part;
+    a.iwe_out = iwe_out;
+    a.mg.acc = single ? c->macc : nullptr;
+    a.mg.done = single ? c->mdone : nullptr;
+    a.mg.full = single ? c->mfull : nullptr;
+    return a;
+}
+
+cudaError_t eval(dd_ctx* c, uint32_t* iwe, bool single) {
     if (c->timing) {
         cudaError_t e = record(c);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = dd::launch_eval(c->g, c->ev, c->rcp, c->row_off, c->tasks, n_tasks_dev, n_tasks_max, tau, c->part, iwe,
-                                    st, c->threads, c->stream, c->work, c->eval_blocks, c->macc, c->mdone,
-                                    c->mfull);
+    cudaError_t e = dd::launch_eval(c->g, eval_args(c, iwe, single), c->threads, c->eval_blocks, c->stream);
     if (e != cudaSuccess) return e;
     c->stats.kernel_launches++;
     c->stats.eval_launches++;
@@ -201,34 +187,183 @@ cudaError_t eval(dd_ctx* c, const int32_t* n_tasks_dev, int32_t n_tasks_max, flo
     return cudaSuccess;
 }
 
-// Evaluate n tasks (point or bound) and copy keys/sums/images to the host.
+// Per-window buffers for at least nw windows.
+int ensure_windows(dd_ctx* c, int nw) {
+    if (nw <= c->win_cap) return DD_OK;
+    drop_graph(c);
+    const int cap = nw < 8 ? 8 : nw + nw / 2;
+    const int bins = c->g.n_tb * c->g.H;
+    release(c->row_count);
+    release(c->row_off);
+    release(c->cursor);
+    release(c->err);
+    release(c->wins);
+    release(c->params);
+    release(c->st);
+    release(c->queues);
+    release(c->tasks);
+    release(c->part);
+    release(c->jobs);
+    release_host(c->h_st);
+    release_host(c->h_wins);
+    release_host(c->h_params);
+    release_host(c->h_err);
+    c->win_cap = 0;
+    const int js = cap * c->max_tasks > c->max_tasks * c->g.max_splits ? cap * c->max_tasks
+                                                                        : c->max_tasks * c->g.max_splits;
+    int rc = DD_OK;
+    auto A = [&](void** p, size_t bytes) {
+        if (rc == DD_OK && cudaMalloc(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
+    };
+    auto AH = [&](void** p, size_t bytes) {
+        if (rc == DD_OK && cudaMallocHost(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
+    };
+    A((void**)&c->row_count, sizeof(int32_t) * (size_t)bins * cap);
+    A((void**)&c->row_off, sizeof(int32_t) * (size_t)(bins + 1) * cap);
+    A((void**)&c->cursor, sizeof(int32_t) * (size_t)bins * cap);
+    A((void**)&c->err, sizeof(int32_t) * (size_t)cap);
+    A((void**)&c->wins, sizeof(dd::WinIn) * (size_t)cap);
+    A((void**)&c->params, sizeof(dd::WinParams) * (size_t)cap);
+    A((void**)&c->st, sizeof(dd::SolveState) * (size_t)cap);
+    A((void**)&c->queues, sizeof(dd::Node) * 2 * (size_t)c->cfg.queue_capacity * cap);
+    A((void**)&c->tasks, sizeof(dd::Task) * (size_t)c->max_tasks * cap);
+    A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles * cap);
+    A((void**)&c->jobs, sizeof(dd::Job) * 2 * (size_t)js);
+    AH((void**)&c->h_st, sizeof(dd::SolveState) * (size_t)cap);
+    AH((void**)&c->h_wins, sizeof(dd::WinIn) * (size_t)cap);
+    AH((void**)&c->h_params, sizeof(dd::WinParams) * (size_t)cap);
+    AH((void**)&c->h_err, sizeof(int32_t) * (size_t)cap);
+    if (rc) return rc;
+    c->job_stride = js;
+    c->win_cap = cap;
+    return DD_OK;
+}
+
+// Upload (host arrays) or alias (device arrays) the events of nw windows,
+// then sort each window's events by (time bucket, row).  Sets err[w] on
+// malformed events of window w.
+int ingest(dd_ctx* c, const dd_events* evs, int nw) {
+    int rc = ensure_windows(c, nw);
+    if (rc) return rc;
+    int64_t total = 0, host_total = 0, chunks = 0;
+    for (int w = 0; w < nw; w++) {
+        total += evs[w].n;
+        if (!evs[w].device_ptrs) host_total += evs[w].n;
+        chunks += (evs[w].n + dd::CHUNK - 1) / dd::CHUNK;
+    }
+    if (total > c->ev_cap) {
+        drop_graph(c);
+        release(c->ev);
+        release(c->rcp);
+        c->ev_cap = 0;
+        const int64_t nc = total < 1024 ? 1024 : total + total / 4;
+        DD_TRY(cudaMalloc((void**)&c->ev, sizeof(dd::Ev) * nc));
+        DD_TRY(cudaMalloc((void**)&c->rcp, sizeof(float2) * nc));
+        c->ev_cap = nc;
+    }
+    if (host_total > c->in_cap) {
+        release(c->in_x);
+        release(c->in_y);
+        release(c->in_t);
+        c->in_cap = 0;
+        const int64_t nc = host_total + host_total / 4;
+        DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
+        DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
+        DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
+        c->in_cap = nc;
+    }
+    if (chunks > c->chunk_cap) {
+        release(c->chunk_win);
+        release_host(c->h_chunks);
+        c->chunk_cap = 0;
+        const int64_t nc = chunks < 256 ? 256 : chunks + chunks / 2;
+        DD_TRY(cudaMalloc((void**)&c->chunk_win, sizeof(int32_t) * nc));
+        DD_TRY(cudaMallocHost((void**)&c->h_chunks, sizeof(int32_t) * nc));
+        c->chunk_cap = nc;
+    }
+    int64_t off = 0, hoff = 0;
+    int32_t ch = 0;
+    for (int w = 0; w < nw; w++) {
+        const dd_events& e = evs[w];
+        dd::WinIn& wi = c->h_wins[w];
+        wi.x = e.x;
+        wi.y = e.y;
+        wi.t = e.t;
+        if (!e.device_ptrs && e.n > 0) {
+            DD_TRY(copy(c, c->in_x + hoff, e.x, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice));
+            DD_TRY(copy(c, c->in_y + hoff, e.y, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice));
+            DD_TRY(copy(c, c->in_t + hoff, e.t, sizeof(float) * e.n, cudaMemcpyHostToDevice));
+            wi.x = c->in_x + hoff;
+            wi.y = c->in_y + hoff;
+            wi.t = c->in_t + hoff;
+            hoff += e.n;
+        }
+        wi.n = e.n;
+        wi.ev_off = off;
+        wi.t0 = e.t0;
+        wi.tau = e.tau;
+        wi.chunk0 = ch;
+        wi.pad = 0;
+        const int32_t nch = (int32_t)((e.n + dd::CHUNK - 1) / dd::CHUNK);
+        for (int32_t k = 0; k < nch; k++) c->h_chunks[ch + k] = w;
+        ch += nch;
+        off += e.n;
+    }
+    DD_TRY(copy(c, c->wins, c->h_wins, sizeof(dd::WinIn) * nw, cudaMemcpyHostToDevice));
+    if (ch) DD_TRY(copy(c, c->chunk_win, c->h_chunks, sizeof(int32_t) * ch, cudaMemcpyHostToDevice));
+    DD_TRY(dd::launch_ingest(c->g, c->wins, nw, c->chunk_win, ch, c->ev, c->rcp, c->row_count, c->row_off,
+                             c->cursor, c->err, c->stream));
+    c->stats.kernel_launches += ch ? 3 : 1;
+    return DD_OK;
+}
+
+dd_i128 from_i128(i128 v) {
+    dd_i128 r;
+    r.lo = (uint64_t)(unsigned __int128)v;
+    r.hi = (int64_t)(uint64_t)((unsigned __int128)v >> 64);
+    return r;
+}
+
+// Evaluate n tasks (point or bound) of one window and copy keys, sums and
+// images to the host.
 int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float* A, const float* B, dd_i128* K,
                uint64_t* S, int64_t* N, uint32_t* iwe) {
     const int64_t M = (int64_t)c->g.W * c->g.H;
     for (int32_t j0 = 0; j0 < n; j0 += c->max_tasks) {
         const int32_t m = n - j0 < c->max_tasks ? n - j0 : c->max_tasks;
+        int32_t nj = 0;
         for (int32_t j = 0; j < m; j++) {
-            c->h_tasks[j].D_lo = A[j0 + j];
-            c->h_tasks[j].D_hi = B[j0 + j];
-            c->h_tasks[j].kind = kind;
-            c->h_tasks[j].splits =
-                kind == dd::TASK_BOUND ? dd::bound_splits(c->g, A[j0 + j], B[j0 + j], ev->tau) : 1;
+            dd::Task& t = c->h_tasks[j];
+            t.D_lo = A[j0 + j];
+            t.D_hi = B[j0 + j];
+            t.kind = kind;
+            t.splits = kind == dd::TASK_BOUND ? dd::bound_splits(c->g, t.D_lo, t.D_hi, ev->tau) : 1;
         }
+        for (int32_t j = m - 1; j >= 0; j--)              // heavier tasks first
+            for (int32_t s = 0; s < c->h_tasks[j].splits; s++) {
+                dd::Job& jb = c->h_jobs[nj++];
+                jb.win = 0;
+                jb.task = j;
+                jb.split = s;
+                jb.splits = c->h_tasks[j].splits;
+            }
+        std::memset(c->h_sch, 0, sizeof(dd::Sched));
+        c->h_sch->n_jobs[0] = nj;
         DD_TRY(copy(c, c->tasks, c->h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice));
+        DD_TRY(copy(c, c->jobs, c->h_jobs, sizeof(dd::Job) * nj, cudaMemcpyHostToDevice));
+        DD_TRY(copy(c, c->sch, c->h_sch, sizeof(dd::Sched), cudaMemcpyHostToDevice));
         uint32_t* iw = nullptr;
         if (iwe) {
             size_t need = (size_t)m * M;
             if (need > c->iwe_cap) {
-                cudaFree(c->iwe);
-                c->iwe = nullptr;
+                release(c->iwe);
                 c->iwe_cap = 0;
                 DD_TRY(cudaMalloc((void**)&c->iwe, need * sizeof(uint32_t)));
                 c->iwe_cap = need;
             }
             iw = c->iwe;
         }
-        DD_TRY(cudaMemsetAsync(c->work, 0, sizeof(int32_t), c->stream));
-        DD_TRY(eval(c, nullptr, m, ev->tau, iw, nullptr));
+        DD_TRY(eval(c, iw, true));
         DD_TRY(dd::launch_keys(c->g, c->tasks, m, c->part, c->keys, c->S, c->C, c->F, c->stream));
         c->stats.kernel_launches++;
         std::vector<i128> hk(m);
@@ -237,11 +372,11 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
         DD_TRY(copy(c, hs.data(), c->S, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost));
         DD_TRY(copy(c, hc.data(), c->C, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost));
         DD_TRY(copy(c, hf.data(), c->F, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost));
-        DD_TRY(copy(c, c->h_flag, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        DD_TRY(copy(c, c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
         if (iwe)
             DD_TRY(copy(c, iwe + (size_t)j0 * M, c->iwe, sizeof(uint32_t) * (size_t)m * M, cudaMemcpyDeviceToHost));
         DD_TRY(sync(c));
-        if (*c->h_flag) return DD_ERR_ARG;
+        if (c->h_err[0]) return DD_ERR_ARG;
         for (int32_t j = 0; j < m; j++) {
             K[j0 + j] = from_i128(hk[j]);
             if (S) S[j0 + j] = hs[j];
@@ -251,18 +386,12 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
     return DD_OK;
 }
 
-void drop_graph(dd_ctx* c) {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->gexec = nullptr;
-    c->graph = nullptr;
-}
-
-// Build the solve graph: a while node whose body is one round (IWE
-// evaluation, then the control kernel, which clears the loop condition when
-// the search is over).  Kernel arguments are baked in, so the graph is
-// rebuilt when a buffer it points to is reallocated.
-int build_graph(dd_ctx* c, dd::TraceRec* trace) {
+// Build the solve graph for nw windows: a while node whose body is one round
+// (IWE evaluation, then one control block per window; the last control block
+// clears the loop condition when no window is still searching).  Kernel
+// arguments are baked in, so the graph is rebuilt when a buffer it points to
+// is reallocated or the window count changes.
+int build_graph(dd_ctx* c, int nw, dd::TraceRec* trace) {
     drop_graph(c);
     DD_TRY(cudaGraphCreate(&c->graph, 0));
     cudaGraphConditionalHandle h;
@@ -275,11 +404,9 @@ int build_graph(dd_ctx* c, dd::TraceRec* trace) {
     DD_TRY(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
     DD_TRY(cudaStreamBeginCaptureToGraph(c->own, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = dd::launch_eval(c->g, c->ev, c->rcp, c->row_off, c->tasks, &c->st->n_tasks, c->max_tasks, 0.0f,
-                                     c->part, nullptr, c->st, c->threads, c->own, c->work, c->eval_blocks, c->macc,
-                                     c->mdone, c->mfull);
-    cudaError_t e2 = dd::launch_control(c->g, c->st, c->queue, c->queue + c->cfg.queue_capacity, c->tasks,
-                                        c->part, c->err, trace, h, 1, c->work, c->own);
+    cudaError_t e1 = dd::launch_eval(c->g, eval_args(c, nullptr, nw == 1), c->threads, c->eval_blocks, c->own);
+    cudaError_t e2 = dd::launch_control(c->g, nw, c->st, c->queues, c->tasks, c->max_tasks, c->part, c->err, trace,
+                                        c->jobs, c->job_stride, c->sch, h, 1, c->own);
     cudaGraph_t captured = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(c->own, &captured);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -290,39 +417,77 @@ int build_graph(dd_ctx* c, dd::TraceRec* trace) {
         drop_graph(c);
         return DD_ERR_CUDA;
     }
-    c->g_ev = c->ev;
-    c->g_trace = trace;
+    c->g_nw = nw;
+    c->g_key[0] = c->ev;
+    c->g_key[1] = trace;
+    c->g_key[2] = c->st;
     return DD_OK;
 }
 
-int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma, dd_result* out,
+void fill_result(const dd::SolveState& s, const dd_events& ev, int64_t M, dd_result* out) {
+    // Sec. 4.1 retrieval and reporting (double precision, from the exact keys).
+    dd_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.D_star = s.D_hat;
+    r.D_end = (float)((double)s.D_hat / (1.0 - (double)s.D_hat * (double)ev.tau));
+    r.K_hat = from_i128(s.K_hat);
+    r.gap_K = from_i128(s.stop_kb);
+    r.contrast = (double)s.K_hat / ((double)M * (double)M);
+    r.bound_gap = (double)s.stop_kb / ((double)M * (double)M);
+    r.nodes_expanded = s.nodes_expanded;
+    r.point_evals = s.point_evals;
+    r.bound_evals = s.bound_evals;
+    r.event_warps = ev.n * (s.point_evals + s.bound_evals);
+    r.cell_increments = s.cells;
+    r.bound_increments = s.bcells;
+    r.rounds = s.rounds;
+    r.max_queue = s.max_queue;
+    r.status = s.status;
+    *out = r;
+}
+
+int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* prm, dd_result* out,
                dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
-    if (!c || !out) return DD_ERR_ARG;
-    int rc = check_events(c, ev);
-    if (rc) return rc;
-    if (!d_ok(D_lo, ev->tau) || !d_ok(D_hi, ev->tau) || !(D_lo < D_hi)) return DD_ERR_ARG;
-    if (!std::isfinite(tol_D) || !(tol_D >= 0.0f) || !std::isfinite(gamma) || !(gamma >= 0.0)) return DD_ERR_ARG;
-    if (trace_cap < 0 || (trace_cap > 0 && !trace)) return DD_ERR_ARG;
+    if (!c || !out || !evs || !prm || nw < 1) return DD_ERR_ARG;
+    for (int w = 0; w < nw; w++) {
+        int rc = check_events(&evs[w]);
+        if (rc) return rc;
+        const dd_window_params& p = prm[w];
+        if (!d_ok(p.D_lo, evs[w].tau) || !d_ok(p.D_hi, evs[w].tau) || !(p.D_lo < p.D_hi)) return DD_ERR_ARG;
+        if (!std::isfinite(p.tol_D) || !(p.tol_D >= 0.0f) || !std::isfinite(p.gamma) || !(p.gamma >= 0.0))
+            return DD_ERR_ARG;
+    }
+    if (trace_cap < 0 || (trace_cap > 0 && (!trace || nw != 1))) return DD_ERR_ARG;
     if (trace_cap > c->trace_cap) {
-        cudaFree(c->trace);
-        c->trace = nullptr;
+        release(c->trace);
         c->trace_cap = 0;
         DD_TRY(cudaMalloc((void**)&c->trace, sizeof(dd::TraceRec) * trace_cap));
         c->trace_cap = trace_cap;
     }
-    rc = ingest(c, ev);
+    int rc = ingest(c, evs, nw);
     if (rc) return rc;
     const int64_t M = (int64_t)c->g.W * c->g.H;
-    const i128 gamma_K = (i128)std::floor(gamma * (double)M * (double)M);
-    DD_TRY(dd::launch_init(c->g, c->st, c->tasks, M, D_lo, D_hi, tol_D, ev->tau, gamma_K, c->cfg.pop_k,
-                           c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap, c->work, c->stream));
+    for (int w = 0; w < nw; w++) {
+        dd::WinParams& q = c->h_params[w];
+        q.gamma_K = (i128)std::floor(prm[w].gamma * (double)M * (double)M);
+        q.D_lo = prm[w].D_lo;
+        q.D_hi = prm[w].D_hi;
+        q.tol = prm[w].tol_D;
+        q.pad = 0.0f;
+    }
+    DD_TRY(copy(c, c->params, c->h_params, sizeof(dd::WinParams) * nw, cudaMemcpyHostToDevice));
+    DD_TRY(cudaMemsetAsync(c->sch, 0, sizeof(dd::Sched), c->stream));
+    DD_TRY(dd::launch_init(c->g, nw, c->st, c->tasks, c->max_tasks, c->wins, c->params, c->jobs, c->job_stride,
+                           c->sch, c->cfg.pop_k, c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap,
+                           c->stream));
     c->stats.kernel_launches++;
     dd::TraceRec* tr_dev = trace_cap > 0 ? c->trace : nullptr;
     const bool graph = !c->cfg.host_loop && !c->timing;
     if (graph) {
         // One graph launch runs every round on the device.
-        if (!c->gexec || c->g_ev != (const void*)c->ev || c->g_trace != (const void*)tr_dev) {
-            rc = build_graph(c, tr_dev);
+        if (!c->gexec || c->g_nw != nw || c->g_key[0] != (const void*)c->ev || c->g_key[1] != (const void*)tr_dev ||
+            c->g_key[2] != (const void*)c->st) {
+            rc = build_graph(c, nw, tr_dev);
             if (rc) return rc;
         }
         DD_TRY(cudaGraphLaunch(c->gexec, c->stream));
@@ -331,48 +496,33 @@ int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol
         int batch = 2;
         for (;;) {
             for (int b = 0; b < batch; b++) {
-                DD_TRY(eval(c, &c->st->n_tasks, c->max_tasks, ev->tau, nullptr, c->st));
-                DD_TRY(dd::launch_control(c->g, c->st, c->queue, c->queue + c->cfg.queue_capacity, c->tasks,
-                                          c->part, c->err, tr_dev, 0, 0, c->work, c->stream));
+                DD_TRY(eval(c, nullptr, nw == 1));
+                DD_TRY(dd::launch_control(c->g, nw, c->st, c->queues, c->tasks, c->max_tasks, c->part, c->err,
+                                          tr_dev, c->jobs, c->job_stride, c->sch, 0, 0, c->stream));
                 c->stats.kernel_launches++;
             }
-            DD_TRY(copy(c, c->h_flag, &c->st->phase, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            DD_TRY(copy(c, c->h_sch, c->sch, sizeof(dd::Sched), cudaMemcpyDeviceToHost));
             DD_TRY(sync(c));
-            if (*c->h_flag == dd::PH_DONE) break;
+            if (c->h_sch->running == 0) break;
             if (batch < 64) batch *= 2;
         }
     }
-    DD_TRY(copy(c, c->h_st, c->st, sizeof(dd::SolveState), cudaMemcpyDeviceToHost));
+    DD_TRY(copy(c, c->h_st, c->st, sizeof(dd::SolveState) * nw, cudaMemcpyDeviceToHost));
+    DD_TRY(copy(c, c->h_sch, c->sch, sizeof(dd::Sched), cudaMemcpyDeviceToHost));
     std::vector<dd::TraceRec> tr((size_t)trace_cap);
     if (trace_cap > 0) DD_TRY(copy(c, tr.data(), c->trace, sizeof(dd::TraceRec) * trace_cap, cudaMemcpyDeviceToHost));
     DD_TRY(sync(c));
-    const dd::SolveState& s = *c->h_st;
-    if (graph) {                                  // the loop ran rounds + 1 times
-        c->stats.kernel_launches += 2 * (s.rounds + 1);
-        c->stats.eval_launches += s.rounds + 1;
+    if (graph) {                                  // every round ran one evaluation and one control launch
+        c->stats.kernel_launches += 2 * (int64_t)c->h_sch->round;
+        c->stats.eval_launches += c->h_sch->round;
     }
-    if (s.status != DD_OK) return s.status;
-    // Sec. 4.1 retrieval and reporting (double precision, from the exact keys).
-    dd_result r;
-    std::memset(&r, 0, sizeof(r));
-    r.D_star = s.D_hat;
-    r.D_end = (float)((double)s.D_hat / (1.0 - (double)s.D_hat * (double)ev->tau));
-    r.K_hat = from_i128(s.K_hat);
-    r.gap_K = from_i128(s.stop_kb);
-    r.contrast = (double)s.K_hat / ((double)M * (double)M);
-    r.bound_gap = (double)s.stop_kb / ((double)M * (double)M);
-    r.nodes_expanded = s.nodes_expanded;
-    r.point_evals = s.point_evals;
-    r.bound_evals = s.bound_evals;
-    r.event_warps = ev->n * (s.point_evals + s.bound_evals);
-    r.cell_increments = s.cells;
-    r.bound_increments = s.bcells;
-    r.rounds = s.rounds;
-    r.max_queue = s.max_queue;
-    r.status = DD_OK;
-    *out = r;
-    if (trace_len) *trace_len = s.trace_len;
-    for (int64_t i = 0; i < trace_cap && i < s.trace_len; i++) {
+    int status = DD_OK;
+    for (int w = 0; w < nw; w++)
+        if (c->h_st[w].status != DD_OK && status == DD_OK) status = c->h_st[w].status;
+    if (nw == 1 && status != DD_OK) return status;
+    for (int w = 0; w < nw; w++) fill_result(c->h_st[w], evs[w], M, &out[w]);
+    if (trace_len) *trace_len = c->h_st[0].trace_len;
+    for (int64_t i = 0; i < trace_cap && i < c->h_st[0].trace_len; i++) {
         trace[i].D_lo = tr[i].D_lo;
         trace[i].D_hi = tr[i].D_hi;
         trace[i].D_c = tr[i].D_c;
@@ -380,7 +530,7 @@ int solve_impl(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol
         trace[i].Kbar = from_i128(tr[i].Kbar);
         trace[i].K_c = from_i128(tr[i].K_c);
     }
-    return DD_OK;
+    return status;
 }
 
 }  // namespace
@@ -403,34 +553,43 @@ const char* dd_strerror(int status) {
 
 void dd_destroy(dd_ctx* c) {
     if (!c) return;
-    cudaFree(c->ev);
-    cudaFree(c->rcp);
-    cudaFree(c->in_x);
-    cudaFree(c->in_y);
-    cudaFree(c->in_t);
-    cudaFree(c->row_count);
-    cudaFree(c->row_off);
-    cudaFree(c->cursor);
-    cudaFree(c->err);
-    cudaFree(c->work);
-    cudaFree(c->macc);
-    cudaFree(c->mdone);
-    cudaFree(c->mfull);
-    cudaFree(c->tasks);
-    cudaFree(c->part);
-    cudaFree(c->keys);
-    cudaFree(c->S);
-    cudaFree(c->C);
-    cudaFree(c->F);
-    cudaFree(c->iwe);
-    cudaFree(c->st);
-    cudaFree(c->queue);
-    cudaFree(c->trace);
-    cudaFreeHost(c->h_st);
-    cudaFreeHost(c->h_tasks);
-    cudaFreeHost(c->h_flag);
-    for (cudaEvent_t e : c->t_ev) cudaEventDestroy(e);
     drop_graph(c);
+    release(c->ev);
+    release(c->rcp);
+    release(c->in_x);
+    release(c->in_y);
+    release(c->in_t);
+    release(c->row_count);
+    release(c->row_off);
+    release(c->cursor);
+    release(c->err);
+    release(c->wins);
+    release(c->params);
+    release(c->st);
+    release(c->queues);
+    release(c->tasks);
+    release(c->part);
+    release(c->jobs);
+    release(c->chunk_win);
+    release(c->sch);
+    release(c->macc);
+    release(c->mdone);
+    release(c->mfull);
+    release(c->keys);
+    release(c->S);
+    release(c->C);
+    release(c->F);
+    release(c->iwe);
+    release(c->trace);
+    release_host(c->h_st);
+    release_host(c->h_tasks);
+    release_host(c->h_jobs);
+    release_host(c->h_sch);
+    release_host(c->h_wins);
+    release_host(c->h_params);
+    release_host(c->h_chunks);
+    release_host(c->h_err);
+    for (cudaEvent_t e : c->t_ev) cudaEventDestroy(e);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }
@@ -482,40 +641,36 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
     c->cfg.threads = c->threads;
     c->cfg.band_rows = rows;
+    c->cfg.max_splits = c->g.max_splits;
 
     int rc = DD_OK;
     auto A = [&](void** p, size_t bytes) {
         if (rc == DD_OK && cudaMalloc(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
     };
-    const int bins = c->g.n_tb * H;
-    A((void**)&c->row_count, sizeof(int32_t) * bins);
-    A((void**)&c->row_off, sizeof(int32_t) * (bins + 1));
-    A((void**)&c->cursor, sizeof(int32_t) * bins);
-    A((void**)&c->err, sizeof(int32_t));
-    A((void**)&c->work, sizeof(int32_t));
-    A((void**)&c->macc, sizeof(uint32_t) * (size_t)c->max_tasks * W * H);
+    const size_t M = (size_t)W * H;
+    A((void**)&c->sch, sizeof(dd::Sched));
+    A((void**)&c->macc, sizeof(uint32_t) * (size_t)c->max_tasks * M);
     A((void**)&c->mdone, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles);
     A((void**)&c->mfull, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles);
-    if (rc == DD_OK && (cudaMemset(c->macc, 0, sizeof(uint32_t) * (size_t)c->max_tasks * W * H) != cudaSuccess ||
+    if (rc == DD_OK && (cudaMemset(c->macc, 0, sizeof(uint32_t) * (size_t)c->max_tasks * M) != cudaSuccess ||
                         cudaMemset(c->mdone, 0, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles) != cudaSuccess ||
                         cudaMemset(c->mfull, 0, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles) !=
                             cudaSuccess))
         rc = DD_ERR_CUDA;
-    A((void**)&c->tasks, sizeof(dd::Task) * c->max_tasks);
-    A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles);
     A((void**)&c->keys, sizeof(i128) * c->max_tasks);
     A((void**)&c->S, sizeof(unsigned long long) * c->max_tasks);
     A((void**)&c->C, sizeof(unsigned long long) * c->max_tasks);
     A((void**)&c->F, sizeof(unsigned long long) * c->max_tasks);
-    A((void**)&c->st, sizeof(dd::SolveState));
-    A((void**)&c->queue, sizeof(dd::Node) * 2 * (size_t)k.queue_capacity);
-    if (rc == DD_OK && cudaMallocHost((void**)&c->h_st, sizeof(dd::SolveState)) != cudaSuccess) rc = DD_ERR_OOM;
     if (rc == DD_OK && cudaMallocHost((void**)&c->h_tasks, sizeof(dd::Task) * c->max_tasks) != cudaSuccess)
         rc = DD_ERR_OOM;
-    if (rc == DD_OK && cudaMallocHost((void**)&c->h_flag, sizeof(int32_t)) != cudaSuccess) rc = DD_ERR_OOM;
+    if (rc == DD_OK &&
+        cudaMallocHost((void**)&c->h_jobs, sizeof(dd::Job) * (size_t)c->max_tasks * c->g.max_splits) != cudaSuccess)
+        rc = DD_ERR_OOM;
+    if (rc == DD_OK && cudaMallocHost((void**)&c->h_sch, sizeof(dd::Sched)) != cudaSuccess) rc = DD_ERR_OOM;
     if (rc == DD_OK && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && dd::eval_smem_setup(c->g) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && (c->eval_blocks = dd::eval_resident_blocks(c->g, c->threads)) <= 0) rc = DD_ERR_CUDA;
+    if (rc == DD_OK) rc = ensure_windows(c, 1);
     if (rc != DD_OK) {
         dd_destroy(c);
         return rc;
@@ -529,40 +684,6 @@ int dd_set_stream(dd_ctx* c, void* stream) {
     if (!c) return DD_ERR_ARG;
     c->stream = stream ? (cudaStream_t)stream : c->own;
     return DD_OK;
-}
-
-int dd_contrast(dd_ctx* c, const dd_events* ev, const float* D, int32_t nD, dd_i128* K, uint64_t* S,
-                int64_t* N_in, uint32_t* iwe) {
-    if (!c || nD < 0 || (nD > 0 && (!D || !K))) return DD_ERR_ARG;
-    int rc = check_events(c, ev);
-    if (rc) return rc;
-    for (int32_t j = 0; j < nD; j++)
-        if (!d_ok(D[j], ev->tau)) return DD_ERR_ARG;
-    rc = ingest(c, ev);
-    if (rc) return rc;
-    if (nD == 0) {
-        DD_TRY(copy(c, c->h_flag, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        DD_TRY(sync(c));
-        return *c->h_flag ? DD_ERR_ARG : DD_OK;
-    }
-    return eval_tasks(c, ev, nD, dd::TASK_POINT, D, D, K, S, N_in, iwe);
-}
-
-int dd_bound(dd_ctx* c, const dd_events* ev, const float* D_lo, const float* D_hi, int32_t n, dd_i128* Kbar,
-             uint64_t* Sbar, int64_t* N_full, uint32_t* iwe) {
-    if (!c || n < 0 || (n > 0 && (!D_lo || !D_hi || !Kbar))) return DD_ERR_ARG;
-    int rc = check_events(c, ev);
-    if (rc) return rc;
-    for (int32_t j = 0; j < n; j++)
-        if (!d_ok(D_lo[j], ev->tau) || !d_ok(D_hi[j], ev->tau) || !(D_lo[j] <= D_hi[j])) return DD_ERR_ARG;
-    rc = ingest(c, ev);
-    if (rc) return rc;
-    if (n == 0) {
-        DD_TRY(copy(c, c->h_flag, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        DD_TRY(sync(c));
-        return *c->h_flag ? DD_ERR_ARG : DD_OK;
-    }
-    return eval_tasks(c, ev, n, dd::TASK_BOUND, D_lo, D_hi, Kbar, Sbar, N_full, iwe);
 }
 
 int dd_get_stats(dd_ctx* c, dd_stats* out) {
@@ -583,13 +704,54 @@ int dd_set_timing(dd_ctx* c, int32_t enable) {
     return DD_OK;
 }
 
+int dd_contrast(dd_ctx* c, const dd_events* ev, const float* D, int32_t nD, dd_i128* K, uint64_t* S,
+                int64_t* N_in, uint32_t* iwe) {
+    if (!c || nD < 0 || (nD > 0 && (!D || !K))) return DD_ERR_ARG;
+    int rc = check_events(ev);
+    if (rc) return rc;
+    for (int32_t j = 0; j < nD; j++)
+        if (!d_ok(D[j], ev->tau)) return DD_ERR_ARG;
+    rc = ingest(c, ev, 1);
+    if (rc) return rc;
+    if (nD == 0) {
+        DD_TRY(copy(c, c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        DD_TRY(sync(c));
+        return c->h_err[0] ? DD_ERR_ARG : DD_OK;
+    }
+    return eval_tasks(c, ev, nD, dd::TASK_POINT, D, D, K, S, N_in, iwe);
+}
+
+int dd_bound(dd_ctx* c, const dd_events* ev, const float* D_lo, const float* D_hi, int32_t n, dd_i128* Kbar,
+             uint64_t* Sbar, int64_t* N_full, uint32_t* iwe) {
+    if (!c || n < 0 || (n > 0 && (!D_lo || !D_hi || !Kbar))) return DD_ERR_ARG;
+    int rc = check_events(ev);
+    if (rc) return rc;
+    for (int32_t j = 0; j < n; j++)
+        if (!d_ok(D_lo[j], ev->tau) || !d_ok(D_hi[j], ev->tau) || !(D_lo[j] <= D_hi[j])) return DD_ERR_ARG;
+    rc = ingest(c, ev, 1);
+    if (rc) return rc;
+    if (n == 0) {
+        DD_TRY(copy(c, c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        DD_TRY(sync(c));
+        return c->h_err[0] ? DD_ERR_ARG : DD_OK;
+    }
+    return eval_tasks(c, ev, n, dd::TASK_BOUND, D_lo, D_hi, Kbar, Sbar, N_full, iwe);
+}
+
 int dd_solve(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma, dd_result* out) {
-    return solve_impl(c, ev, D_lo, D_hi, tol_D, gamma, out, nullptr, 0, nullptr);
+    dd_window_params p = {D_lo, D_hi, tol_D, 0, gamma};
+    return solve_impl(c, ev, 1, &p, out, nullptr, 0, nullptr);
 }
 
 int dd_solve_trace(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float tol_D, double gamma,
                    dd_result* out, dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
-    return solve_impl(c, ev, D_lo, D_hi, tol_D, gamma, out, trace, trace_cap, trace_len);
+    dd_window_params p = {D_lo, D_hi, tol_D, 0, gamma};
+    return solve_impl(c, ev, 1, &p, out, trace, trace_cap, trace_len);
+}
+
+int dd_solve_batch(dd_ctx* c, const dd_events* windows, int32_t n_windows, const dd_window_params* params,
+                   dd_result* out) {
+    return solve_impl(c, windows, n_windows, params, out, nullptr, 0, nullptr);
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 // Internal types and launch interface shared by the kernels (dd_kernels.cu)
-// and the C-ABI host code (dd_api.cu).  Not part of the public ABI.
+// and the host code (dd_api.cu, dd_noalloc.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cstdint>
@@ -25,8 +25,13 @@ struct Task {
     int32_t kind, splits;
 };
 
+// One schedulable job: split `split` of `splits` of task `task` of window
+// `win`; a job covers every row band of the frame.
+struct Job {
+    int32_t win, task, split, splits;
+};
 
-// Per (task, tile) partial sums of one IWE tile.
+// Per (window, task, row band) partial sums of one IWE tile.
 struct Partial {
     unsigned long long S;      // sum of squared counts
     unsigned long long cells;  // sum of counts (N_in for a point, increments for a bound)
@@ -55,7 +60,8 @@ struct __align__(16) TraceRec {
 enum Phase : int32_t { PH_INIT = 0, PH_RUN = 1, PH_DONE = 2 };
 
 constexpr int MAX_POP = 64;
-constexpr int MAX_TASKS = 3 * MAX_POP;   // tasks of one evaluation launch
+constexpr int MAX_TASKS = 3 * MAX_POP;   // tasks of one window in one round
+constexpr int CHUNK = 8192;              // events per ingest block
 
 // Device-resident state of one BnB search (Algorithm 1).
 struct __align__(16) SolveState {
@@ -70,6 +76,34 @@ struct __align__(16) SolveState {
     int32_t phase, status, n_tasks, n_pop, q_n, q_start, q_cur, have_leaf, have_stop;
     int64_t nodes_expanded, point_evals, bound_evals, cells, bcells, rounds, max_queue, trace_len;
     Popped pop[MAX_POP];
+};
+
+// Search parameters of one window.
+struct __align__(16) WinParams {
+    i128 gamma_K;
+    float D_lo, D_hi, tol, pad;
+};
+
+// One window's input and where its sorted events go.
+struct WinIn {
+    const int16_t* x;
+    const int16_t* y;
+    const float* t;
+    int64_t n, ev_off;     // event count; offset in the sorted event buffers
+    float t0, tau;
+    int32_t chunk0, pad;   // first ingest chunk of the window
+};
+
+// Round bookkeeping of one context, in device memory.  Job lists and unit
+// counters are double-buffered by round parity: the evaluation of round r
+// reads list r % 2 and clears the other list's counters; the control blocks
+// of round r fill list (r + 1) % 2; the last control block to finish counts
+// the windows still searching and advances the round.
+struct Sched {
+    int32_t round;
+    int32_t n_jobs[2];
+    int32_t work[2];
+    int32_t ticket, active, running;
 };
 
 // Geometry of a context.  Events are sorted by (time bucket, row): n_tb
@@ -96,32 +130,51 @@ __host__ __device__ inline int32_t bound_splits(const Geom& g, float D_lo, float
     return s < 1 ? 1 : (s > g.max_splits ? g.max_splits : s);
 }
 
-// Kernel launches (dd_kernels.cu).  All asynchronous on `s`.
-cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
-                          float t0, float tau, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
-                          int32_t* cursor, int32_t* err, cudaStream_t s);
-// work: an item counter that is zero at launch (the kernel then runs a
-// persistent grid of grid_blocks blocks), or nullptr (one block per item).
-cudaError_t launch_eval(const Geom& g, const Ev* ev, const float2* rcp, const int32_t* row_off, const Task* tasks,
-                        const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
-                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s,
-                        int32_t* work = nullptr, int grid_blocks = 0, uint32_t* merge_acc = nullptr,
-                        int32_t* merge_done = nullptr, unsigned long long* merge_full = nullptr);
-int eval_resident_blocks(const Geom& g, int threads);
 // Time buckets for a frame of H rows: as many as fit 4096 bins, at most 8.
 inline int32_t time_buckets(int32_t H) {
     int32_t b = 4096 / H;
     return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
-cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part,
-                        i128* key, unsigned long long* S, unsigned long long* cells,
-                        unsigned long long* full, cudaStream_t s);
-cudaError_t launch_init(const Geom& g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol,
-                        float tau, i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds,
-                        int32_t trace_cap, int32_t* work, cudaStream_t s);
-cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,
-                           const int32_t* err, TraceRec* trace, cudaGraphConditionalHandle loop, int32_t use_loop,
-                           int32_t* work, cudaStream_t s);
+
+// Merge buffers of split jobs (single-window searches only).
+struct Merge {
+    uint32_t* acc;                 // [task][M] counts, zero between uses
+    int32_t* done;                 // [task][tile] finished splits, zero between uses
+    unsigned long long* full;      // [task][tile] N_full sums, zero between uses
+};
+
+// Everything an evaluation launch reads or writes.
+struct EvalArgs {
+    const Ev* ev;
+    const float2* rcp;
+    const int32_t* row_off;        // per window: n_tb * H + 1 entries
+    const WinIn* wins;
+    const Task* tasks;             // per window: task_stride entries
+    int32_t task_stride;
+    const Job* jobs;               // two lists of job_stride entries
+    int32_t job_stride;
+    Sched* sch;
+    Partial* part;                 // [(win * task_stride + task) * n_tiles + tile]
+    uint32_t* iwe_out;             // nullable: [task][M] (single window)
+    Merge mg;
+};
+
+// Kernel launches (dd_kernels.cu).  All asynchronous on `s`.
+cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_windows, const int32_t* chunk_win_dev,
+                          int32_t n_chunks, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
+                          int32_t* cursor, int32_t* err, cudaStream_t s);
+cudaError_t launch_eval(const Geom& g, const EvalArgs& a, int threads, int grid_blocks, cudaStream_t s);
+int eval_resident_blocks(const Geom& g, int threads);
+cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part, i128* key,
+                        unsigned long long* S, unsigned long long* cells, unsigned long long* full,
+                        cudaStream_t s);
+cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
+                        const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
+                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s);
+cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
+                           int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
+                           Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
+                           int32_t use_loop, cudaStream_t s);
 cudaError_t eval_smem_setup(const Geom& g);
 
 }  // namespace dd

@@ -1,10 +1,11 @@
 // GB300 (sm_103a) kernels of the exact divergence estimator:
-//   ingest   validate + counting-sort events by row (once per window)
+//   ingest   validate + counting-sort events by (time bucket, row), per window
 //   eval     point contrast (Eqs. 11-13) and interval bound (Eqs. 14-19) on
-//            shared-memory IWE tiles, one (task, row band) per block
+//            shared-memory IWE tiles: a resident grid takes (job, row band)
+//            units, a job being one task (or one split of it) of one window
 //   keys     per-task integer keys from the per-tile partial sums
-//   control  Algorithm 1 on the device: incumbent, priority queue, pruning,
-//            next batch of tasks
+//   control  Algorithm 1 on the device, one block per window: incumbent,
+//            priority queue, pruning, the next round's jobs
 //
 // Arithmetic contract.  The warp is evaluated in IEEE binary32 with one
 // rounding per operation, in this order, with no contraction into FMA:
@@ -12,7 +13,7 @@
 // __fmul_rn/__fadd_rn/__fsub_rn/__frcp_rn are never contracted.  The pixel a
 // warped event lands in is an integer decided by that arithmetic, and all
 // later work (counts, sums of squares, keys) is exact integer arithmetic, so
-// results do not depend on thread or block order.
+// results do not depend on thread, block or launch order.
 #include "dd_internal.cuh"
 #include "../../include/dd.h"
 
@@ -42,10 +43,25 @@ __device__ constexpr float WIDEN_UP = 1.0f + 0x1p-19f;
 // Half a pixel plus a 2^-8 px margin (above the cell rounding error).
 __device__ constexpr float HALF_PLUS = 0.50390625f;
 
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Inclusive prefix sum over the warp.
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
 // ------------------------------------------------------------------ ingest
 
 constexpr int INGEST_THREADS = 512;
-constexpr int MAX_ROWS = 4096;
+constexpr int MAX_BINS = 4096;
 
 __device__ __forceinline__ bool event_ok(int xi, int yi, float ti, float tr, float tau, int W, int H) {
     return isfinite(ti) && tr >= 0.0f && tr <= tau && xi >= 0 && xi < W && yi >= 0 && yi < H;
@@ -59,33 +75,42 @@ __device__ __forceinline__ int event_key(const Geom& g, int yi, float tr, float 
     return b * g.H + yi;
 }
 
-__global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const int16_t* __restrict__ x,
-                                                             const int16_t* __restrict__ y,
-                                                             const float* __restrict__ t, int64_t n,
-                                                             float t0, float tau, int32_t* row_count, int32_t* err) {
-    __shared__ int32_t h[MAX_ROWS];
+// Block c counts chunk c of its window into a shared histogram of the
+// window's bins, then adds it to the window's global counts.
+__global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const WinIn* __restrict__ wins,
+                                                             const int32_t* __restrict__ chunk_win,
+                                                             int32_t* row_count, int32_t* err) {
+    __shared__ int32_t h[MAX_BINS];
+    const int w = chunk_win[blockIdx.x];
+    const WinIn win = wins[w];
     const int bins = g.n_tb * g.H;
-    const float bscale = __fdiv_rn((float)g.n_tb, tau);
+    const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
     for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
+    const int64_t i0 = (int64_t)(blockIdx.x - win.chunk0) * CHUNK, i1 = min(win.n, i0 + CHUNK);
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int xi = x[i], yi = y[i];
-        float ti = t[i];
-        float tr = __fsub_rn(ti, t0);
-        if (!event_ok(xi, yi, ti, tr, tau, g.W, g.H)) { bad = 1; continue; }
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int xi = win.x[i], yi = win.y[i];
+        const float ti = win.t[i];
+        const float tr = __fsub_rn(ti, win.t0);
+        if (!event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) { bad = 1; continue; }
         atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
     }
-    if (bad) atomicOr(err, 1);
+    if (bad) atomicOr(&err[w], 1);
     __syncthreads();
+    int32_t* rc = row_count + (size_t)w * bins;
     for (int r = threadIdx.x; r < bins; r += blockDim.x)
-        if (h[r]) atomicAdd(&row_count[r], h[r]);
+        if (h[r]) atomicAdd(&rc[r], h[r]);
 }
 
-// Exclusive scan of the bin counts (at most 4096 bins) by one block.
-__global__ void __launch_bounds__(1024) k_row_scan(const int32_t* row_count, int bins, int32_t* row_off,
+// Exclusive scan of one window's bin counts (at most 4096 bins), block = window.
+__global__ void __launch_bounds__(1024) k_row_scan(int bins, const int32_t* row_count, int32_t* row_off,
                                                    int32_t* cursor) {
     __shared__ int32_t wsum[32];
+    const int w = blockIdx.x;
+    row_count += (size_t)w * bins;
+    cursor += (size_t)w * bins;
+    row_off += (size_t)w * (bins + 1);
     const int per = (bins + 1023) / 1024;
     int base = threadIdx.x * per;
     int local[4];
@@ -121,69 +146,66 @@ __global__ void __launch_bounds__(1024) k_row_scan(const int32_t* row_count, int
     if (threadIdx.x == 1023) row_off[bins] = excl;
 }
 
-// Scatter each valid event to its bin; a block reserves one range per bin,
-// so the global atomics are per (block, bin).  Also stores the reciprocals
-// of the event's offsets from the FOE (used by the bound's cell walk).
-__global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const int16_t* __restrict__ x,
-                                                                const int16_t* __restrict__ y,
-                                                                const float* __restrict__ t, int64_t n,
-                                                                float t0, float tau, int32_t* cursor,
-                                                                Ev* __restrict__ out, float2* __restrict__ rcp,
-                                                                int64_t chunk) {
-    __shared__ int32_t h[MAX_ROWS];
-    __shared__ int32_t base[MAX_ROWS];
+// Scatter each valid event of chunk c to its bin (offsets within the
+// window); a block reserves one range per bin, so the global atomics are per
+// (block, bin).  Also stores the reciprocals of the event's offsets from the
+// FOE (used by the bound's cell walk).
+__global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const WinIn* __restrict__ wins,
+                                                                const int32_t* __restrict__ chunk_win,
+                                                                int32_t* cursor, Ev* __restrict__ out,
+                                                                float2* __restrict__ rcp) {
+    __shared__ int32_t h[MAX_BINS];
+    __shared__ int32_t base[MAX_BINS];
+    const int w = chunk_win[blockIdx.x];
+    const WinIn win = wins[w];
     const int bins = g.n_tb * g.H;
-    const float bscale = __fdiv_rn((float)g.n_tb, tau);
-    int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
+    const int64_t i0 = (int64_t)(blockIdx.x - win.chunk0) * CHUNK, i1 = min(win.n, i0 + CHUNK);
+    int32_t* cur = cursor + (size_t)w * bins;
+    Ev* o = out + win.ev_off;
+    float2* rc = rcp + win.ev_off;
     for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        int xi = x[i], yi = y[i];
-        float ti = t[i];
-        float tr = __fsub_rn(ti, t0);
-        if (event_ok(xi, yi, ti, tr, tau, g.W, g.H)) atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
+        const int xi = win.x[i], yi = win.y[i];
+        const float ti = win.t[i];
+        const float tr = __fsub_rn(ti, win.t0);
+        if (event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < bins; r += blockDim.x) {
-        base[r] = h[r] ? atomicAdd(&cursor[r], h[r]) : 0;
+        base[r] = h[r] ? atomicAdd(&cur[r], h[r]) : 0;
         h[r] = 0;
     }
     __syncthreads();
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        int xi = x[i], yi = y[i];
-        float ti = t[i];
-        float tr = __fsub_rn(ti, t0);
-        if (!event_ok(xi, yi, ti, tr, tau, g.W, g.H)) continue;
+        const int xi = win.x[i], yi = win.y[i];
+        const float ti = win.t[i];
+        const float tr = __fsub_rn(ti, win.t0);
+        if (!event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) continue;
         const int key = event_key(g, yi, tr, bscale);
-        int pos = base[key] + atomicAdd(&h[key], 1);
+        const int pos = base[key] + atomicAdd(&h[key], 1);
         Ev e;
         e.x = (int16_t)xi;
         e.y = (int16_t)yi;
         e.t = tr;
-        out[pos] = e;
-        rcp[pos] = make_float2(__frcp_rn(__fsub_rn((float)xi, g.fx)), __frcp_rn(__fsub_rn((float)yi, g.fy)));
+        o[pos] = e;
+        rc[pos] = make_float2(__frcp_rn(__fsub_rn((float)xi, g.fx)), __frcp_rn(__fsub_rn((float)yi, g.fy)));
     }
 }
 
-cudaError_t launch_ingest(const Geom& g, const int16_t* x, const int16_t* y, const float* t, int64_t n,
-                          float t0, float tau, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
+cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_windows, const int32_t* chunk_win_dev,
+                          int32_t n_chunks, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
                           int32_t* cursor, int32_t* err, cudaStream_t s) {
     const int bins = g.n_tb * g.H;
-    cudaError_t e = cudaMemsetAsync(row_count, 0, sizeof(int32_t) * bins, s);
+    if (n_windows <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(row_count, 0, sizeof(int32_t) * bins * (size_t)n_windows, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    e = cudaMemsetAsync(err, 0, sizeof(int32_t) * (size_t)n_windows, s);
     if (e != cudaSuccess) return e;
-    if (n > 0) {
-        int64_t nb = (n + INGEST_THREADS - 1) / INGEST_THREADS;
-        int blocks = (int)(nb < 304 ? nb : 304);
-        k_row_hist<<<blocks, INGEST_THREADS, 0, s>>>(g, x, y, t, n, t0, tau, row_count, err);
-    }
-    k_row_scan<<<1, 1024, 0, s>>>(row_count, bins, row_off, cursor);
-    if (n > 0) {
-        int64_t chunk = 8192;
-        int blocks = (int)((n + chunk - 1) / chunk);
-        k_row_scatter<<<blocks, INGEST_THREADS, 0, s>>>(g, x, y, t, n, t0, tau, cursor, out, rcp, chunk);
-    }
+    if (n_chunks > 0) k_row_hist<<<n_chunks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, row_count, err);
+    k_row_scan<<<n_windows, 1024, 0, s>>>(bins, row_count, row_off, cursor);
+    if (n_chunks > 0) k_row_scatter<<<n_chunks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, cursor, out, rcp);
     return cudaGetLastError();
 }
 
@@ -315,51 +337,40 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
     }
 }
 
-// Inclusive prefix sum over the warp.
-__device__ __forceinline__ int warp_incl_scan(int v) {
-    const int lane = threadIdx.x & 31;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 constexpr int MAX_TB = 8;    // time buckets of the event sort
 
-// Buffers that merge the tiles of an item split over several blocks.
-struct Merge {
-    uint32_t* acc;                 // [task][M] counts, zero between uses
-    int32_t* done;                 // [task][tile] finished splits, zero between uses
-    unsigned long long* full;      // [task][tile] N_full sums, zero between uses
+// Where one unit reads and writes.
+struct UnitPtrs {
+    const Ev* ev;                 // the window's sorted events
+    const float2* rcp;
+    const int32_t* row_off;       // the window's bin offsets
+    Partial* part;                // the task's partials [n_tiles]
+    uint32_t* out;                // nullable: the task's image [H][W]
+    uint32_t* acc;                // split jobs: the task's accumulator [H][W]
+    int32_t* done;                // split jobs: finished splits per tile
+    unsigned long long* full;     // split jobs: N_full sums per tile
 };
 
-// One unit: split `split` of `splits` of the (task, tile) item.  The block
-// scatters its share of the events that can reach the tile's rows into the
-// shared tile.  An unsplit item reduces the tile itself; a split item adds
+// One unit: split `split` of `splits` of one task's row band `ti`.  The block
+// scatters its share of the events that can reach the band's rows into the
+// shared tile.  An unsplit task reduces the tile itself; a split task adds
 // its tile into the L2 accumulator, and the last of its blocks to finish
-// reduces the accumulated tile.  Writes part[task * n_tiles + tile].
-__device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ ev, const float2* __restrict__ rcp,
-                                          const int32_t* __restrict__ row_off, const Task& tk, int task, int ti,
-                                          int split, int splits, const Merge& mg, float tau,
-                                          Partial* __restrict__ part, uint32_t* __restrict__ iwe_out,
-                                          uint32_t* tile, unsigned long long (*red)[32], int* erange, int* s_last) {
+// reduces the accumulated band.  The tile arrives zeroed and leaves zeroed.
+__device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
+                                          int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
+                                          int* erange, int* s_last) {
     const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
-    // The tile arrives zeroed (the previous item's reduce clears what it read).
     // erange[b] = first event of bucket b's candidate run; erange[MAX_TB + b] =
     // the run's offset in the concatenation of all runs (MAX_TB + n_tb: total).
     if (threadIdx.x < 32) {
         int e0 = 0, e1 = 0;
         if (lane < g.n_tb)
-            bucket_event_range(g, row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
+            bucket_event_range(g, p.row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
                                e1);
         const int len = e1 - e0, incl = warp_incl_scan(len);
         if (lane < g.n_tb) {
@@ -386,7 +397,7 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
         const float D = tk.D_lo, gg = warp_g(D, tau);
 #pragma unroll 4
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
-            const Ev v = ev[event_at(f)];
+            const Ev v = p.ev[event_at(f)];
             const float s = warp_s(D, v.t, gg);
             const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
             if (uy < y0 || uy >= y1) continue;
@@ -395,81 +406,78 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
         }
     } else {
         const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
-        {
-            // Warps take 32 positions at a time, one event per lane.
-            for (int base = f_begin + (threadIdx.x >> 5) * 32; base < total; base += nw * 32) {
-                const int f = base + lane;
-                Seg sg;
-                sg.mode = SEG_NONE;
-                sg.k0 = sg.count = sg.addr = 0;
-                sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
-                if (f < total) {
-                    const int e = event_at(f);
-                    const Ev v = ev[e];
-                    const float dy = __fsub_rn((float)v.y, g.fy);
-                    const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-                    const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-                    const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-                    const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
-                    // Every covered cell lies between the rows of the two end
-                    // cells (each cell coordinate is monotone in s).
-                    if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
-                        const float dx = __fsub_rn((float)v.x, g.fx);
-                        const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
-                        // Eq. (19): both end cells in the frame; counted by the tile of row ya.
-                        if (xa >= 0 && xa < W && ya >= 0 && ya < g.H && xb >= 0 && xb < W && yb >= 0 &&
-                            yb < g.H && ya >= y0 && ya < y1)
-                            full++;
-                        if (xa == xb && ya == yb) {
-                            // Both ends in one pixel: each cell coordinate is
-                            // monotone in s, so the segment covers that pixel only.
-                            if (xa >= 0 && xa < W && ya >= y0 && ya < y1) {
-                                sg.mode = SEG_ONE;
-                                sg.count = 1;
-                                sg.addr = (ya - y0) * P + xa;
-                            }
-                        } else {
-                            const float2 r = rcp[e];
-                            sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+        // Warps take 32 positions at a time, one event per lane.
+        for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
+            const int f = base + lane;
+            Seg sg;
+            sg.mode = SEG_NONE;
+            sg.k0 = sg.count = sg.addr = 0;
+            sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
+            if (f < total) {
+                const int e = event_at(f);
+                const Ev v = p.ev[e];
+                const float dy = __fsub_rn((float)v.y, g.fy);
+                const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+                const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+                const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+                const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
+                // Every covered cell lies between the rows of the two end
+                // cells (each cell coordinate is monotone in s).
+                if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                    const float dx = __fsub_rn((float)v.x, g.fx);
+                    const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
+                    // Eq. (19): both end cells in the frame; counted by the tile of row ya.
+                    if (xa >= 0 && xa < W && ya >= 0 && ya < g.H && xb >= 0 && xb < W && yb >= 0 && yb < g.H &&
+                        ya >= y0 && ya < y1)
+                        full++;
+                    if (xa == xb && ya == yb) {
+                        // Both ends in one pixel: each cell coordinate is
+                        // monotone in s, so the segment covers that pixel only.
+                        if (xa >= 0 && xa < W && ya >= y0 && ya < y1) {
+                            sg.mode = SEG_ONE;
+                            sg.count = 1;
+                            sg.addr = (ya - y0) * P + xa;
                         }
+                    } else {
+                        const float2 r = p.rcp[e];
+                        sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
                     }
                 }
-                const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
-                if (cmax == 0) continue;
-                if (cmax <= 2) {                  // short runs: each lane walks its own
-                    for (int i = 0; i < sg.count; i++)
-                        seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile);
-                    continue;
+            }
+            const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
+            if (cmax == 0) continue;
+            if (cmax <= 2) {                      // short runs: each lane walks its own
+                for (int i = 0; i < sg.count; i++)
+                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile);
+                continue;
+            }
+            // Long runs: spread the (event, major cell) pairs over the lanes.
+            const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            for (int c0 = 0; c0 < tot; c0 += 32) {
+                const int gi = c0 + lane;
+                int o = 0;                        // owner: first lane whose inclusive sum exceeds gi
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int probe = __shfl_sync(0xffffffffu, incl, o + step - 1);
+                    if (probe <= gi) o += step;
                 }
-                // Long runs: spread the (event, major cell) pairs over the lanes.
-                const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                for (int c0 = 0; c0 < total; c0 += 32) {
-                    const int gi = c0 + lane;
-                    int o = 0;                    // owner: first lane whose inclusive sum exceeds gi
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int probe = __shfl_sync(0xffffffffu, incl, o + step - 1);
-                        if (probe <= gi) o += step;
-                    }
-                    const int om = __shfl_sync(0xffffffffu, sg.mode, o);
-                    const int ok = __shfl_sync(0xffffffffu, sg.k0 - excl, o);
-                    const int oa = __shfl_sync(0xffffffffu, sg.addr, o);
-                    const float odn = __shfl_sync(0xffffffffu, sg.dn, o);
-                    const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
-                    const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
-                    const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
-                    if (gi < total) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile);
-                }
+                const int om = __shfl_sync(0xffffffffu, sg.mode, o);
+                const int ok = __shfl_sync(0xffffffffu, sg.k0 - excl, o);
+                const int oa = __shfl_sync(0xffffffffu, sg.addr, o);
+                const float odn = __shfl_sync(0xffffffffu, sg.dn, o);
+                const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
+                const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
+                const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
+                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile);
             }
         }
     }
     __syncthreads();
 
-    uint32_t* out = iwe_out ? iwe_out + (size_t)task * W * g.H + (size_t)y0 * W : nullptr;
-    const int item = task * g.n_tiles + ti;
+    uint32_t* out = p.out ? p.out + (size_t)y0 * W : nullptr;
     unsigned long long S = 0, C = 0;
-    // Tile rows have pitch P (odd), frame rows have pitch W: warps take rows,
-    // lanes take columns.
+    // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
+    // take columns.
     if (splits == 1) {
         for (int r = wid; r < rows; r += nw)
             for (int c = lane; c < W; c += 32) {
@@ -480,8 +488,8 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
                 if (out) out[r * W + c] = (uint32_t)v;
             }
     } else {
-        uint32_t* acc = mg.acc + (size_t)task * W * g.H + (size_t)y0 * W;
-        // Splits of one item finish together: each starts its pass at its own
+        uint32_t* acc = p.acc + (size_t)y0 * W;
+        // Splits of one band finish together: each starts its pass at its own
         // row so that they add into different words at a time.
         const int rot = (int)((long long)rows * split / splits);
         for (int q = wid; q < rows; q += nw) {
@@ -501,12 +509,12 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
         if (threadIdx.x == 0) {
             unsigned long long f = 0;
             for (int w = 0; w < nw; w++) f += red[2][w];
-            if (f) atomicAdd(&mg.full[item], f);
+            if (f) atomicAdd(&p.full[ti], f);
             __threadfence();
-            *s_last = atomicAdd(&mg.done[item], 1) == splits - 1;
+            *s_last = atomicAdd(&p.done[ti], 1) == splits - 1;
         }
         __syncthreads();
-        if (!*s_last) return;                     // another split finishes the item
+        if (!*s_last) return;                     // another split finishes the band
         __threadfence();                          // every split's additions are visible now
         for (int i = threadIdx.x; i < rows * W; i += blockDim.x) {
             const unsigned long long v = __ldcg(&acc[i]);
@@ -517,8 +525,8 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
         }
         full = 0;
         if (threadIdx.x == 0) {
-            full = atomicExch(&mg.full[item], 0ull);
-            mg.done[item] = 0;
+            full = atomicExch(&p.full[ti], 0ull);
+            p.done[ti] = 0;
         }
     }
     S = warp_sum(S);
@@ -535,76 +543,59 @@ __device__ __forceinline__ void eval_item(const Geom& g, const Ev* __restrict__ 
         C = warp_sum(C);
         full = warp_sum(full);
         if (lane == 0) {
-            Partial p;
-            p.S = S;
-            p.cells = C;
-            p.full = full;
-            part[item] = p;
+            Partial q;
+            q.S = S;
+            q.cells = C;
+            q.full = full;
+            p.part[ti] = q;
         }
     }
 }
 
-// IWE evaluation of a task list.  With `work` (a unit counter that is zero
-// at launch), a grid of resident blocks takes units in turn: a task of
-// `splits` splits has n_tiles * splits units, and the tasks queued last (a
-// round's bound tasks) come first.  Without it, block b evaluates (task,
-// tile) item b unsplit.  A finished search launches nothing.
-__global__ void __launch_bounds__(1024) k_eval(Geom g, const Ev* __restrict__ ev,
-                                               const float2* __restrict__ rcp,
-                                               const int32_t* __restrict__ row_off,
-                                               const Task* __restrict__ tasks, const int32_t* n_tasks_dev,
-                                               int32_t n_tasks_host, float tau, Partial* __restrict__ part,
-                                               uint32_t* __restrict__ iwe_out, const SolveState* st,
-                                               int32_t* work, Merge mg) {
+// IWE evaluation of the round's job list.  A grid of resident blocks takes
+// units (job, row band) from a counter; block 0 clears the other parity's
+// list and counter for the control blocks of this round.
+__global__ void __launch_bounds__(1024) k_eval(Geom g, EvalArgs a) {
     extern __shared__ uint32_t tile[];
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
-    __shared__ int ustart[MAX_TASKS + 1];
-    __shared__ int s_item, s_last;
-    if (st && st->phase == PH_DONE) return;
-    const int n_tasks = n_tasks_dev ? *n_tasks_dev : n_tasks_host;
-    if (st) tau = st->tau;                       // a solve keeps its tau in the state
+    __shared__ int s_unit, s_last;
+    Sched* sch = a.sch;
+    const int par = sch->round & 1;
+    const int n_units = sch->n_jobs[par] * g.n_tiles;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sch->n_jobs[par ^ 1] = 0;
+        sch->work[par ^ 1] = 0;
+    }
+    if (n_units == 0) return;
+    int32_t* work = &sch->work[par];
+    const Job* jobs = a.jobs + (size_t)par * a.job_stride;
     const int tile_words = g.band_rows * tile_pitch(g);
-    if (!work) {
-        const int task = blockIdx.x / g.n_tiles;
-        if (task >= n_tasks) return;
-        for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
-        eval_item(g, ev, rcp, row_off, tasks[task], task, blockIdx.x - task * g.n_tiles, 0, 1, mg, tau, part,
-                  iwe_out, tile, red, erange, &s_last);
-        return;
-    }
-    if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
-    if (threadIdx.x < 32) {                       // unit offsets, tasks in processing order
-        int run = 0;
-        for (int base = 0; base < n_tasks; base += 32) {
-            const int p = base + threadIdx.x;
-            const int c = p < n_tasks ? g.n_tiles * max(1, tasks[n_tasks - 1 - p].splits) : 0;
-            const int incl = warp_incl_scan(c);
-            if (p < n_tasks) ustart[p] = run + incl - c;
-            run += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (threadIdx.x == 0) ustart[n_tasks] = run;
-    }
+    const int bins1 = g.n_tb * g.H + 1;
+    if (threadIdx.x == 0) s_unit = atomicAdd(work, 1);
     for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
     __syncthreads();
-    const int n_units = ustart[n_tasks];
     for (;;) {
-        const int u = s_item;
+        const int u = s_unit;
         if (u >= n_units) break;
-        __syncthreads();                          // every thread has read s_item
-        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);   // the next unit, fetched early
-        int lo = 0, hi = n_tasks - 1;             // last p with ustart[p] <= u
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (ustart[mid] <= u) lo = mid;
-            else hi = mid - 1;
-        }
-        const int task = n_tasks - 1 - lo;
-        const Task tk = tasks[task];
-        const int splits = max(1, tk.splits), r = u - ustart[lo];
-        eval_item(g, ev, rcp, row_off, tk, task, r / splits, r % splits, splits, mg, tau, part, iwe_out, tile, red,
-                  erange, &s_last);
-        __syncthreads();                          // the unit's readers are done; s_item is set
+        __syncthreads();                          // every thread has read s_unit
+        if (threadIdx.x == 0) s_unit = atomicAdd(work, 1);   // the next unit, fetched early
+        const int j = u / g.n_tiles, ti = u - j * g.n_tiles;
+        const Job jb = jobs[j];
+        const int64_t ev_off = a.wins[jb.win].ev_off;
+        const float tau = a.wins[jb.win].tau;
+        const Task tk = a.tasks[(size_t)jb.win * a.task_stride + jb.task];
+        UnitPtrs p;
+        p.ev = a.ev + ev_off;
+        p.rcp = a.rcp + ev_off;
+        p.row_off = a.row_off + (size_t)jb.win * bins1;
+        p.part = a.part + ((size_t)jb.win * a.task_stride + jb.task) * g.n_tiles;
+        p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * g.W * g.H : nullptr;
+        p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * g.W * g.H : nullptr;
+        p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
+        p.full = a.mg.full ? a.mg.full + (size_t)jb.task * g.n_tiles : nullptr;
+        eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last);
+        __syncthreads();                          // the unit's readers are done; s_unit is set
     }
 }
 
@@ -617,23 +608,10 @@ int eval_resident_blocks(const Geom& g, int threads) {
     return per_sm * sms;
 }
 
-cudaError_t launch_eval(const Geom& g, const Ev* ev, const float2* rcp, const int32_t* row_off, const Task* tasks,
-                        const int32_t* n_tasks_dev, int32_t n_tasks_max, float tau, Partial* part,
-                        uint32_t* iwe_out, const SolveState* st, int threads, cudaStream_t s, int32_t* work,
-                        int grid_blocks, uint32_t* merge_acc, int32_t* merge_done, unsigned long long* merge_full) {
-    if (work && (!merge_acc || !merge_done || !merge_full)) return cudaErrorInvalidValue;
-    Merge mg;
-    mg.acc = merge_acc;
-    mg.done = merge_done;
-    mg.full = merge_full;
-    if (n_tasks_max <= 0) return cudaSuccess;
-    size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
-    // Split units: up to max_splits per (task, tile) item when a work counter
-    // schedules them.
-    const long long units = (long long)n_tasks_max * g.n_tiles * (work ? g.max_splits : 1);
-    const int grid = work && grid_blocks > 0 && grid_blocks < units ? grid_blocks : (int)units;
-    k_eval<<<grid, threads, smem, s>>>(g, ev, rcp, row_off, tasks, n_tasks_dev, n_tasks_max, tau, part, iwe_out,
-                                       st, work, mg);
+cudaError_t launch_eval(const Geom& g, const EvalArgs& a, int threads, int grid_blocks, cudaStream_t s) {
+    if (grid_blocks <= 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
+    k_eval<<<grid_blocks, threads, smem, s>>>(g, a);
     return cudaGetLastError();
 }
 
@@ -677,23 +655,27 @@ cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------- Algorithm 1
-
 __device__ __forceinline__ float centre(float lo, float hi) {
     return __fadd_rn(lo, __fmul_rn(0.5f, __fsub_rn(hi, lo)));
 }
 
-__global__ void k_init(Geom g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
-                       i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
-                       int32_t* work) {
+// One block per window: the search state, the round-0 tasks (the centre of
+// the domain and the bound of the domain) and their jobs in list 0.
+__global__ void k_init(Geom g, int32_t n_windows, SolveState* st_all, Task* tasks_all, int32_t task_stride,
+                       const WinIn* wins, const WinParams* params, Job* jobs, Sched* sch, int32_t K_pop,
+                       int32_t qcap, int64_t max_rounds, int32_t trace_cap) {
     if (threadIdx.x != 0) return;
-    *work = 0;
-    st->gamma_K = gamma_K;
-    st->M = M;
+    const int w = blockIdx.x;
+    SolveState* st = st_all + w;
+    Task* tasks = tasks_all + (size_t)w * task_stride;
+    const WinParams pr = params[w];
+    const float tau = wins[w].tau;
+    st->gamma_K = pr.gamma_K;
+    st->M = (int64_t)g.W * g.H;
     st->max_rounds = max_rounds;
-    st->D_lo = D_lo;
-    st->D_hi = D_hi;
-    st->tol = tol;
+    st->D_lo = pr.D_lo;
+    st->D_hi = pr.D_hi;
+    st->tol = pr.tol;
     st->tau = tau;
     st->K_pop = K_pop;
     st->qcap = qcap;
@@ -701,7 +683,7 @@ __global__ void k_init(Geom g, SolveState* st, Task* tasks, int64_t M, float D_l
     st->K_hat = 0;
     st->leaf_max = 0;
     st->stop_kb = 0;
-    st->D_hat = centre(D_lo, D_hi);               // incumbent = centre of the domain
+    st->D_hat = centre(pr.D_lo, pr.D_hi);         // incumbent = centre of the domain
     st->phase = PH_INIT;
     st->status = DD_OK;
     st->n_pop = 0;
@@ -716,19 +698,36 @@ __global__ void k_init(Geom g, SolveState* st, Task* tasks, int64_t M, float D_l
     a.D_lo = a.D_hi = st->D_hat;
     a.kind = TASK_POINT;
     a.splits = 1;
-    b.D_lo = D_lo;                                // bound of the domain (queued first)
-    b.D_hi = D_hi;
+    b.D_lo = pr.D_lo;                             // bound of the domain (queued first)
+    b.D_hi = pr.D_hi;
     b.kind = TASK_BOUND;
-    b.splits = bound_splits(g, D_lo, D_hi, tau);
+    b.splits = n_windows == 1 ? bound_splits(g, pr.D_lo, pr.D_hi, tau) : 1;
     tasks[0] = a;
     tasks[1] = b;
     st->n_tasks = 2;
+    const int base = atomicAdd(&sch->n_jobs[0], 1 + b.splits);
+    for (int s = 0; s < b.splits; s++) {
+        Job j;
+        j.win = w;
+        j.task = 1;
+        j.split = s;
+        j.splits = b.splits;
+        jobs[base + s] = j;
+    }
+    Job j;
+    j.win = w;
+    j.task = 0;
+    j.split = 0;
+    j.splits = 1;
+    jobs[base + b.splits] = j;
 }
 
-cudaError_t launch_init(const Geom& g, SolveState* st, Task* tasks, int64_t M, float D_lo, float D_hi, float tol, float tau,
-                        i128 gamma_K, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
-                        int32_t* work, cudaStream_t s) {
-    k_init<<<1, 32, 0, s>>>(g, st, tasks, M, D_lo, D_hi, tol, tau, gamma_K, K_pop, qcap, max_rounds, trace_cap, work);
+cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
+                        const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
+                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s) {
+    (void)job_stride;
+    k_init<<<n_windows, 32, 0, s>>>(g, n_windows, st, tasks, task_stride, wins, params, jobs, sch, K_pop, qcap,
+                                    max_rounds, trace_cap);
     return cudaGetLastError();
 }
 
@@ -766,17 +765,21 @@ __device__ __forceinline__ i128 warp_max_i128(i128 v) {
     return v;
 }
 
-// One block per search.  Consumes the keys of the round just evaluated
+// One block per window.  Consumes the keys of the round just evaluated
 // (Algorithm 1: incumbent update, leaves, child bounds and their insertion),
-// then dequeues the next batch (dequeue and gap test) and writes its tasks,
-// or finishes.  The search state is staged in shared memory; per-interval
-// work runs one interval per lane of warp 0.  The queue is kept sorted in
-// priority order in one of two buffers: insertion is a parallel merge into
-// the other buffer, a dequeue takes a prefix.
-__global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st, Node* qa, Node* qb, Task* tasks,
-                                                        const Partial* part, const int32_t* err, TraceRec* trace,
-                                                        cudaGraphConditionalHandle loop, int32_t use_loop,
-                                                        int32_t* work) {
+// then dequeues the next batch (dequeue and gap test) and writes its tasks
+// and jobs, or finishes.  The search state is staged in shared memory;
+// per-interval work runs one interval per lane of warp 0.  The queue is kept
+// sorted in priority order in one of two buffers: insertion is a parallel
+// merge into the other buffer, a dequeue takes a prefix.  The last block to
+// finish counts the windows still searching, advances the round and sets the
+// graph loop condition.
+__global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windows, SolveState* st_all,
+                                                        Node* queues, Task* tasks_all, int32_t task_stride,
+                                                        const Partial* part_all, const int32_t* err_all,
+                                                        TraceRec* trace, Job* jobs_all, int32_t job_stride,
+                                                        Sched* sch, cudaGraphConditionalHandle loop,
+                                                        int32_t use_loop) {
     __shared__ SolveState s;
     __shared__ i128 key[3 * MAX_POP];
     __shared__ unsigned long long cells[3 * MAX_POP];
@@ -784,15 +787,20 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
     __shared__ Node sorted_kids[2 * MAX_POP + 1];
     __shared__ int s_nk, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int w = blockIdx.x;
+    const int par = sch->round & 1;
+    SolveState* st = st_all + w;
+    Task* tasks = tasks_all + (size_t)w * task_stride;
+    const Partial* part = part_all + (size_t)w * task_stride * g.n_tiles;
+    Job* jobs = jobs_all + (size_t)(par ^ 1) * job_stride;
     static_assert(sizeof(SolveState) % 16 == 0, "state is copied as int4");
     for (int i = tid; i < (int)(sizeof(SolveState) / 16); i += blockDim.x)
         reinterpret_cast<int4*>(&s)[i] = reinterpret_cast<const int4*>(st)[i];
     __syncthreads();
-    if (s.phase == PH_DONE) {
-        if (use_loop && tid == 0) cudaGraphSetConditional(loop, 0);
-        return;
-    }
-    if (tid == 0) *work = 0;                      // the next evaluation starts at item 0
+    if (s.phase != PH_DONE) {
+    Node* qa = queues + (size_t)w * 2 * s.qcap;
+    Node* qb = qa + s.qcap;
+    const int32_t* err = err_all + w;
     const int64_t M = s.M;
     const int n_tasks = s.n_tasks;
 
@@ -867,7 +875,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
                 const bool v = j < np;
                 Popped p;
                 if (v) p = s.pop[j];
-                if (v && trace && s.trace_len + j < s.trace_cap) {
+                if (v && trace && w == 0 && s.trace_len + j < s.trace_cap) {
                     TraceRec r;
                     r.D_lo = p.lo;
                     r.D_hi = p.hi;
@@ -1045,11 +1053,11 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
                         l.D_lo = p.lo;
                         l.D_hi = p.c;
                         l.kind = TASK_BOUND;
-                        l.splits = bound_splits(g, p.lo, p.c, s.tau);
+                        l.splits = n_windows == 1 ? bound_splits(g, p.lo, p.c, s.tau) : 1;
                         r.D_lo = p.c;
                         r.D_hi = p.hi;
                         r.kind = TASK_BOUND;
-                        r.splits = bound_splits(g, p.c, p.hi, s.tau);
+                        r.splits = n_windows == 1 ? bound_splits(g, p.c, p.hi, s.tau) : 1;
                         tasks[t] = l;
                         tasks[t + 1] = r;
                     } else {
@@ -1071,17 +1079,62 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, SolveState* st,
             }
         }
         __syncwarp();
-        if (use_loop && lane == 0) cudaGraphSetConditional(loop, s.phase == PH_DONE ? 0u : 1u);
+        // Jobs of the next round, bound tasks first: a task of `splits`
+        // splits contributes that many jobs.
+        if (s.phase != PH_DONE) {
+            const int nt = s.n_tasks;
+            int run = 0, base = 0;
+            int total = 0;
+            for (int c0 = 0; c0 < nt; c0 += 32) {
+                const int q = c0 + lane;
+                const int c = q < nt ? max(1, tasks[nt - 1 - q].splits) : 0;
+                total += __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
+            }
+            if (lane == 0) base = atomicAdd(&sch->n_jobs[par ^ 1], total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int c0 = 0; c0 < nt; c0 += 32) {
+                const int q = c0 + lane;
+                const int t = nt - 1 - q;
+                const int c = q < nt ? max(1, tasks[t].splits) : 0;
+                const int incl = warp_incl_scan(c);
+                for (int k = 0; k < c; k++) {
+                    Job j;
+                    j.win = w;
+                    j.task = t;
+                    j.split = k;
+                    j.splits = c;
+                    jobs[base + run + incl - c + k] = j;
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
     }
     __syncthreads();
     for (int i = tid; i < (int)(sizeof(SolveState) / 16); i += blockDim.x)
         reinterpret_cast<int4*>(st)[i] = reinterpret_cast<const int4*>(&s)[i];
+    } // s.phase != PH_DONE at entry
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (s.phase != PH_DONE) atomicAdd(&sch->active, 1);
+        if (atomicAdd(&sch->ticket, 1) == n_windows - 1) {    // the last block of the round
+            __threadfence();
+            const int active = atomicAdd(&sch->active, 0);
+            sch->running = active;
+            sch->active = 0;
+            sch->ticket = 0;
+            sch->round += 1;
+            if (use_loop) cudaGraphSetConditional(loop, active > 0 ? 1u : 0u);
+        }
+    }
 }
 
-cudaError_t launch_control(const Geom& g, SolveState* st, Node* qa, Node* qb, Task* tasks, const Partial* part,
-                           const int32_t* err, TraceRec* trace, cudaGraphConditionalHandle loop, int32_t use_loop,
-                           int32_t* work, cudaStream_t s) {
-    k_control<<<1, CTL_THREADS, 0, s>>>(g, st, qa, qb, tasks, part, err, trace, loop, use_loop, work);
+cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
+                           int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
+                           Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
+                           int32_t use_loop, cudaStream_t s) {
+    k_control<<<n_windows, CTL_THREADS, 0, s>>>(g, n_windows, st, queues, tasks, task_stride, part, err, trace, jobs,
+                                                job_stride, sch, loop, use_loop);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,12 @@ constexpr size_t OFF_ROW_COUNT = align256(OFF_RCP + sizeof(float2) * NA_MAX_EVEN
 constexpr size_t OFF_ROW_OFF = align256(OFF_ROW_COUNT + sizeof(int32_t) * NA_MAX_ROWS);
 constexpr size_t OFF_CURSOR = align256(OFF_ROW_OFF + sizeof(int32_t) * (NA_MAX_ROWS + 1));
 constexpr size_t OFF_ERR = align256(OFF_CURSOR + sizeof(int32_t) * NA_MAX_ROWS);
-constexpr size_t OFF_TASKS = align256(OFF_ERR + sizeof(int32_t));
+constexpr size_t OFF_WIN = align256(OFF_ERR + sizeof(int32_t));
+constexpr size_t OFF_CHUNKS = align256(OFF_WIN + sizeof(dd::WinIn));
+constexpr size_t NA_MAX_CHUNKS = (NA_MAX_EVENTS + dd::CHUNK - 1) / dd::CHUNK;
+constexpr size_t OFF_SCHED = align256(OFF_CHUNKS + sizeof(int32_t) * NA_MAX_CHUNKS);
+constexpr size_t OFF_JOBS = align256(OFF_SCHED + sizeof(dd::Sched));
+constexpr size_t OFF_TASKS = align256(OFF_JOBS + sizeof(dd::Job) * 2 * NA_MAX_TASKS);
 constexpr size_t OFF_PART = align256(OFF_TASKS + sizeof(dd::Task) * NA_MAX_TASKS);
 constexpr size_t OFF_KEYS = align256(OFF_PART + sizeof(dd::Partial) * NA_MAX_TASKS * NA_MAX_TILES);
 constexpr size_t OFF_S = align256(OFF_KEYS + sizeof(dd::i128) * NA_MAX_TASKS);
@@ -109,6 +114,10 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     int32_t* row_off = (int32_t*)(base + OFF_ROW_OFF);
     int32_t* cursor = (int32_t*)(base + OFF_CURSOR);
     int32_t* err = (int32_t*)(base + OFF_ERR);
+    dd::WinIn* win = (dd::WinIn*)(base + OFF_WIN);
+    int32_t* chunk_win = (int32_t*)(base + OFF_CHUNKS);
+    dd::Sched* sch = (dd::Sched*)(base + OFF_SCHED);
+    dd::Job* jobs = (dd::Job*)(base + OFF_JOBS);
     dd::Task* tasks = (dd::Task*)(base + OFF_TASKS);
     dd::Partial* part = (dd::Partial*)(base + OFF_PART);
     dd::i128* keys = (dd::i128*)(base + OFF_KEYS);
@@ -116,14 +125,51 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     unsigned long long* C = (unsigned long long*)(base + OFF_C);
     unsigned long long* F = (unsigned long long*)(base + OFF_F);
 
-    // row_count and err are cleared by the ingest before use; every live
-    // (task, tile) block overwrites its partial, so nothing else needs zeroing.
-    if (dd::launch_ingest(g, ev->x, ev->y, ev->t, ev->n, ev->t0, ev->tau, ev_sorted, rcp, row_count, row_off, cursor,
-                          err, s) != cudaSuccess)
+    // The window descriptor and chunk map go in from host stack buffers; the
+    // ingest clears the bin counts and the error flag itself, and every live
+    // (task, tile) unit overwrites its partial, so nothing else needs zeroing.
+    dd::WinIn h_win;
+    h_win.x = ev->x;
+    h_win.y = ev->y;
+    h_win.t = ev->t;
+    h_win.n = ev->n;
+    h_win.ev_off = 0;
+    h_win.t0 = ev->t0;
+    h_win.tau = ev->tau;
+    h_win.chunk0 = 0;
+    h_win.pad = 0;
+    const int32_t n_chunks = (int32_t)((ev->n + dd::CHUNK - 1) / dd::CHUNK);
+    int32_t h_chunks[NA_MAX_CHUNKS];
+    for (int32_t k = 0; k < n_chunks; k++) h_chunks[k] = 0;
+    if (cudaMemcpyAsync(win, &h_win, sizeof(h_win), cudaMemcpyHostToDevice, s) != cudaSuccess) return DD_ERR_CUDA;
+    if (n_chunks &&
+        cudaMemcpyAsync(chunk_win, h_chunks, sizeof(int32_t) * n_chunks, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DD_ERR_CUDA;
+    if (dd::launch_ingest(g, win, 1, chunk_win, n_chunks, ev_sorted, rcp, row_count, row_off, cursor, err, s) !=
+        cudaSuccess)
+        return DD_ERR_CUDA;
+    dd::EvalArgs a;
+    a.ev = ev_sorted;
+    a.rcp = rcp;
+    a.row_off = row_off;
+    a.wins = win;
+    a.tasks = tasks;
+    a.task_stride = NA_MAX_TASKS;
+    a.jobs = jobs;
+    a.job_stride = NA_MAX_TASKS;
+    a.sch = sch;
+    a.part = part;
+    a.iwe_out = nullptr;
+    a.mg.acc = nullptr;
+    a.mg.done = nullptr;
+    a.mg.full = nullptr;
     dd::Task h_tasks[NA_MAX_TASKS];
+    dd::Job h_jobs[NA_MAX_TASKS];
+    dd::Sched h_sch;
     dd::i128 h_keys[NA_MAX_TASKS];
     int32_t h_err = 0;
+    const int grid = dd::eval_resident_blocks(g, 512);
+    if (grid <= 0) return DD_ERR_CUDA;
     for (int32_t j0 = 0; j0 < nD || j0 == 0; j0 += NA_MAX_TASKS) {
         const int32_t m = nD - j0 < NA_MAX_TASKS ? nD - j0 : NA_MAX_TASKS;
         if (m > 0) {
@@ -131,12 +177,18 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
                 h_tasks[j].D_lo = h_tasks[j].D_hi = D[j0 + j];
                 h_tasks[j].kind = dd::TASK_POINT;
                 h_tasks[j].splits = 1;
+                h_jobs[j].win = 0;
+                h_jobs[j].task = j;
+                h_jobs[j].split = 0;
+                h_jobs[j].splits = 1;
             }
-            if (cudaMemcpyAsync(tasks, h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            std::memset(&h_sch, 0, sizeof(h_sch));
+            h_sch.n_jobs[0] = m;
+            if (cudaMemcpyAsync(tasks, h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(jobs, h_jobs, sizeof(dd::Job) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(sch, &h_sch, sizeof(h_sch), cudaMemcpyHostToDevice, s) != cudaSuccess)
                 return DD_ERR_CUDA;
-            if (dd::launch_eval(g, ev_sorted, rcp, row_off, tasks, nullptr, m, ev->tau, part, nullptr, nullptr, 512, s) !=
-                cudaSuccess)
-                return DD_ERR_CUDA;
+            if (dd::launch_eval(g, a, 512, grid, s) != cudaSuccess) return DD_ERR_CUDA;
             if (dd::launch_keys(g, tasks, m, part, keys, S, C, F, s) != cudaSuccess) return DD_ERR_CUDA;
             if (cudaMemcpyAsync(h_keys, keys, sizeof(dd::i128) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess)
                 return DD_ERR_CUDA;

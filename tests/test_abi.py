@@ -58,6 +58,7 @@ def test_struct_layouts_match_header(tmp_path):
     fields = {"dd_events": [f for f, _ in dd.dd_events._fields_], "dd_result": [f for f, _ in dd.dd_result._fields_],
               "dd_config": [f for f, _ in dd.dd_config._fields_], "dd_node_rec": [f for f, _ in dd.dd_node_rec._fields_],
               "dd_stats": [f for f, _ in dd.dd_stats._fields_],
+              "dd_window_params": [f for f, _ in dd.dd_window_params._fields_],
               "dd_i128": ["lo", "hi"]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dd.h"', "int main(void) {"]
     for s, fs in fields.items():
