@@ -287,6 +287,15 @@ class Context:
     def M(self):
         return self.W * self.H
 
+    @classmethod
+    def tuned(cls, W, H, foe_x, foe_y, n_events, mode="single", **kw):
+        """A context with the autotuned knobs for this geometry and size
+        (autotune.py's table), falling back to the defaults."""
+        from . import autotune
+        knobs = autotune.lookup(W, H, n_events, mode) or {}
+        knobs.update(kw)
+        return cls(W, H, foe_x, foe_y, **knobs)
+
     def close(self):
         if self.h:
             dd_destroy(self.h)

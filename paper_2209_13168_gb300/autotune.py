@@ -1,0 +1,138 @@
+"""Autotuner for the IWE tiling and the BnB schedule.
+
+Times exact solves of sample windows on the current GPU for each candidate
+(band rows, threads per block, intervals per round, split cap) and records
+the fastest in a JSON table keyed by (frame geometry, event-count bucket,
+single-window or batch, GPU name).  The knobs change only the schedule:
+results are identical for every candidate (the table stores times, and the
+tuner checks that every candidate returned the same keys).
+
+    python -m paper_2209_13168_gb300.autotune --out tuned.json
+"""
+import argparse
+import itertools
+import json
+import math
+import os
+import time
+
+import paper_2209_13168_gb300 as dd
+
+DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
+
+CANDIDATES = {
+    "band_rows": [8, 16, 24, 38],
+    "threads": [256, 512, 1024],
+    "pop_k": [8, 16, 32],
+    "max_splits": [4, 8, 16],
+}
+
+
+def size_bucket(n_events):
+    """Event counts are bucketed by powers of two."""
+    return int(2 ** max(0, round(math.log2(max(1, n_events)))))
+
+
+def key(W, H, n_events, mode, gpu):
+    return "%dx%d/n%d/%s/%s" % (W, H, size_bucket(n_events), mode, gpu)
+
+
+def gpu_name():
+    import torch
+    return torch.cuda.get_device_name(0).replace(" ", "_")
+
+
+def _time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, out
+
+
+def tune(windows, mode="single", candidates=None, reps=3, log=print):
+    """Best knobs for windows of one geometry (synth.Window objects)."""
+    import torch
+    cand = dict(CANDIDATES)
+    if candidates:
+        cand.update(candidates)
+    w0 = windows[0]
+    evs = [dd.Events.of(w, device="cuda") for w in windows]
+    best, ref = None, None
+    grid = list(itertools.product(cand["band_rows"], cand["threads"], cand["pop_k"],
+                                  cand["max_splits"] if mode == "single" else [1]))
+    for rows, thr, k, ms in grid:
+        ctx = dd.Context(w0.W, w0.H, w0.foe_x, w0.foe_y, pop_k=k, band_rows=rows, threads=thr, max_splits=ms)
+        if mode == "single":
+            dt, out = _time(lambda: [ctx.solve(e) for e in evs], reps)
+            keys = [r["K_hat"] for r in out]
+            dt /= len(evs)
+        else:
+            dt, out = _time(lambda: ctx.solve_batch(evs), reps)
+            keys = [r["K_hat"] for r in out[1]]
+            dt /= len(evs)
+        ctx.close()
+        if ref is None:
+            ref = keys
+        assert keys == ref, "a schedule knob changed a result"
+        log("  rows=%3d threads=%4d pop_k=%2d max_splits=%2d: %.3f ms per window" % (rows, thr, k, ms, dt * 1e3))
+        if best is None or dt < best["ms_per_window"] / 1e3:
+            best = {"band_rows": rows, "threads": thr, "pop_k": k, "max_splits": ms, "ms_per_window": dt * 1e3}
+    torch.cuda.synchronize()
+    return best
+
+
+def load_table(path=DEFAULT_TABLE):
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(W, H, n_events, mode="single", path=DEFAULT_TABLE):
+    """Tuned knobs for this geometry and size on this GPU, or None."""
+    try:
+        name = gpu_name()
+    except Exception:
+        return None
+    entry = load_table(path).get(key(W, H, n_events, mode, name))
+    if not entry:
+        return None
+    return {k: entry[k] for k in ("band_rows", "threads", "pop_k", "max_splits")}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_TABLE)
+    ap.add_argument("--quick", action="store_true", help="fewer candidates")
+    args = ap.parse_args()
+    import torch
+    from synth import window_config1, window_config2
+    from synth.descent import batch_params3, batch_window3
+    torch.cuda.set_device(0)
+    name = gpu_name()
+    table = load_table(args.out)
+    cand = None
+    if args.quick:
+        cand = {"band_rows": [16, 38], "threads": [512, 1024], "pop_k": [16, 32], "max_splits": [8, 16]}
+    jobs = [("single", [window_config1()]), ("single", [window_config2()])]
+    params = batch_params3()
+    jobs.append(("batch", [batch_window3(i, params) for i in range(256)]))
+    for mode, ws in jobs:
+        n = int(sum(w.n for w in ws) / len(ws))
+        print("tuning %s %dx%d, %d windows of ~%d events" % (mode, ws[0].W, ws[0].H, len(ws), n), flush=True)
+        best = tune(ws, mode, cand)
+        best["windows"] = len(ws)
+        best["events_per_window"] = n
+        table[key(ws[0].W, ws[0].H, n, mode, name)] = best
+        print("  best:", best, flush=True)
+    with open(args.out + ".tmp", "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(args.out + ".tmp", args.out)
+
+
+if __name__ == "__main__":
+    main()

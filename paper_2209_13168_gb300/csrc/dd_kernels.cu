@@ -384,13 +384,12 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     const int all = erange[MAX_TB + g.n_tb];
     const int f_begin = (int)((long long)all * split / splits);
     const int total = (int)((long long)all * (split + 1) / splits);
-    // Event index of position f of the concatenated runs.
+    // Event index of position f of the concatenated runs.  Each thread visits
+    // increasing positions, so its bucket cursor only moves forward.
+    int cur_b = 0;
     auto event_at = [&](int f) {
-        int b = 0;
-#pragma unroll
-        for (int q = 1; q < MAX_TB; q++)
-            if (q < g.n_tb && f >= erange[MAX_TB + q]) b = q;
-        return erange[b] + (f - erange[MAX_TB + b]);
+        while (cur_b + 1 < g.n_tb && f >= erange[MAX_TB + cur_b + 1]) cur_b++;
+        return erange[cur_b] + (f - erange[MAX_TB + cur_b]);
     };
 
     if (tk.kind == TASK_POINT) {
