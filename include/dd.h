@@ -52,7 +52,9 @@ enum {
     DD_ERR_TIMEOUT = -4,        /* the round limit was reached before the proof  */
     DD_ERR_CUDA = -5,           /* a CUDA runtime call failed                    */
     DD_ERR_NO_DEVICE = -6,      /* no usable sm_103 device                       */
-    DD_ERR_CAPACITY = -7        /* input exceeds dd_contrast_noalloc's fixed scratch */
+    DD_ERR_CAPACITY = -7,       /* input exceeds a fixed capacity (no-alloc scratch, */
+                                /* serving slot)                                     */
+    DD_PENDING = 1              /* dd_serve_poll: the request has not finished yet   */
 };
 
 typedef struct dd_ctx dd_ctx;
@@ -204,6 +206,56 @@ int dd_reset_stats(dd_ctx* ctx);
  * context's stream and add its duration to dd_stats.eval_ms (costs a few
  * microseconds per launch; off by default). */
 int dd_set_timing(dd_ctx* ctx, int32_t enable);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of windows from concurrent event streams
+ * (the stream-wise estimation of Sec. 4.4, one estimate per window).
+ *
+ * A server owns max_slots device slots, each holding one window of up to
+ * max_events events with its whole search state, and one host thread that
+ * loops: admit every request whose arrival time has passed into a free slot
+ * (copy in, ingest, start its search), run one BnB round for every busy slot
+ * in shared launches, retire finished windows.  Requests join and leave
+ * between rounds while others are running; each window's result is the same
+ * as dd_solve on it alone with the context's pop_k.  The server uses the
+ * context's geometry and knobs but its own buffers and stream.
+ */
+typedef struct dd_server dd_server;
+
+/* Start a server.  max_slots = 0 picks the slot count from free device
+ * memory (at most half of it, at most 64 slots).  Errors: DD_ERR_ARG,
+ * DD_ERR_OOM, DD_ERR_CUDA. */
+int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server** out);
+
+/* The server's slot count and per-slot event capacity. */
+int dd_serve_slots(dd_server* s, int32_t* slots, int64_t* max_events);
+
+/* Queue one window (events and search parameters) that arrives at
+ * arrival_s on the dd_serve_clock() scale (negative: now); it is admitted no
+ * earlier than that.  The event arrays (host or device, ev->device_ptrs) must
+ * stay valid and unchanged until the request finishes.  Writes a ticket.
+ * Errors: DD_ERR_ARG, DD_ERR_CAPACITY (ev->n > max_events), a previous
+ * DD_ERR_CUDA of the server. */
+int dd_serve_submit(dd_server* s, const dd_events* ev, const dd_window_params* p, double arrival_s,
+                    uint64_t* ticket);
+
+/* DD_PENDING while the request runs or waits; otherwise its status (results
+ * and latency = finish time - arrival time, in seconds, written when not
+ * NULL), and the ticket is released. */
+int dd_serve_poll(dd_server* s, uint64_t ticket, dd_result* out, double* latency_s);
+
+/* As dd_serve_poll, but blocks until the request has finished. */
+int dd_serve_wait(dd_server* s, uint64_t ticket, dd_result* out, double* latency_s);
+
+/* Rounds run, requests admitted and the largest number of windows that
+ * shared a round, since dd_serve_start. */
+int dd_serve_stats(dd_server* s, int64_t* rounds, int64_t* admitted, int64_t* peak_busy);
+
+/* Finish every queued request, stop the loop thread and free the server. */
+int dd_serve_stop(dd_server* s);
+
+/* The serving clock: seconds on a monotonic clock. */
+double dd_serve_clock(void);
 
 /* ------------------------------------------------------------------------
  * Allocation-free contrast evaluation.  The paper has no counterpart: this

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libdd.so")
 DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_NO_DEVICE = \
     0, -1, -2, -3, -4, -5, -6
 DD_ERR_CAPACITY = -7
+DD_PENDING = 1
 DD_NOALLOC_MAX_EVENTS = 1 << 20
 
 
@@ -98,6 +99,15 @@ SIGNATURES = {
     "dd_solve_trace": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_double, _P(dd_result), _VP, ctypes.c_int64, _P(ctypes.c_int64)]),
     "dd_solve_batch": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, _P(dd_window_params), _P(dd_result)]),
+    "dd_serve_start": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64, _P(_VP)]),
+    "dd_serve_slots": (ctypes.c_int, [_VP, _P(ctypes.c_int32), _P(ctypes.c_int64)]),
+    "dd_serve_submit": (ctypes.c_int, [_VP, _P(dd_events), _P(dd_window_params), ctypes.c_double,
+                                       _P(ctypes.c_uint64)]),
+    "dd_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(dd_result), _P(ctypes.c_double)]),
+    "dd_serve_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(dd_result), _P(ctypes.c_double)]),
+    "dd_serve_stats": (ctypes.c_int, [_VP, _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "dd_serve_stop": (ctypes.c_int, [_VP]),
+    "dd_serve_clock": (ctypes.c_double, []),
     "dd_get_stats": (ctypes.c_int, [_VP, _P(dd_stats)]),
     "dd_reset_stats": (ctypes.c_int, [_VP]),
     "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -272,6 +282,61 @@ def dd_contrast_noalloc(W, H, foe_x, foe_y, ev, D, stream_ptr=None):
                                       ctypes.cast(K, _VP), _VP(stream_ptr) if stream_ptr else None),
            "dd_contrast_noalloc")
     return [K[i].value() for i in range(n)]
+
+
+class Server:
+    """Continuous-batching server over a Context's geometry (dd_serve_*)."""
+
+    def __init__(self, ctx, max_slots=0, max_events=1 << 20):
+        h = _VP()
+        _check(load().dd_serve_start(ctx.h, max_slots, max_events, ctypes.byref(h)), "dd_serve_start")
+        self.h = h
+        self._keep = {}
+        s, e = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().dd_serve_slots(h, ctypes.byref(s), ctypes.byref(e)), "dd_serve_slots")
+        self.slots, self.max_events = s.value, e.value
+
+    @staticmethod
+    def clock():
+        return load().dd_serve_clock()
+
+    def submit(self, ev, params=(-1.0, 1.0, 1e-4, 0.0), arrival=-1.0):
+        t = ctypes.c_uint64()
+        p = dd_window_params(params[0], params[1], params[2], 0, params[3])
+        _check(load().dd_serve_submit(self.h, ctypes.byref(ev.c), ctypes.byref(p), float(arrival), ctypes.byref(t)),
+               "dd_serve_submit")
+        self._keep[t.value] = ev            # the arrays must outlive the request
+        return t.value
+
+    def _take(self, fn, ticket):
+        r, lat = dd_result(), ctypes.c_double()
+        rc = fn(self.h, ticket, ctypes.byref(r), ctypes.byref(lat))
+        if rc == DD_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        if rc != DD_OK:
+            raise DDError(rc, "serve request %d" % ticket)
+        d = r.as_dict()
+        d["latency_s"] = lat.value
+        return d
+
+    def poll(self, ticket):
+        return self._take(load().dd_serve_poll, ticket)
+
+    def wait(self, ticket):
+        return self._take(load().dd_serve_wait, ticket)
+
+    def stats(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().dd_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "dd_serve_stats")
+        return {"rounds": a.value, "admitted": b.value, "peak_busy": c.value}
+
+    def stop(self):
+        if self.h:
+            rc = load().dd_serve_stop(self.h)
+            self.h = None
+            self._keep.clear()
+            _check(rc, "dd_serve_stop")
 
 
 class Context:

@@ -535,6 +535,20 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
 
 }  // namespace
 
+namespace dd {
+void ctx_info(const ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks, int32_t* pop_k,
+              int32_t* queue_capacity, int64_t* max_rounds) {
+    *g = c->g;
+    *threads = c->threads;
+    *eval_blocks = c->eval_blocks;
+    *max_tasks = c->max_tasks;
+    *pop_k = c->cfg.pop_k;
+    *queue_capacity = c->cfg.queue_capacity;
+    *max_rounds = c->cfg.max_rounds;
+}
+cudaStream_t ctx_stream(const ::dd_ctx* c) { return c->stream; }
+}  // namespace dd
+
 extern "C" {
 
 const char* dd_strerror(int status) {

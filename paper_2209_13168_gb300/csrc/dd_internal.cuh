@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct dd_ctx;
+
 namespace dd {
 
 typedef __int128 i128;
@@ -168,13 +170,23 @@ int eval_resident_blocks(const Geom& g, int threads);
 cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part, i128* key,
                         unsigned long long* S, unsigned long long* cells, unsigned long long* full,
                         cudaStream_t s);
+// Windows w0 .. w0 + n_windows - 1 start a search; split_ok < 0: split bound
+// tasks only when n_windows == 1.
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
                         const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
-                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s);
+                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s,
+                        int32_t w0 = 0, int32_t split_ok = -1);
+// One control block per window 0 .. n_windows - 1; phase_out (nullable)
+// receives each window's phase after the round.
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
                            int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
-                           int32_t use_loop, cudaStream_t s);
+                           int32_t use_loop, cudaStream_t s, int32_t split_ok = -1, int32_t* phase_out = nullptr);
+
+// Context accessors for the serving engine (dd_serve.cu).
+void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks,
+              int32_t* pop_k, int32_t* queue_capacity, int64_t* max_rounds);
+cudaStream_t ctx_stream(const struct ::dd_ctx* c);
 cudaError_t eval_smem_setup(const Geom& g);
 
 }  // namespace dd

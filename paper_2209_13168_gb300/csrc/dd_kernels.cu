@@ -658,13 +658,18 @@ __device__ __forceinline__ float centre(float lo, float hi) {
     return __fadd_rn(lo, __fmul_rn(0.5f, __fsub_rn(hi, lo)));
 }
 
-// One block per window: the search state, the round-0 tasks (the centre of
-// the domain and the bound of the domain) and their jobs in list 0.
-__global__ void k_init(Geom g, int32_t n_windows, SolveState* st_all, Task* tasks_all, int32_t task_stride,
-                       const WinIn* wins, const WinParams* params, Job* jobs, Sched* sch, int32_t K_pop,
-                       int32_t qcap, int64_t max_rounds, int32_t trace_cap) {
+// One block per window w0 + b: the search state, the first tasks (the centre
+// of the domain and the bound of the domain) and their jobs in the list the
+// next evaluation reads.  `split_ok`: bound tasks may be split (single-window
+// searches).
+__global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all, Task* tasks_all,
+                       int32_t task_stride, const WinIn* wins, const WinParams* params, Job* jobs_all,
+                       int32_t job_stride, Sched* sch, int32_t K_pop, int32_t qcap, int64_t max_rounds,
+                       int32_t trace_cap) {
     if (threadIdx.x != 0) return;
-    const int w = blockIdx.x;
+    const int w = w0 + blockIdx.x;
+    const int par = sch->round & 1;
+    Job* jobs = jobs_all + (size_t)par * job_stride;
     SolveState* st = st_all + w;
     Task* tasks = tasks_all + (size_t)w * task_stride;
     const WinParams pr = params[w];
@@ -700,11 +705,11 @@ __global__ void k_init(Geom g, int32_t n_windows, SolveState* st_all, Task* task
     b.D_lo = pr.D_lo;                             // bound of the domain (queued first)
     b.D_hi = pr.D_hi;
     b.kind = TASK_BOUND;
-    b.splits = n_windows == 1 ? bound_splits(g, pr.D_lo, pr.D_hi, tau) : 1;
+    b.splits = split_ok ? bound_splits(g, pr.D_lo, pr.D_hi, tau) : 1;
     tasks[0] = a;
     tasks[1] = b;
     st->n_tasks = 2;
-    const int base = atomicAdd(&sch->n_jobs[0], 1 + b.splits);
+    const int base = atomicAdd(&sch->n_jobs[par], 1 + b.splits);
     for (int s = 0; s < b.splits; s++) {
         Job j;
         j.win = w;
@@ -723,10 +728,11 @@ __global__ void k_init(Geom g, int32_t n_windows, SolveState* st_all, Task* task
 
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
                         const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
-                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s) {
-    (void)job_stride;
-    k_init<<<n_windows, 32, 0, s>>>(g, n_windows, st, tasks, task_stride, wins, params, jobs, sch, K_pop, qcap,
-                                    max_rounds, trace_cap);
+                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s,
+                        int32_t w0, int32_t split_ok) {
+    if (split_ok < 0) split_ok = n_windows == 1;
+    k_init<<<n_windows, 32, 0, s>>>(g, split_ok, w0, st, tasks, task_stride, wins, params, jobs, job_stride, sch,
+                                    K_pop, qcap, max_rounds, trace_cap);
     return cudaGetLastError();
 }
 
@@ -778,7 +784,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                                                         const Partial* part_all, const int32_t* err_all,
                                                         TraceRec* trace, Job* jobs_all, int32_t job_stride,
                                                         Sched* sch, cudaGraphConditionalHandle loop,
-                                                        int32_t use_loop) {
+                                                        int32_t use_loop, int32_t split_ok, int32_t* phase_out) {
     __shared__ SolveState s;
     __shared__ i128 key[3 * MAX_POP];
     __shared__ unsigned long long cells[3 * MAX_POP];
@@ -1052,11 +1058,11 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                         l.D_lo = p.lo;
                         l.D_hi = p.c;
                         l.kind = TASK_BOUND;
-                        l.splits = n_windows == 1 ? bound_splits(g, p.lo, p.c, s.tau) : 1;
+                        l.splits = split_ok ? bound_splits(g, p.lo, p.c, s.tau) : 1;
                         r.D_lo = p.c;
                         r.D_hi = p.hi;
                         r.kind = TASK_BOUND;
-                        r.splits = n_windows == 1 ? bound_splits(g, p.c, p.hi, s.tau) : 1;
+                        r.splits = split_ok ? bound_splits(g, p.c, p.hi, s.tau) : 1;
                         tasks[t] = l;
                         tasks[t + 1] = r;
                     } else {
@@ -1113,6 +1119,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         reinterpret_cast<int4*>(st)[i] = reinterpret_cast<const int4*>(&s)[i];
     } // s.phase != PH_DONE at entry
     __syncthreads();
+    if (tid == 0 && phase_out) phase_out[w] = s.phase;
     if (tid == 0) {
         __threadfence();
         if (s.phase != PH_DONE) atomicAdd(&sch->active, 1);
@@ -1131,9 +1138,10 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
                            int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
-                           int32_t use_loop, cudaStream_t s) {
+                           int32_t use_loop, cudaStream_t s, int32_t split_ok, int32_t* phase_out) {
+    if (split_ok < 0) split_ok = n_windows == 1;
     k_control<<<n_windows, CTL_THREADS, 0, s>>>(g, n_windows, st, queues, tasks, task_stride, part, err, trace, jobs,
-                                                job_stride, sch, loop, use_loop);
+                                                job_stride, sch, loop, use_loop, split_ok, phase_out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,88 @@
+"""Serving: continuous batching gives each window the result it gets alone.
+
+Windows of several descents (the 1280x720 descent recipe at reduced event
+counts) arrive at staggered times; the server admits them into free slots
+between rounds, so they share evaluation launches with whatever else is in
+flight.  Every result must be bit-identical to a single-window solve (same
+pop width), and a sample to the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import serve_config5
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2209_13168_gb300 as dd  # noqa: E402
+
+KEYS = ("D_star", "D_end", "K_hat", "gap_K", "nodes_expanded", "point_evals", "bound_evals", "event_warps",
+        "cell_increments", "bound_increments", "rounds", "max_queue")
+PARAMS = (-1.0, 2.0, 1e-4, 0.0)
+
+
+def windows(streams=3, per_stream=5, scale=0.02):
+    return [serve_config5(s, 20 + 30 * w, n_scale=scale) for s in range(streams) for w in range(per_stream)]
+
+
+def test_mixed_arrivals_match_solo_solves():
+    ws = windows()
+    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=8)
+    solo = [ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS) for w in ws]
+    srv = dd.Server(ctx, max_slots=4, max_events=1 << 16)
+    t0 = dd.Server.clock() + 0.01
+    evs = [dd.Events.of(w, device="cuda" if i % 2 else None) for i, w in enumerate(ws)]
+    tickets = [srv.submit(e, PARAMS, t0 + 0.002 * i) for i, e in enumerate(evs)]
+    got = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.stop()
+    for a, b in zip(got, solo):
+        for k in KEYS:
+            assert a[k] == b[k], k
+        assert a["latency_s"] >= 0.0
+    assert st["admitted"] == len(ws) and 1 <= st["peak_busy"] <= 4
+    for i in (0, 7):
+        want = O.solve(O.Window.of(ws[i]), *PARAMS, 8)
+        assert got[i]["K_hat"] == want["K_hat"] and got[i]["nodes_expanded"] == want["nodes_expanded"]
+    ctx.close()
+
+
+def test_burst_waits_for_slots():
+    ws = windows(streams=2, per_stream=4, scale=0.01)
+    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=4)
+    srv = dd.Server(ctx, max_slots=2, max_events=1 << 15)
+    tickets = [srv.submit(dd.Events.of(w, device="cuda"), PARAMS) for w in ws]
+    got = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.stop()
+    assert st["peak_busy"] <= 2 and st["admitted"] == len(ws)
+    for w, r in zip(ws, got):
+        one = ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS)
+        for k in KEYS:
+            assert r[k] == one[k], k
+    ctx.close()
+
+
+def test_capacity_and_malformed_windows():
+    ws = windows(streams=1, per_stream=3, scale=0.01)
+    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=4)
+    srv = dd.Server(ctx, max_slots=2, max_events=int(max(w.n for w in ws)))
+    big = serve_config5(0, 150, n_scale=0.05)
+    with pytest.raises(dd.DDError) as e:
+        srv.submit(dd.Events.of(big, device="cuda"), PARAMS)
+    assert e.value.status == dd.DD_ERR_CAPACITY
+    ws[1].t[5] = np.float32(1.0)                 # outside its 0.2 s window
+    tickets = [srv.submit(dd.Events.of(w, device="cuda"), PARAMS) for w in ws]
+    r0 = srv.wait(tickets[0])
+    with pytest.raises(dd.DDError) as e:
+        srv.wait(tickets[1])
+    assert e.value.status == dd.DD_ERR_ARG
+    r2 = srv.wait(tickets[2])
+    srv.stop()
+    for w, r in ((ws[0], r0), (ws[2], r2)):
+        assert r["K_hat"] == ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS)["K_hat"]
+    ctx.close()
