@@ -205,7 +205,10 @@ class Events:
 
     @classmethod
     def of(cls, w, device=None):
-        """From a synth.Window; device='cuda' uploads the SoA as torch tensors."""
+        """From a synth.Window (numpy arrays, or torch CUDA tensors already on the
+        device); device='cuda' uploads numpy arrays as torch tensors."""
+        if hasattr(w.x, "is_cuda") and w.x.is_cuda:
+            return cls(w.x, w.y, w.t, w.t0, w.tau)
         if device is None:
             return cls(w.x, w.y, w.t, w.t0, w.tau)
         import torch

@@ -148,13 +148,17 @@ def batch_params3(n_windows=256, seed=3000):
     return n, D, noise, tau
 
 
-def batch_window3(i, params, seed=3000, W=640, H=480):
+def batch_spec3(i, params, seed=3000, W=640, H=480):
+    """make_window arguments of window i of the uneven batch."""
     n, D, noise, tau = params
     N = int(n[i])
     n_noise = int(round(N * float(noise[i])))
     n_sig = N - n_noise
-    return make_window(W, H, W / 2.0, H / 2.0, n_sig, max(1, n_sig // 35), n_noise, float(D[i]),
-                       float(tau[i]), seed + 1 + i)
+    return (W, H, W / 2.0, H / 2.0, n_sig, max(1, n_sig // 35), n_noise, float(D[i]), float(tau[i]), seed + 1 + i)
+
+
+def batch_window3(i, params, seed=3000, W=640, H=480):
+    return make_window(*batch_spec3(i, params, seed, W, H))
 
 
 def batch_config3(n_windows=256, seed=3000):
@@ -163,16 +167,18 @@ def batch_config3(n_windows=256, seed=3000):
     return [batch_window3(i, params, seed) for i in range(n_windows)]
 
 
-def serve_config5(stream, w, n_scale=1.0):
-    """Window w (t_w = 0.1 w) of descent `stream` at 1280x720: D = 1/(20 - t_w).
-
-    N rises linearly with D from 50k (D=0.05) to 1M (D=1.0); 15% noise; tau=0.2.
-    `n_scale` shrinks N for small test cases.
-    """
+def serve_spec5(stream, w, n_scale=1.0):
+    """make_window arguments of window w (t_w = 0.1 w) of descent `stream` at
+    1280x720: D = 1/(20 - t_w); N rises linearly with D from 50k (D=0.05) to
+    1M (D=1.0); 15% noise; tau=0.2.  `n_scale` shrinks N for small cases."""
     tw = 0.1 * w
     D = 1.0 / (20.0 - tw)
     N = int((50_000 + (1_000_000 - 50_000) * (D - 0.05) / 0.95) * n_scale)
     n_noise = int(round(0.15 * N))
     n_sig = N - n_noise
-    return make_window(1280, 720, 640.0, 360.0, n_sig, max(1, n_sig // 35), n_noise, D, 0.2,
-                       5000 + 1000 * stream + w)
+    return (1280, 720, 640.0, 360.0, n_sig, max(1, n_sig // 35), n_noise, D, 0.2, 5000 + 1000 * stream + w)
+
+
+def serve_config5(stream, w, n_scale=1.0):
+    """Window w of descent `stream` of the serving workload (serve_spec5)."""
+    return make_window(*serve_spec5(stream, w, n_scale))

@@ -1,0 +1,70 @@
+"""Synthetic windows generated on the GPU (synth/gen.cu), for workloads too
+large to generate with numpy in reasonable time.  Same windows as
+synth.descent.make_window (event order aside); tests/test_synth_gpu.py
+checks that."""
+import ctypes
+import os
+import subprocess
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.cu")
+_LIB = os.path.join(_HERE, "libsynth.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile gen.cu into libsynth.so (binary64 without FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    nvcc = "nvcc" if subprocess.run(["which", "nvcc"], capture_output=True).returncode == 0 else "/usr/local/cuda/bin/nvcc"
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false", "-shared",
+                           "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.synth_window_gpu.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+        L.synth_window_gpu.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class GpuWindow:
+    """A window whose SoA events live in torch CUDA tensors."""
+
+    def __init__(self, spec, x, y, t):
+        (self.W, self.H, self.foe_x, self.foe_y, self.n_signal, self.n_points, self.n_noise, self.D_true,
+         tau, self.seed) = spec
+        import numpy as np
+        self.tau = float(np.float32(tau))
+        self.t0 = 0.0
+        self.x, self.y, self.t = x, y, t
+
+    @property
+    def n(self):
+        return int(self.x.shape[0])
+
+
+def make_window_gpu(spec, device="cuda", stream=None):
+    """Generate make_window(*spec) on the GPU; returns a GpuWindow."""
+    import torch
+    W, H, fx, fy, n_sig, n_pts, n_noise, D, tau, seed = spec
+    n = int(n_sig) + int(n_noise)
+    x = torch.empty(n, dtype=torch.int16, device=device)
+    y = torch.empty(n, dtype=torch.int16, device=device)
+    t = torch.empty(n, dtype=torch.float32, device=device)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = lib().synth_window_gpu(int(W), int(H), float(fx), float(fy), int(n_sig), int(n_pts), int(n_noise), float(D),
+                                float(tau), int(seed), x.data_ptr(), y.data_ptr(), t.data_ptr(), s)
+    if rc != 0:
+        raise RuntimeError("synth_window_gpu failed (%d)" % rc)
+    return GpuWindow(spec, x, y, t)
