@@ -10,7 +10,13 @@ What each function follows (paper: McLeod et al., arXiv 2209.13168):
   scale, scale_interval  the warp scale and the bound's widened scale range
   contrast        Eqs. (12)-(13) as the integer key K = M*S - N_in^2 = M^2 C
   bound           Eqs. (14)-(19) as Kbar = M*Sbar - N_full^2 >= K(D)
-  solve           Algorithm 1 (pop-K rounds; K_pop = 1 is Algorithm 1 itself)
+  solve           Algorithm 1 (pop-K rounds; K_pop = 1 is Algorithm 1 itself),
+                  optionally warm-started from a guess D_warm +- w_warm
+  features        the warm start's 16 radial x 8 temporal count histogram
+  mlp_forward_f32 the warm start network in binary32, the device's order
+  mlp_forward_f64, mlp_loss_f64  the same network in binary64, its training
+                  loss and backprop gradient
+  warm_map        network outputs -> (D_warm, w_warm)
   grid_max        exhaustive dense grid (brute force)
   sweep_max       exact breakpoint sweep (brute force)
   fp64_disagreements  the same warp in binary64, diagnostic only
@@ -97,6 +103,20 @@ def lib():
         L.or_solve.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_double,
                                ctypes.c_int32, P(_Res), ctypes.c_void_p, ctypes.c_int64,
                                P(ctypes.c_int64)]
+        L.or_solve_warm.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_double,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, P(_Res),
+                                    ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_int64)]
+        L.or_features.argtypes = [P(_Win), ctypes.c_void_p, ctypes.c_void_p]
+        L.or_mlp_forward_f32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_mlp_forward_f32.restype = None
+        L.or_mlp_forward_f64.argtypes = [ctypes.c_void_p] * 5
+        L.or_mlp_forward_f64.restype = None
+        L.or_mlp_loss_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_void_p]
+        L.or_mlp_loss_f64.restype = ctypes.c_double
+        L.or_warm_map.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, P(ctypes.c_float),
+                                  P(ctypes.c_float)]
+        L.or_warm_map.restype = None
         L.or_grid_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, P(_I128),
                                   P(ctypes.c_float), P(ctypes.c_int64)]
         L.or_sweep_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, P(_I128), P(ctypes.c_float),
@@ -180,13 +200,15 @@ def bound(win, D_lo, D_hi, want_iwe=False):
     return k.value(), int(s.value), int(n.value), (img.reshape(win.H, win.W) if want_iwe else None)
 
 
-def solve(win, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, K_pop=1, trace_cap=0):
+def solve(win, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, K_pop=1, trace_cap=0, warm=None):
+    """Algorithm 1; warm = (D_warm, w_warm) starts it from a guess."""
     r = _Res()
     tr = (_Rec * trace_cap)() if trace_cap else None
     tl = ctypes.c_int64(0)
-    _check(lib().or_solve(ctypes.byref(win.c), D_lo, D_hi, tol_D, gamma, K_pop, ctypes.byref(r),
-                          ctypes.cast(tr, ctypes.c_void_p) if tr is not None else None, trace_cap,
-                          ctypes.byref(tl)))
+    wf, wd, ww = (0, 0.0, 0.0) if warm is None else (1, float(warm[0]), float(warm[1]))
+    _check(lib().or_solve_warm(ctypes.byref(win.c), D_lo, D_hi, tol_D, gamma, K_pop, wf, wd, ww, ctypes.byref(r),
+                               ctypes.cast(tr, ctypes.c_void_p) if tr is not None else None, trace_cap,
+                               ctypes.byref(tl)))
     out = {f: getattr(r, f) for f, _ in _Res._fields_ if f not in ("K_hat", "gap_K")}
     out["K_hat"] = r.K_hat.value()
     out["gap_K"] = r.gap_K.value()
@@ -210,3 +232,54 @@ def sweep_max(win, D_lo, D_hi):
     _check(lib().or_sweep_max(ctypes.byref(win.c), D_lo, D_hi, ctypes.byref(k), ctypes.byref(d),
                               ctypes.byref(n)))
     return k.value(), d.value, n.value
+
+
+# ------------------------------------------------------ learned warm start
+N_FEATURES = 128
+N_HIDDEN = 128
+N_PARAMS = 128 * 128 + 128 + 128 * 128 + 128 + 2 * 128 + 2
+# offsets of W1 b1 W2 b2 W3 b3 in the parameter vector ([out][in] matrices)
+OFFSETS = {"W1": 0, "b1": 16384, "W2": 16512, "b2": 32896, "W3": 33024, "b3": 33280}
+
+
+def features(win):
+    """(features float32[128], counts int64[128]); bin index = 8 * radial + temporal."""
+    f = np.zeros(N_FEATURES, np.float32)
+    c = np.zeros(N_FEATURES, np.int64)
+    _check(lib().or_features(ctypes.byref(win.c), f.ctypes.data, c.ctypes.data))
+    return f, c
+
+
+def mlp_forward_f32(params, x):
+    p = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    o = np.zeros(2, np.float32)
+    lib().or_mlp_forward_f32(p.ctypes.data, x.ctypes.data, o.ctypes.data)
+    return o
+
+
+def mlp_forward_f64(params, x):
+    """(h1, h2, out) in binary64."""
+    p = np.ascontiguousarray(params, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    h1, h2, o = np.zeros(N_HIDDEN), np.zeros(N_HIDDEN), np.zeros(2)
+    lib().or_mlp_forward_f64(p.ctypes.data, x.ctypes.data, h1.ctypes.data, h2.ctypes.data, o.ctypes.data)
+    return h1, h2, o
+
+
+def mlp_loss_f64(params, X, u_star, want_grad=True):
+    """(mean loss, gradient or None) over the samples X[B][128] with targets u_star[B]."""
+    p = np.ascontiguousarray(params, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, N_FEATURES)
+    u = np.ascontiguousarray(u_star, np.float64)
+    g = np.zeros(N_PARAMS) if want_grad else None
+    loss = lib().or_mlp_loss_f64(p.ctypes.data, X.ctypes.data, u.ctypes.data, X.shape[0],
+                                 g.ctypes.data if want_grad else None)
+    return float(loss), g
+
+
+def warm_map(u, l, tau):
+    """(D_warm, w_warm) from the network outputs (u = D tau guess, l = log half-width)."""
+    d, w = ctypes.c_float(), ctypes.c_float()
+    lib().or_warm_map(u, l, tau, ctypes.byref(d), ctypes.byref(w))
+    return d.value, w.value

@@ -323,10 +323,42 @@ static float centre(float lo, float hi) { return lo + 0.5f * (hi - lo); }
  * stopped the search) - K_hat). */
 int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
              or_result* out, or_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
+    return or_solve_warm(w, D_lo, D_hi, tol_D, gamma, K_pop, 0, 0.0f, 0.0f, out, trace, trace_cap, trace_len);
+}
+
+/* The root pieces of a warm start at D_warm +- w_warm: the guess is clamped
+ * into the domain, the cuts a = D0 - w, b = D0 + w (binary32) are clamped to
+ * the domain, and the domain is cut at them into up to three intervals of
+ * positive width, in increasing D.  Returns the number of pieces. */
+static int warm_pieces(float D_lo, float D_hi, float D_warm, float w_warm, float* D0, node* piece) {
+    float d = D_warm;
+    if (!(d >= D_lo)) d = D_lo;                  /* also catches NaN */
+    if (d > D_hi) d = D_hi;
+    float a = d - w_warm, b = d + w_warm;
+    if (!(a >= D_lo)) a = D_lo;
+    if (!(b <= D_hi)) b = D_hi;
+    float cut[4] = {D_lo, a, b, D_hi};
+    int n = 0;
+    for (int i = 0; i < 3; i++)
+        if (cut[i] < cut[i + 1]) {
+            piece[n].lo = cut[i];
+            piece[n].hi = cut[i + 1];
+            piece[n].kb = 0;
+            n++;
+        }
+    *D0 = d;
+    return n;
+}
+
+int or_solve_warm(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
+                  int32_t warm, float D_warm, float w_warm, or_result* out, or_node_rec* trace,
+                  int64_t trace_cap, int64_t* trace_len) {
     int rc = or_validate(w, D_lo, D_hi);
     if (rc) return rc;
     if (!out || K_pop < 1 || !(D_lo < D_hi) || !(tol_D >= 0.0f) || !isfinite(tol_D) || !(gamma >= 0.0) ||
         !isfinite(gamma))
+        return OR_ERR_ARG;
+    if (warm != 0 && (warm != 1 || !isfinite(D_warm) || !isfinite(w_warm) || !(w_warm > 0.0f)))
         return OR_ERR_ARG;
     const int64_t M = (int64_t)w->W * w->H;
     const i128 gamma_K = (i128)floor(gamma * (double)M * (double)M);
@@ -346,18 +378,41 @@ int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gam
     uint64_t S;
     int64_t N;
 
-    float D_hat = centre(D_lo, D_hi);                         /* init: incumbent */
-    i128 K_hat = eval_point(w, D_hat, img, &S, &N);
-    r.point_evals = 1;
-    cells += N;
-    node root = {D_lo, D_hi, 0};                              /* init: queue */
     int64_t nf, nc;
-    root.kb = eval_bound(w, D_lo, D_hi, img, &S, &nf, &nc);
-    r.bound_evals = 1;
-    cells += nc;
-    bcells += nc;
-    if ((rc = q_push(&q, root))) goto done;
-    r.max_queue = 1;
+    float D_hat;
+    i128 K_hat;
+    if (!warm) {
+        D_hat = centre(D_lo, D_hi);                           /* init: incumbent */
+        K_hat = eval_point(w, D_hat, img, &S, &N);
+        r.point_evals = 1;
+        cells += N;
+        node root = {D_lo, D_hi, 0};                          /* init: queue */
+        root.kb = eval_bound(w, D_lo, D_hi, img, &S, &nf, &nc);
+        r.bound_evals = 1;
+        cells += nc;
+        bcells += nc;
+        if ((rc = q_push(&q, root))) goto done;
+    } else {
+        /* Warm start: the guess replaces the centre as the first incumbent,
+         * and the domain enters the queue as the pieces around the guess;
+         * a piece is queued when its bound reaches the incumbent, as
+         * children are (the piece holding the guess always is). */
+        node piece[3];
+        const int np0 = warm_pieces(D_lo, D_hi, D_warm, w_warm, &D_hat, piece);
+        K_hat = eval_point(w, D_hat, img, &S, &N);
+        r.point_evals = 1;
+        cells += N;
+        for (int i = 0; i < np0; i++) {
+            piece[i].kb = eval_bound(w, piece[i].lo, piece[i].hi, img, &S, &nf, &nc);
+            r.bound_evals++;
+            cells += nc;
+            bcells += nc;
+        }
+        for (int i = 0; i < np0; i++)
+            if (piece[i].kb >= K_hat)
+                if ((rc = q_push(&q, piece[i]))) goto done;
+    }
+    r.max_queue = q.n;
 
     int have_leaf = 0, have_stop = 0;
     i128 leaf_max = 0, stop_kb = 0;
@@ -553,4 +608,155 @@ int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, flo
     *D_at = bd;
     if (n_evals) *n_evals = ne;
     return OR_OK;
+}
+
+/* ------------------------------------------------- learned warm start */
+
+/* Input features of the learned warm start: event counts in 16 radial x 8
+ * temporal bins, divided by the window's event count.  The radius is the
+ * event's distance from the FOE relative to R, the largest distance from the
+ * FOE to a corner pixel centre; radial bin floor(16 r / R) (at most 15).
+ * The temporal bin is floor(8 (t - t0) / tau) (at most 7).  Every step is
+ * one binary32 operation in the order written (sqrtf and the divisions are
+ * correctly rounded), so the bins are decided in binary32. */
+int or_features(const or_window* w, float* f, int64_t* counts) {
+    int rc = or_validate(w, 0.0f, 0.0f);
+    if (rc) return rc;
+    int64_t c[OR_FEATURES];
+    memset(c, 0, sizeof(c));
+    const float ax = w->foe_x, bx = (float)(w->W - 1) - w->foe_x;
+    const float ay = w->foe_y, by = (float)(w->H - 1) - w->foe_y;
+    const float cx = ax > bx ? ax : bx, cy = ay > by ? ay : by;
+    const float R2 = cx * cx + cy * cy;
+    const float tsc = (float)OR_FEAT_T / w->tau;
+    for (int64_t i = 0; i < w->n; i++) {
+        const float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
+        const float r2 = dx * dx + dy * dy;
+        const float u = R2 > 0.0f ? r2 / R2 : 0.0f;
+        int rb = (int)floorf(sqrtf(u) * (float)OR_FEAT_R);
+        if (rb > OR_FEAT_R - 1) rb = OR_FEAT_R - 1;
+        const float v = (w->t[i] - w->t0) * tsc;
+        int tb = (int)floorf(v);
+        if (tb < 0) tb = 0;
+        if (tb > OR_FEAT_T - 1) tb = OR_FEAT_T - 1;
+        c[rb * OR_FEAT_T + tb]++;
+    }
+    for (int k = 0; k < OR_FEATURES; k++) {
+        if (f) f[k] = w->n > 0 ? (float)c[k] / (float)w->n : 0.0f;
+        if (counts) counts[k] = c[k];
+    }
+    return OR_OK;
+}
+
+/* Parameter vector of the network 128 -> 128 -> 128 -> 2 (ReLU after the two
+ * hidden layers), weight matrices row-major [out][in]:
+ *   W1[128][128] b1[128] W2[128][128] b2[128] W3[2][128] b3[2]. */
+enum {
+    P_W1 = 0,
+    P_B1 = P_W1 + OR_MLP_H * OR_FEATURES,
+    P_W2 = P_B1 + OR_MLP_H,
+    P_B2 = P_W2 + OR_MLP_H * OR_MLP_H,
+    P_W3 = P_B2 + OR_MLP_H,
+    P_B3 = P_W3 + OR_MLP_OUT * OR_MLP_H,
+    P_END = P_B3 + OR_MLP_OUT
+};
+
+/* The network in binary32 as the device evaluates it: each unit starts from
+ * its bias and adds weight * input for inputs 0, 1, ..., 127 in turn (one
+ * rounded product, one rounded sum), then the ReLU. */
+static void dense_f32(const float* Wt, const float* b, const float* x, int n_in, int n_out, int relu, float* y) {
+    for (int j = 0; j < n_out; j++) {
+        float acc = b[j];
+        for (int k = 0; k < n_in; k++) acc = acc + Wt[j * n_in + k] * x[k];
+        y[j] = relu && !(acc > 0.0f) ? 0.0f : acc;
+    }
+}
+
+void or_mlp_forward_f32(const float* p, const float* x, float* out) {
+    float h1[OR_MLP_H], h2[OR_MLP_H];
+    dense_f32(p + P_W1, p + P_B1, x, OR_FEATURES, OR_MLP_H, 1, h1);
+    dense_f32(p + P_W2, p + P_B2, h1, OR_MLP_H, OR_MLP_H, 1, h2);
+    dense_f32(p + P_W3, p + P_B3, h2, OR_MLP_H, OR_MLP_OUT, 0, out);
+}
+
+/* The same network in binary64 (the definition the binary32 one is checked
+ * against). */
+static void dense_f64(const double* Wt, const double* b, const double* x, int n_in, int n_out, int relu,
+                      double* y) {
+    for (int j = 0; j < n_out; j++) {
+        double acc = b[j];
+        for (int k = 0; k < n_in; k++) acc += Wt[j * n_in + k] * x[k];
+        y[j] = relu && !(acc > 0.0) ? 0.0 : acc;
+    }
+}
+
+void or_mlp_forward_f64(const double* p, const double* x, double* h1, double* h2, double* out) {
+    double a[OR_MLP_H], b[OR_MLP_H];
+    if (!h1) h1 = a;
+    if (!h2) h2 = b;
+    dense_f64(p + P_W1, p + P_B1, x, OR_FEATURES, OR_MLP_H, 1, h1);
+    dense_f64(p + P_W2, p + P_B2, h1, OR_MLP_H, OR_MLP_H, 1, h2);
+    dense_f64(p + P_W3, p + P_B3, h2, OR_MLP_H, OR_MLP_OUT, 0, out);
+}
+
+/* Training loss of the warm start, mean over B samples.  Output 0 is the
+ * guess u of the dimensionless product D tau, output 1 the log half-width l
+ * of the interval around it, read as 3 standard deviations of a Gaussian:
+ *     loss = 9/2 (u* - u)^2 exp(-2 lc) + lc,   lc = clamp(l, -10, 2)
+ * (its negative log-likelihood up to a constant; no gradient flows through l
+ * where it is clamped).  With grad != NULL, writes d loss / d p (backprop,
+ * ReLU derivative 1 where the pre-activation is > 0). */
+double or_mlp_loss_f64(const double* p, const double* X, const double* u_star, int64_t B, double* grad) {
+    if (grad) memset(grad, 0, sizeof(double) * P_END);
+    double loss = 0.0;
+    for (int64_t s = 0; s < B; s++) {
+        const double* x = X + s * OR_FEATURES;
+        double h1[OR_MLP_H], h2[OR_MLP_H], o[OR_MLP_OUT];
+        or_mlp_forward_f64(p, x, h1, h2, o);
+        const double e = u_star[s] - o[0];
+        const int clamped = !(o[1] > OR_MLP_LMIN && o[1] < OR_MLP_LMAX);
+        const double lc = o[1] < OR_MLP_LMIN ? OR_MLP_LMIN : (o[1] > OR_MLP_LMAX ? OR_MLP_LMAX : o[1]);
+        const double q = 9.0 * exp(-2.0 * lc);
+        loss += 0.5 * q * e * e + lc;
+        if (!grad) continue;
+        double go[OR_MLP_OUT];
+        go[0] = -q * e / (double)B;
+        go[1] = clamped ? 0.0 : (1.0 - q * e * e) / (double)B;
+        double g2[OR_MLP_H], g1[OR_MLP_H];
+        for (int k = 0; k < OR_MLP_H; k++) {
+            double a = 0.0;
+            for (int j = 0; j < OR_MLP_OUT; j++) {
+                grad[P_W3 + j * OR_MLP_H + k] += go[j] * h2[k];
+                a += p[P_W3 + j * OR_MLP_H + k] * go[j];
+            }
+            g2[k] = h2[k] > 0.0 ? a : 0.0;
+        }
+        for (int j = 0; j < OR_MLP_OUT; j++) grad[P_B3 + j] += go[j];
+        for (int k = 0; k < OR_MLP_H; k++) {
+            double a = 0.0;
+            for (int j = 0; j < OR_MLP_H; j++) {
+                grad[P_W2 + j * OR_MLP_H + k] += g2[j] * h1[k];
+                a += p[P_W2 + j * OR_MLP_H + k] * g2[j];
+            }
+            g1[k] = h1[k] > 0.0 ? a : 0.0;
+        }
+        for (int j = 0; j < OR_MLP_H; j++) grad[P_B2 + j] += g2[j];
+        for (int j = 0; j < OR_MLP_H; j++) {
+            for (int k = 0; k < OR_FEATURES; k++) grad[P_W1 + j * OR_FEATURES + k] += g1[j] * x[k];
+            grad[P_B1 + j] += g1[j];
+        }
+    }
+    return loss / (double)B;
+}
+
+/* From the network's outputs to a warm start for a window of length tau:
+ * D_warm = u / tau; the half-width exp(l) is rounded to the nearest power
+ * of two 2^e (e = floor(l log2(e) + 1/2), clamped to [-20, 1]; NaN gives
+ * -20) and w_warm = 2^e / tau. */
+void or_warm_map(float u, float l, float tau, float* D_warm, float* w_warm) {
+    *D_warm = u / tau;
+    float v = l * OR_LOG2E + 0.5f;
+    if (!(v >= -20.0f)) v = -20.0f;
+    if (v > 1.0f) v = 1.0f;
+    *w_warm = ldexpf(1.0f, (int)floorf(v)) / tau;
 }

@@ -64,10 +64,34 @@ int or_bound(const or_window* w, float D_lo, float D_hi, or_i128* Kbar, uint64_t
              int64_t* N_full, uint32_t* iwe);
 int or_solve(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
              or_result* out, or_node_rec* trace, int64_t trace_cap, int64_t* trace_len);
+/* Algorithm 1 with an optional warm start (warm = 1): the first incumbent is
+ * D_warm (clamped into the domain) instead of the centre, and the domain is
+ * queued as the pieces cut at D_warm -/+ w_warm (w_warm > 0).  warm = 0 is
+ * or_solve. */
+int or_solve_warm(const or_window* w, float D_lo, float D_hi, float tol_D, double gamma, int32_t K_pop,
+                  int32_t warm, float D_warm, float w_warm, or_result* out, or_node_rec* trace,
+                  int64_t trace_cap, int64_t* trace_len);
 int or_grid_max(const or_window* w, float D_lo, float D_hi, float h, or_i128* K_max, float* D_at,
                 int64_t* n_evals);
 int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, float* D_at,
                  int64_t* n_evals);
+
+/* Learned warm start (features, network, loss, mapping to a warm start). */
+#define OR_FEAT_R 16
+#define OR_FEAT_T 8
+#define OR_FEATURES (OR_FEAT_R * OR_FEAT_T)
+#define OR_MLP_H 128
+#define OR_MLP_OUT 2
+#define OR_MLP_PARAMS (OR_MLP_H * OR_FEATURES + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H + \
+                       OR_MLP_OUT * OR_MLP_H + OR_MLP_OUT)
+#define OR_MLP_LMIN (-10.0)
+#define OR_MLP_LMAX 2.0
+#define OR_LOG2E 1.44269504f
+int or_features(const or_window* w, float* f, int64_t* counts);
+void or_mlp_forward_f32(const float* params, const float* x, float* out);
+void or_mlp_forward_f64(const double* params, const double* x, double* h1, double* h2, double* out);
+double or_mlp_loss_f64(const double* params, const double* X, const double* u_star, int64_t B, double* grad);
+void or_warm_map(float u, float l, float tau, float* D_warm, float* w_warm);
 
 #ifdef __cplusplus
 }

@@ -167,6 +167,24 @@ def batch_config3(n_windows=256, seed=3000):
     return [batch_window3(i, params, seed) for i in range(n_windows)]
 
 
+def batch_params4(n_windows, seed):
+    """Per-window (N, D, noise fraction, tau) of warm-start training or
+    evaluation windows: as the uneven batch, with N log-uniform in [20k, 100k]."""
+    k = stream_key(seed, _S_PARAM)
+    c = np.arange(n_windows, dtype=np.uint64) * np.uint64(4)
+    n = np.floor(np.exp(math.log(2e4) + uniform01(k, c) * (math.log(1e5) - math.log(2e4)))).astype(np.int64)
+    D = 0.05 + uniform01(k, c + np.uint64(1)) * 0.75
+    noise = 0.1 + uniform01(k, c + np.uint64(2)) * 0.3
+    tau = 0.1 + uniform01(k, c + np.uint64(3)) * 0.4
+    return n, D, noise, tau
+
+
+# Seed bases of the warm-start windows: training and held-out evaluation sets
+# are disjoint from each other and from every other workload's seeds.
+WARM_TRAIN_SEED = 20_000_000
+WARM_EVAL_SEED = 10_000_000
+
+
 def serve_spec5(stream, w, n_scale=1.0):
     """make_window arguments of window w (t_w = 0.1 w) of descent `stream` at
     1280x720: D = 1/(20 - t_w); N rises linearly with D from 50k (D=0.05) to
