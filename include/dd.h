@@ -106,15 +106,33 @@ typedef struct {
     int64_t rounds;         /* BnB rounds (dequeue batches)                         */
     int64_t max_queue;      /* largest queue length seen                            */
     int32_t status;         /* DD_OK                                                */
+    float D_warm, w_warm;   /* the warm start the search began from (guess, clamped */
+                            /* into the domain, and half-width); 0, 0 without one   */
 } dd_result;
 
-/* Search parameters of one window of dd_solve_batch. */
+/* Warm start of one search (dd_window_params.warm). */
+enum {
+    DD_WARM_NONE = 0,       /* Algorithm 1 as printed: the first incumbent is the   */
+                            /* centre of the domain, which is queued whole          */
+    DD_WARM_GIVEN = 1,      /* start from the caller's guess D_warm +- w_warm       */
+    DD_WARM_MODEL = 2       /* start from the context's learned model's guess       */
+                            /* (dd_set_warm_model), computed on the device          */
+};
+
+/* Search parameters of one window of dd_solve_batch / dd_serve_submit. */
 typedef struct {
     float D_lo, D_hi;       /* search range, D_lo < D_hi, both in the domain        */
     float tol_D;            /* leaf width (>= 0)                                     */
-    int32_t reserved;       /* 0                                                     */
+    int32_t warm;           /* DD_WARM_*                                             */
     double gamma;           /* stopping gap of Algorithm 1, contrast units (>= 0)    */
+    float D_warm, w_warm;   /* DD_WARM_GIVEN: guess (finite) and half-width (> 0)   */
 } dd_window_params;
+/* A warm start changes where the search begins, never what it certifies:
+ * the guess, clamped into [D_lo, D_hi], is the first incumbent in place of
+ * the centre, and the domain enters the queue as the pieces
+ * [D_lo, a], [a, b], [b, D_hi] of positive width, a = max(D_lo, guess - w),
+ * b = min(D_hi, guess + w) (binary32), each queued if its bound reaches the
+ * incumbent.  The certificate (gap_K) keeps its meaning. */
 
 /* One expanded interval, in expansion order (dd_solve_trace). */
 typedef struct {
@@ -186,6 +204,11 @@ int dd_solve_trace(dd_ctx* ctx, const dd_events* ev, float D_lo, float D_hi, flo
                    double gamma, dd_result* out, dd_node_rec* trace, int64_t trace_cap,
                    int64_t* trace_len);
 
+/* One window with full search parameters (warm start included) and an
+ * optional trace as dd_solve_trace (trace_cap 0: none). */
+int dd_solve_window(dd_ctx* ctx, const dd_events* ev, const dd_window_params* p, dd_result* out,
+                    dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len);
+
 /* Counters of one context since dd_create or the last dd_reset_stats. */
 typedef struct {
     int64_t kernel_launches;  /* kernels this library launched                      */
@@ -206,6 +229,82 @@ int dd_reset_stats(dd_ctx* ctx);
  * context's stream and add its duration to dd_stats.eval_ms (costs a few
  * microseconds per launch; off by default). */
 int dd_set_timing(dd_ctx* ctx, int32_t enable);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start.  An extension of the paper's method: its Algorithm 1
+ * starts every search from the centre of the domain; here a small network
+ * trained on exactly solved windows proposes where to start instead.
+ *
+ * Features: the window's events counted in 16 radial x 8 temporal bins,
+ * each count as 128 * count / n (the bin's share relative to an even
+ * spread); feature 8*r + k counts radial bin r = floor(16 d/R) and
+ * temporal bin k = floor(8 (t - t0)/tau) (each clamped to the last bin), d the
+ * event's distance from the FOE and R the largest distance from the FOE to a
+ * corner pixel centre, every step one binary32 operation.
+ * Network: 128 -> 128 -> 128 -> 2, ReLU after both hidden layers, weights
+ * bfloat16, biases, activations and accumulation binary32; each unit adds
+ * weight * input for inputs 0..127 in turn onto its bias.  Output 0 is a
+ * guess u of D*tau, output 1 the log of the half-width l (in D*tau units).
+ * The guess is D_warm = u / tau and the half-width w_warm = 2^e / tau, e =
+ * floor(l log2(e) + 1/2) clamped to [-20, 1].
+ * Parameters (dd_mlp_get_params / set_params, host float arrays of
+ * DD_MLP_PARAMS): W1[128][128] b1[128] W2[128][128] b2[128] W3[2][128] b3[2],
+ * matrices [out][in] row-major.
+ * Training loss: mean over samples of 9/2 (u* - u)^2 exp(-2 l) + l,
+ * u* = D* tau of the exact solve (the negative log-likelihood of a Gaussian
+ * whose 3 standard deviations are the half-width).
+ */
+#define DD_MLP_FEATURES 128
+#define DD_MLP_PARAMS 33282
+typedef struct dd_mlp dd_mlp;
+
+/* A model on the current device, weights drawn uniformly in
+ * +-sqrt(6/fan_in) from `seed` (biases 0, except b3[1] = log(0.05)).
+ * Errors: DD_ERR_NO_DEVICE, DD_ERR_OOM, DD_ERR_CUDA. */
+int dd_mlp_create(uint64_t seed, dd_mlp** out);
+void dd_mlp_destroy(dd_mlp* m);
+
+/* Run the model's work on `stream` (NULL: the legacy default stream). */
+int dd_mlp_set_stream(dd_mlp* m, void* stream);
+
+/* The parameters the network evaluates with (weights rounded to bfloat16),
+ * n = DD_MLP_PARAMS floats (host).  set_params also resets the optimiser. */
+int dd_mlp_get_params(dd_mlp* m, float* params, int64_t n);
+int dd_mlp_set_params(dd_mlp* m, const float* params, int64_t n);
+
+/* Save / load the binary32 master parameters: a 32-byte header ("DDMLP001",
+ * parameter count, optimiser step, reserved) and DD_MLP_PARAMS
+ * little-endian floats.  Errors: DD_ERR_ARG (I/O, bad header). */
+int dd_mlp_save(dd_mlp* m, const char* path);
+int dd_mlp_load(dd_mlp* m, const char* path);
+
+/* Network outputs for B samples: X [B][128] and out [B][2] in DEVICE memory.
+ * Synchronises the model's stream.  Errors: DD_ERR_ARG (B < 0, NULL),
+ * DD_ERR_CUDA. */
+int dd_mlp_forward(dd_mlp* m, const float* X, int32_t B, float* out);
+
+/* Gradient of the training loss over B samples (1 <= B <= 4096): X [B][128],
+ * u_star [B], grad [DD_MLP_PARAMS] and loss [1] in DEVICE memory (grad in
+ * the parameter layout above; weight gradients are with respect to the
+ * bfloat16 weights the network evaluates with).  Asynchronous on the model's
+ * stream. */
+int dd_mlp_grad(dd_mlp* m, const float* X, const float* u_star, int32_t B, float* grad, float* loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) of learning rate lr on
+ * the master parameters from the gradient over the B samples; the bfloat16
+ * weights are re-rounded.  loss (DEVICE, nullable) receives the loss before
+ * the step.  Asynchronous on the model's stream. */
+int dd_mlp_train_step(dd_mlp* m, const float* X, const float* u_star, int32_t B, float lr, float* loss);
+
+/* The features of n_windows windows (all of the context's geometry) into
+ * feat [n_windows][128] in DEVICE memory, computed on the context's stream
+ * (synchronised before return).  Errors: as dd_solve_batch's checks. */
+int dd_features(dd_ctx* ctx, const dd_events* windows, int32_t n_windows, float* feat);
+
+/* The model that DD_WARM_MODEL windows of this context (and of servers
+ * started from it afterwards) take their warm start from; NULL clears it.
+ * The model must live on the context's device and outlive its use. */
+int dd_set_warm_model(dd_ctx* ctx, dd_mlp* m);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of windows from concurrent event streams

@@ -243,7 +243,8 @@ OFFSETS = {"W1": 0, "b1": 16384, "W2": 16512, "b2": 32896, "W3": 33024, "b3": 33
 
 
 def features(win):
-    """(features float32[128], counts int64[128]); bin index = 8 * radial + temporal."""
+    """(features float32[128], counts int64[128]); bin index = 8 * radial + temporal,
+    feature = 128 * count / n."""
     f = np.zeros(N_FEATURES, np.float32)
     c = np.zeros(N_FEATURES, np.int64)
     _check(lib().or_features(ctypes.byref(win.c), f.ctypes.data, c.ctypes.data))

@@ -613,7 +613,8 @@ int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, flo
 /* ------------------------------------------------- learned warm start */
 
 /* Input features of the learned warm start: event counts in 16 radial x 8
- * temporal bins, divided by the window's event count.  The radius is the
+ * temporal bins as the bin's share of the window's events relative to an
+ * even spread, 128 * count / n (one binary32 division; 1 on average).  The radius is the
  * event's distance from the FOE relative to R, the largest distance from the
  * FOE to a corner pixel centre; radial bin floor(16 r / R) (at most 15).
  * The temporal bin is floor(8 (t - t0) / tau) (at most 7).  Every step is
@@ -642,7 +643,7 @@ int or_features(const or_window* w, float* f, int64_t* counts) {
         c[rb * OR_FEAT_T + tb]++;
     }
     for (int k = 0; k < OR_FEATURES; k++) {
-        if (f) f[k] = w->n > 0 ? (float)c[k] / (float)w->n : 0.0f;
+        if (f) f[k] = w->n > 0 ? (float)(c[k] * OR_FEATURES) / (float)w->n : 0.0f;
         if (counts) counts[k] = c[k];
     }
     return OR_OK;
@@ -702,10 +703,9 @@ void or_mlp_forward_f64(const double* p, const double* x, double* h1, double* h2
 /* Training loss of the warm start, mean over B samples.  Output 0 is the
  * guess u of the dimensionless product D tau, output 1 the log half-width l
  * of the interval around it, read as 3 standard deviations of a Gaussian:
- *     loss = 9/2 (u* - u)^2 exp(-2 lc) + lc,   lc = clamp(l, -10, 2)
- * (its negative log-likelihood up to a constant; no gradient flows through l
- * where it is clamped).  With grad != NULL, writes d loss / d p (backprop,
- * ReLU derivative 1 where the pre-activation is > 0). */
+ *     loss = 9/2 (u* - u)^2 exp(-2 l) + l
+ * (its negative log-likelihood up to a constant).  With grad != NULL, writes
+ * d loss / d p (backprop, ReLU derivative 1 where the pre-activation is > 0). */
 double or_mlp_loss_f64(const double* p, const double* X, const double* u_star, int64_t B, double* grad) {
     if (grad) memset(grad, 0, sizeof(double) * P_END);
     double loss = 0.0;
@@ -714,14 +714,12 @@ double or_mlp_loss_f64(const double* p, const double* X, const double* u_star, i
         double h1[OR_MLP_H], h2[OR_MLP_H], o[OR_MLP_OUT];
         or_mlp_forward_f64(p, x, h1, h2, o);
         const double e = u_star[s] - o[0];
-        const int clamped = !(o[1] > OR_MLP_LMIN && o[1] < OR_MLP_LMAX);
-        const double lc = o[1] < OR_MLP_LMIN ? OR_MLP_LMIN : (o[1] > OR_MLP_LMAX ? OR_MLP_LMAX : o[1]);
-        const double q = 9.0 * exp(-2.0 * lc);
-        loss += 0.5 * q * e * e + lc;
+        const double q = 9.0 * exp(-2.0 * o[1]);
+        loss += 0.5 * q * e * e + o[1];
         if (!grad) continue;
         double go[OR_MLP_OUT];
         go[0] = -q * e / (double)B;
-        go[1] = clamped ? 0.0 : (1.0 - q * e * e) / (double)B;
+        go[1] = (1.0 - q * e * e) / (double)B;
         double g2[OR_MLP_H], g1[OR_MLP_H];
         for (int k = 0; k < OR_MLP_H; k++) {
             double a = 0.0;

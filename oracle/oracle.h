@@ -84,8 +84,6 @@ int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, flo
 #define OR_MLP_OUT 2
 #define OR_MLP_PARAMS (OR_MLP_H * OR_FEATURES + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H + \
                        OR_MLP_OUT * OR_MLP_H + OR_MLP_OUT)
-#define OR_MLP_LMIN (-10.0)
-#define OR_MLP_LMAX 2.0
 #define OR_LOG2E 1.44269504f
 int or_features(const or_window* w, float* f, int64_t* counts);
 void or_mlp_forward_f32(const float* params, const float* x, float* out);

@@ -6,9 +6,15 @@ CUDA kernels behind include/dd.h.  There is no CPU fallback: if libdd.so is
 missing or fails to load, every entry point raises.
 
 The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
-dd_solve_trace, dd_solve_batch, dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing,
-dd_destroy, dd_strerror); ``Context`` wraps
-them for numpy arrays (host events) and torch CUDA tensors (device events).
+dd_solve_trace, dd_solve_window, dd_solve_batch, dd_features, dd_set_warm_model,
+dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing, dd_destroy,
+dd_strerror, the dd_serve_* and dd_mlp_* families); ``Context``, ``Server``
+and ``Mlp`` wrap them for numpy arrays (host events) and torch CUDA tensors
+(device events, features, training batches).
+
+Window parameters are tuples (D_lo, D_hi, tol_D, gamma[, warm]) with warm
+None (Algorithm 1 from the centre), "model" (the context's warm-start model)
+or (D_warm, w_warm) (a given guess and half-width).
 """
 import ctypes
 import os
@@ -23,6 +29,8 @@ DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_CUD
 DD_ERR_CAPACITY = -7
 DD_PENDING = 1
 DD_NOALLOC_MAX_EVENTS = 1 << 20
+DD_WARM_NONE, DD_WARM_GIVEN, DD_WARM_MODEL = 0, 1, 2
+DD_MLP_FEATURES, DD_MLP_PARAMS = 128, 33282
 
 
 class DDError(RuntimeError):
@@ -56,7 +64,7 @@ class dd_result(ctypes.Structure):
                 ("bound_evals", ctypes.c_int64), ("event_warps", ctypes.c_int64),
                 ("cell_increments", ctypes.c_int64), ("bound_increments", ctypes.c_int64),
                 ("rounds", ctypes.c_int64), ("max_queue", ctypes.c_int64),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("D_warm", ctypes.c_float), ("w_warm", ctypes.c_float)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("K_hat", "gap_K")}
@@ -67,7 +75,20 @@ class dd_result(ctypes.Structure):
 
 class dd_window_params(ctypes.Structure):
     _fields_ = [("D_lo", ctypes.c_float), ("D_hi", ctypes.c_float), ("tol_D", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double)]
+                ("warm", ctypes.c_int32), ("gamma", ctypes.c_double), ("D_warm", ctypes.c_float),
+                ("w_warm", ctypes.c_float)]
+
+
+def window_params(p):
+    """dd_window_params from (D_lo, D_hi, tol_D, gamma[, warm])."""
+    warm = p[4] if len(p) > 4 else None
+    if warm is None:
+        return dd_window_params(p[0], p[1], p[2], DD_WARM_NONE, p[3], 0.0, 0.0)
+    if isinstance(warm, str):
+        if warm != "model":
+            raise ValueError("warm must be None, 'model' or (D_warm, w_warm)")
+        return dd_window_params(p[0], p[1], p[2], DD_WARM_MODEL, p[3], 0.0, 0.0)
+    return dd_window_params(p[0], p[1], p[2], DD_WARM_GIVEN, p[3], float(warm[0]), float(warm[1]))
 
 
 class dd_node_rec(ctypes.Structure):
@@ -99,6 +120,20 @@ SIGNATURES = {
     "dd_solve_trace": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_double, _P(dd_result), _VP, ctypes.c_int64, _P(ctypes.c_int64)]),
     "dd_solve_batch": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, _P(dd_window_params), _P(dd_result)]),
+    "dd_solve_window": (ctypes.c_int, [_VP, _P(dd_events), _P(dd_window_params), _P(dd_result), _VP,
+                                       ctypes.c_int64, _P(ctypes.c_int64)]),
+    "dd_features": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, _VP]),
+    "dd_set_warm_model": (ctypes.c_int, [_VP, _VP]),
+    "dd_mlp_create": (ctypes.c_int, [ctypes.c_uint64, _P(_VP)]),
+    "dd_mlp_destroy": (None, [_VP]),
+    "dd_mlp_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "dd_mlp_get_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "dd_mlp_set_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "dd_mlp_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "dd_mlp_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "dd_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP]),
+    "dd_mlp_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP, _VP]),
+    "dd_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, _VP]),
     "dd_serve_start": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64, _P(_VP)]),
     "dd_serve_slots": (ctypes.c_int, [_VP, _P(ctypes.c_int32), _P(ctypes.c_int64)]),
     "dd_serve_submit": (ctypes.c_int, [_VP, _P(dd_events), _P(dd_window_params), ctypes.c_double,
@@ -253,7 +288,7 @@ def dd_solve_batch(h, evs, params):
     own status); raises when the call itself failed."""
     n = len(evs)
     E = (dd_events * n)(*[e.c for e in evs])
-    P = (dd_window_params * n)(*[dd_window_params(a, b, t, 0, g) for (a, b, t, g) in params])
+    P = (dd_window_params * n)(*[window_params(p) for p in params])
     R = (dd_result * n)()
     rc = load().dd_solve_batch(h, E, n, P, R)
     res = [R[i].as_dict() for i in range(n)]
@@ -273,6 +308,101 @@ def dd_solve_trace(h, ev, D_lo, D_hi, tol_D, gamma, trace_cap):
                   for i in range(min(tl.value, trace_cap))]
     d["trace_len"] = tl.value
     return d
+
+
+def dd_solve_window(h, ev, params, trace_cap=0):
+    """One window with full parameters (warm start included), optional trace."""
+    r = dd_result()
+    p = window_params(params)
+    tr = (dd_node_rec * max(trace_cap, 1))()
+    tl = ctypes.c_int64(0)
+    _check(load().dd_solve_window(h, ctypes.byref(ev.c), ctypes.byref(p), ctypes.byref(r),
+                                  ctypes.cast(tr, _VP) if trace_cap else None, trace_cap, ctypes.byref(tl)),
+           "dd_solve_window")
+    d = r.as_dict()
+    if trace_cap:
+        d["trace"] = [(tr[i].D_lo, tr[i].D_hi, tr[i].D_c, tr[i].leaf, tr[i].Kbar.value(), tr[i].K_c.value())
+                      for i in range(min(tl.value, trace_cap))]
+        d["trace_len"] = tl.value
+    return d
+
+
+def dd_features(h, evs):
+    """Warm-start features of the windows (list of Events): torch CUDA tensor [n][128]."""
+    import torch
+    n = len(evs)
+    E = (dd_events * n)(*[e.c for e in evs])
+    out = torch.empty((n, DD_MLP_FEATURES), dtype=torch.float32, device="cuda")
+    _check(load().dd_features(h, E, n, out.data_ptr()), "dd_features")
+    return out
+
+
+class Mlp:
+    """The warm-start network (dd_mlp_*); batches are torch CUDA tensors."""
+
+    def __init__(self, seed=0, path=None):
+        h = _VP()
+        _check(load().dd_mlp_create(int(seed), ctypes.byref(h)), "dd_mlp_create")
+        self.h = h
+        if path:
+            self.load(path)
+
+    def close(self):
+        if self.h:
+            load().dd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        _check(load().dd_mlp_set_stream(self.h, _VP(stream_ptr) if stream_ptr else None), "dd_mlp_set_stream")
+
+    def get_params(self):
+        p = np.zeros(DD_MLP_PARAMS, np.float32)
+        _check(load().dd_mlp_get_params(self.h, p.ctypes.data, p.size), "dd_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(load().dd_mlp_set_params(self.h, p.ctypes.data, p.size), "dd_mlp_set_params")
+
+    def save(self, path):
+        _check(load().dd_mlp_save(self.h, os.fsencode(path)), "dd_mlp_save")
+
+    def load(self, path):
+        _check(load().dd_mlp_load(self.h, os.fsencode(path)), "dd_mlp_load")
+
+    @staticmethod
+    def _dev(X):
+        assert X.is_cuda and X.dtype.is_floating_point and X.is_contiguous()
+        return X
+
+    def forward(self, X):
+        import torch
+        X = self._dev(X)
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(load().dd_mlp_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr()), "dd_mlp_forward")
+        return out
+
+    def grad(self, X, u_star):
+        """(gradient [DD_MLP_PARAMS], loss [1]) as CUDA tensors."""
+        import torch
+        X, u_star = self._dev(X), self._dev(u_star)
+        g = torch.empty(DD_MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(load().dd_mlp_grad(self.h, X.data_ptr(), u_star.data_ptr(), X.shape[0], g.data_ptr(),
+                                  loss.data_ptr()), "dd_mlp_grad")
+        return g, loss
+
+    def train_step(self, X, u_star, lr, loss=None):
+        """One Adam step; `loss` (CUDA tensor [1], optional) receives the loss."""
+        X, u_star = self._dev(X), self._dev(u_star)
+        _check(load().dd_mlp_train_step(self.h, X.data_ptr(), u_star.data_ptr(), X.shape[0], float(lr),
+                                        loss.data_ptr() if loss is not None else None), "dd_mlp_train_step")
 
 
 def dd_contrast_noalloc(W, H, foe_x, foe_y, ev, D, stream_ptr=None):
@@ -305,7 +435,7 @@ class Server:
 
     def submit(self, ev, params=(-1.0, 1.0, 1e-4, 0.0), arrival=-1.0):
         t = ctypes.c_uint64()
-        p = dd_window_params(params[0], params[1], params[2], 0, params[3])
+        p = window_params(params)
         _check(load().dd_serve_submit(self.h, ctypes.byref(ev.c), ctypes.byref(p), float(arrival), ctypes.byref(t)),
                "dd_serve_submit")
         self._keep[t.value] = ev            # the arrays must outlive the request
@@ -401,7 +531,18 @@ class Context:
             params = [(-1.0, 1.0, 1e-4, 0.0)] * len(evs)
         return dd_solve_batch(self.h, evs, params)
 
-    def solve(self, ev, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, trace_cap=0):
+    def solve(self, ev, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, trace_cap=0, warm=None):
+        """One exact solve; warm = None, "model" or (D_warm, w_warm)."""
+        if warm is not None:
+            return dd_solve_window(self.h, ev, (D_lo, D_hi, tol_D, gamma, warm), trace_cap)
         if trace_cap:
             return dd_solve_trace(self.h, ev, D_lo, D_hi, tol_D, gamma, trace_cap)
         return dd_solve(self.h, ev, D_lo, D_hi, tol_D, gamma)
+
+    def features(self, evs):
+        return dd_features(self.h, evs)
+
+    def set_warm_model(self, mlp):
+        """The model DD_WARM_MODEL windows start from (None clears); keep it alive."""
+        _check(load().dd_set_warm_model(self.h, mlp.h if mlp is not None else None), "dd_set_warm_model")
+        self._model = mlp

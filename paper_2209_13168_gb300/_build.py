@@ -1,6 +1,6 @@
 """Build libdd.so (the CUDA library behind include/dd.h) for sm_103a, in-tree.
 
-Two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 paper_2209_13168_gb300/libdd.so.  -fmad=false keeps every binary32 add and
 multiply a separate rounding (the kernels also use __fmul_rn/__fadd_rn
 explicitly); -prec-div/-prec-sqrt keep IEEE division and square root.
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libdd.so")
-SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_serve.cu", "dd_noalloc.cu"]
+SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_serve.cu", "dd_noalloc.cu", "dd_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
            "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]

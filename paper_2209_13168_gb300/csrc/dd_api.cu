@@ -41,6 +41,12 @@ struct dd_ctx {
     int job_stride = 0;
     int32_t* chunk_win = nullptr;
     int64_t chunk_cap = 0;
+    int32_t n_chunks = 0;         // ingest chunks of the last call
+
+    // learned warm start
+    dd_mlp* warm_model = nullptr;
+    int32_t* feat_counts = nullptr;   // [window][128]
+    int feat_cap = 0;
     dd::Sched* sch = nullptr;
 
     // single-window extras
@@ -311,6 +317,7 @@ int ingest(dd_ctx* c, const dd_events* evs, int nw) {
     }
     DD_TRY(copy(c, c->wins, c->h_wins, sizeof(dd::WinIn) * nw, cudaMemcpyHostToDevice));
     if (ch) DD_TRY(copy(c, c->chunk_win, c->h_chunks, sizeof(int32_t) * ch, cudaMemcpyHostToDevice));
+    c->n_chunks = ch;
     DD_TRY(dd::launch_ingest(c->g, c->wins, nw, c->chunk_win, ch, c->ev, c->rcp, c->row_count, c->row_off,
                              c->cursor, c->err, c->stream));
     c->stats.kernel_launches += ch ? 3 : 1;
@@ -443,7 +450,34 @@ void fill_result(const dd::SolveState& s, const dd_events& ev, int64_t M, dd_res
     r.rounds = s.rounds;
     r.max_queue = s.max_queue;
     r.status = s.status;
+    r.D_warm = s.D_warm;
+    r.w_warm = s.w_warm;
     *out = r;
+}
+
+// Feature counts of the nw windows just ingested, into c->feat_counts.
+int feature_counts(dd_ctx* c, int nw) {
+    if (nw > c->feat_cap) {
+        release(c->feat_counts);
+        c->feat_cap = 0;
+        DD_TRY(cudaMalloc((void**)&c->feat_counts, sizeof(int32_t) * dd::FEATURES * (size_t)nw));
+        c->feat_cap = nw;
+    }
+    DD_TRY(cudaMemsetAsync(c->feat_counts, 0, sizeof(int32_t) * dd::FEATURES * (size_t)nw, c->stream));
+    DD_TRY(dd::launch_features(c->g, c->wins, c->chunk_win, c->n_chunks, c->ev, c->feat_counts, c->stream));
+    c->stats.kernel_launches += c->n_chunks ? 1 : 0;
+    return DD_OK;
+}
+
+// Checks of one window's search parameters (warm start included).
+int check_params(const dd_ctx* c, const dd_window_params& p, float tau) {
+    if (!d_ok(p.D_lo, tau) || !d_ok(p.D_hi, tau) || !(p.D_lo < p.D_hi)) return DD_ERR_ARG;
+    if (!std::isfinite(p.tol_D) || !(p.tol_D >= 0.0f) || !std::isfinite(p.gamma) || !(p.gamma >= 0.0))
+        return DD_ERR_ARG;
+    if (p.warm == DD_WARM_GIVEN)
+        return std::isfinite(p.D_warm) && std::isfinite(p.w_warm) && p.w_warm > 0.0f ? DD_OK : DD_ERR_ARG;
+    if (p.warm == DD_WARM_MODEL) return c->warm_model ? DD_OK : DD_ERR_ARG;
+    return p.warm == DD_WARM_NONE ? DD_OK : DD_ERR_ARG;
 }
 
 int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* prm, dd_result* out,
@@ -452,10 +486,8 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
     for (int w = 0; w < nw; w++) {
         int rc = check_events(&evs[w]);
         if (rc) return rc;
-        const dd_window_params& p = prm[w];
-        if (!d_ok(p.D_lo, evs[w].tau) || !d_ok(p.D_hi, evs[w].tau) || !(p.D_lo < p.D_hi)) return DD_ERR_ARG;
-        if (!std::isfinite(p.tol_D) || !(p.tol_D >= 0.0f) || !std::isfinite(p.gamma) || !(p.gamma >= 0.0))
-            return DD_ERR_ARG;
+        rc = check_params(c, prm[w], evs[w].tau);
+        if (rc) return rc;
     }
     if (trace_cap < 0 || (trace_cap > 0 && (!trace || nw != 1))) return DD_ERR_ARG;
     if (trace_cap > c->trace_cap) {
@@ -467,15 +499,29 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
     int rc = ingest(c, evs, nw);
     if (rc) return rc;
     const int64_t M = (int64_t)c->g.W * c->g.H;
+    bool model = false;
     for (int w = 0; w < nw; w++) {
         dd::WinParams& q = c->h_params[w];
         q.gamma_K = (i128)std::floor(prm[w].gamma * (double)M * (double)M);
         q.D_lo = prm[w].D_lo;
         q.D_hi = prm[w].D_hi;
         q.tol = prm[w].tol_D;
-        q.pad = 0.0f;
+        q.warm = prm[w].warm;
+        q.D_warm = prm[w].warm == DD_WARM_GIVEN ? prm[w].D_warm : 0.0f;
+        q.w_warm = prm[w].warm == DD_WARM_GIVEN ? prm[w].w_warm : 0.0f;
+        q.pad0 = q.pad1 = 0;
+        model |= prm[w].warm == DD_WARM_MODEL;
     }
     DD_TRY(copy(c, c->params, c->h_params, sizeof(dd::WinParams) * nw, cudaMemcpyHostToDevice));
+    if (model) {                                  // the model's guesses, on the device
+        dd::MlpDev m;
+        int dev = -1;
+        if (!dd::mlp_device_view(c->warm_model, &m, &dev) || dev != c->device) return DD_ERR_ARG;
+        rc = feature_counts(c, nw);
+        if (rc) return rc;
+        DD_TRY(dd::launch_warm(c->g, nw, c->feat_counts, c->wins, c->params, m, c->stream));
+        c->stats.kernel_launches++;
+    }
     DD_TRY(cudaMemsetAsync(c->sch, 0, sizeof(dd::Sched), c->stream));
     DD_TRY(dd::launch_init(c->g, nw, c->st, c->tasks, c->max_tasks, c->wins, c->params, c->jobs, c->job_stride,
                            c->sch, c->cfg.pop_k, c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap,
@@ -547,6 +593,7 @@ void ctx_info(const ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks
     *max_rounds = c->cfg.max_rounds;
 }
 cudaStream_t ctx_stream(const ::dd_ctx* c) { return c->stream; }
+const ::dd_mlp* ctx_warm_model(const ::dd_ctx* c) { return c->warm_model; }
 }  // namespace dd
 
 extern "C" {
@@ -595,6 +642,7 @@ void dd_destroy(dd_ctx* c) {
     release(c->F);
     release(c->iwe);
     release(c->trace);
+    release(c->feat_counts);
     release_host(c->h_st);
     release_host(c->h_tasks);
     release_host(c->h_jobs);
@@ -766,6 +814,41 @@ int dd_solve_trace(dd_ctx* c, const dd_events* ev, float D_lo, float D_hi, float
 int dd_solve_batch(dd_ctx* c, const dd_events* windows, int32_t n_windows, const dd_window_params* params,
                    dd_result* out) {
     return solve_impl(c, windows, n_windows, params, out, nullptr, 0, nullptr);
+}
+
+int dd_solve_window(dd_ctx* c, const dd_events* ev, const dd_window_params* p, dd_result* out,
+                    dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
+    return solve_impl(c, ev, 1, p, out, trace, trace_cap, trace_len);
+}
+
+int dd_features(dd_ctx* c, const dd_events* windows, int32_t n_windows, float* feat) {
+    if (!c || !windows || n_windows < 1 || !feat) return DD_ERR_ARG;
+    for (int w = 0; w < n_windows; w++) {
+        const int rc = check_events(&windows[w]);
+        if (rc) return rc;
+    }
+    int rc = ingest(c, windows, n_windows);
+    if (rc) return rc;
+    rc = feature_counts(c, n_windows);
+    if (rc) return rc;
+    DD_TRY(dd::launch_feature_norm(n_windows, c->feat_counts, c->wins, feat, c->stream));
+    c->stats.kernel_launches++;
+    DD_TRY(copy(c, c->h_err, c->err, sizeof(int32_t) * n_windows, cudaMemcpyDeviceToHost));
+    DD_TRY(sync(c));
+    for (int w = 0; w < n_windows; w++)
+        if (c->h_err[w]) return DD_ERR_ARG;
+    return DD_OK;
+}
+
+int dd_set_warm_model(dd_ctx* c, dd_mlp* m) {
+    if (!c) return DD_ERR_ARG;
+    if (m) {
+        dd::MlpDev v;
+        int dev = -1;
+        if (!dd::mlp_device_view(m, &v, &dev) || dev != c->device) return DD_ERR_ARG;
+    }
+    c->warm_model = m;
+    return DD_OK;
 }
 
 }  // extern "C"

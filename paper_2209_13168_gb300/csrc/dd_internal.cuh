@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 struct dd_ctx;
+struct dd_mlp;
 
 namespace dd {
 
@@ -71,20 +72,37 @@ struct __align__(16) SolveState {
     i128 gamma_K;
     int64_t M, max_rounds;
     float D_lo, D_hi, tol, tau;
-    int32_t K_pop, qcap, trace_cap, pad0;
+    int32_t K_pop, qcap, trace_cap, warm;
     // search state
     i128 K_hat, leaf_max, stop_kb;
     float D_hat;
     int32_t phase, status, n_tasks, n_pop, q_n, q_start, q_cur, have_leaf, have_stop;
+    float D_warm, w_warm;                 // the warm start the search began from
     int64_t nodes_expanded, point_evals, bound_evals, cells, bcells, rounds, max_queue, trace_len;
     Popped pop[MAX_POP];
 };
 
-// Search parameters of one window.
+// Search parameters of one window.  warm: 0 none, 1 from (D_warm, w_warm);
+// the model warm start writes its guess here on the device and sets warm = 1.
 struct __align__(16) WinParams {
     i128 gamma_K;
-    float D_lo, D_hi, tol, pad;
+    float D_lo, D_hi, tol;
+    int32_t warm;
+    float D_warm, w_warm;
+    int32_t pad0, pad1;
 };
+
+// Device view of a warm-start model: bfloat16 weights transposed to
+// [in][out] (unit j of a layer reads column j), binary32 biases.
+struct MlpDev {
+    const uint16_t* w1t;    // [128][128]
+    const uint16_t* w2t;    // [128][128]
+    const uint16_t* w3t;    // [128][2]
+    const float* b1;
+    const float* b2;
+    const float* b3;
+};
+constexpr int FEAT_R = 16, FEAT_T = 8, FEATURES = FEAT_R * FEAT_T, MLP_H = 128, MLP_OUT = 2;
 
 // One window's input and where its sorted events go.
 struct WinIn {
@@ -183,9 +201,23 @@ cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Nod
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
                            int32_t use_loop, cudaStream_t s, int32_t split_ok = -1, int32_t* phase_out = nullptr);
 
+// Learned warm start (dd_mlp.cu).  Feature counts of windows 0..n_windows-1
+// (counts [w][128], zeroed by the caller) from their sorted events; then,
+// for every window whose params have warm == 2, the network's guess written
+// into its params (warm = 1).
+cudaError_t launch_features(const Geom& g, const WinIn* wins, const int32_t* chunk_win, int32_t n_chunks,
+                            const Ev* ev, int32_t* counts, cudaStream_t s);
+cudaError_t launch_warm(const Geom& g, int32_t n_windows, const int32_t* counts, const WinIn* wins,
+                        WinParams* params, const MlpDev& m, cudaStream_t s);
+bool mlp_device_view(const struct ::dd_mlp* m, MlpDev* out, int* device);
+// feat[w][k] = 128 counts[w][k] / n_w (binary32), windows 0..n_windows-1.
+cudaError_t launch_feature_norm(int32_t n_windows, const int32_t* counts, const WinIn* wins, float* feat,
+                                cudaStream_t s);
+
 // Context accessors for the serving engine (dd_serve.cu).
 void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks,
               int32_t* pop_k, int32_t* queue_capacity, int64_t* max_rounds);
+const struct ::dd_mlp* ctx_warm_model(const struct ::dd_ctx* c);
 cudaStream_t ctx_stream(const struct ::dd_ctx* c);
 cudaError_t eval_smem_setup(const Geom& g);
 

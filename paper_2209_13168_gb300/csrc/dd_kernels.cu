@@ -687,7 +687,29 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
     st->K_hat = 0;
     st->leaf_max = 0;
     st->stop_kb = 0;
-    st->D_hat = centre(pr.D_lo, pr.D_hi);         // incumbent = centre of the domain
+    st->warm = pr.warm;
+    st->D_warm = 0.0f;
+    st->w_warm = 0.0f;
+    // The pieces the domain enters the queue as: the domain itself, or with
+    // a warm start the pieces of positive width cut at guess -/+ half-width.
+    float cut[4] = {pr.D_lo, pr.D_hi, pr.D_hi, pr.D_hi};
+    int n_cut = 2;
+    if (pr.warm) {
+        float d = pr.D_warm;                      // the guess, clamped into the domain
+        if (!(d >= pr.D_lo)) d = pr.D_lo;
+        if (d > pr.D_hi) d = pr.D_hi;
+        float a = __fsub_rn(d, pr.w_warm), b = __fadd_rn(d, pr.w_warm);
+        if (!(a >= pr.D_lo)) a = pr.D_lo;
+        if (!(b <= pr.D_hi)) b = pr.D_hi;
+        cut[1] = a;
+        cut[2] = b;
+        n_cut = 4;
+        st->D_hat = d;                            // incumbent = the guess
+        st->D_warm = d;
+        st->w_warm = pr.w_warm;
+    } else {
+        st->D_hat = centre(pr.D_lo, pr.D_hi);     // incumbent = centre of the domain
+    }
     st->phase = PH_INIT;
     st->status = DD_OK;
     st->n_pop = 0;
@@ -698,32 +720,40 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
     st->have_stop = 0;
     st->nodes_expanded = st->point_evals = st->bound_evals = st->cells = st->bcells = 0;
     st->rounds = st->max_queue = st->trace_len = 0;
-    Task a, b;
+    Task a;
     a.D_lo = a.D_hi = st->D_hat;
     a.kind = TASK_POINT;
     a.splits = 1;
-    b.D_lo = pr.D_lo;                             // bound of the domain (queued first)
-    b.D_hi = pr.D_hi;
-    b.kind = TASK_BOUND;
-    b.splits = split_ok ? bound_splits(g, pr.D_lo, pr.D_hi, tau) : 1;
     tasks[0] = a;
-    tasks[1] = b;
-    st->n_tasks = 2;
-    const int base = atomicAdd(&sch->n_jobs[par], 1 + b.splits);
-    for (int s = 0; s < b.splits; s++) {
-        Job j;
-        j.win = w;
-        j.task = 1;
-        j.split = s;
-        j.splits = b.splits;
-        jobs[base + s] = j;
+    int nt = 1, n_jobs = 1;
+    for (int i = 0; i + 1 < n_cut; i++) {
+        if (!(cut[i] < cut[i + 1])) continue;
+        Task b;                                   // bound of one piece
+        b.D_lo = cut[i];
+        b.D_hi = cut[i + 1];
+        b.kind = TASK_BOUND;
+        b.splits = split_ok ? bound_splits(g, b.D_lo, b.D_hi, tau) : 1;
+        tasks[nt++] = b;
+        n_jobs += b.splits;
     }
+    st->n_tasks = nt;
+    const int base = atomicAdd(&sch->n_jobs[par], n_jobs);
+    int o = base;
+    for (int t = 1; t < nt; t++)                  // bounds first (heavier)
+        for (int s = 0; s < tasks[t].splits; s++) {
+            Job j;
+            j.win = w;
+            j.task = t;
+            j.split = s;
+            j.splits = tasks[t].splits;
+            jobs[o++] = j;
+        }
     Job j;
     j.win = w;
     j.task = 0;
     j.split = 0;
     j.splits = 1;
-    jobs[base + b.splits] = j;
+    jobs[o] = j;
 }
 
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
@@ -836,18 +866,25 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             if (lane == 0) {
                 s.K_hat = key[0];
                 s.point_evals = 1;
-                s.bound_evals = 1;
-                s.cells = (int64_t)(cells[0] + cells[1]);
-                s.bcells = (int64_t)cells[1];
-                Node root;
-                root.lo = s.D_lo;
-                root.hi = s.D_hi;
-                root.pad0 = root.pad1 = 0;
-                root.kb = key[1];
-                kids[0] = root;                   // the domain is queued unconditionally
+                s.bound_evals = n_tasks - 1;
+                s.cells = (int64_t)cells[0];
+                s.bcells = 0;
+                for (int t = 1; t < n_tasks; t++) {
+                    s.cells += (int64_t)cells[t];
+                    s.bcells += (int64_t)cells[t];
+                    // the domain is queued unconditionally; warm-start pieces
+                    // when their bound reaches the incumbent, as children are
+                    if (s.warm && !(key[t] >= s.K_hat)) continue;
+                    Node nd;
+                    nd.lo = tasks[t].D_lo;
+                    nd.hi = tasks[t].D_hi;
+                    nd.pad0 = nd.pad1 = 0;
+                    nd.kb = key[t];
+                    kids[nk++] = nd;
+                }
                 s.phase = PH_RUN;
             }
-            nk = 1;
+            nk = __shfl_sync(0xffffffffu, nk, 0);
         } else {
             const int np = s.n_pop;
             // Incumbent update in dequeue order (a centre with K >= K_hat wins):

@@ -72,6 +72,9 @@ struct dd_server {
     dd::Job* jobs = nullptr;
     int job_stride = 0;
     dd::Sched* sch = nullptr;
+    int32_t* feat_counts = nullptr;    // [128], the admitted window's features
+    dd::MlpDev model{};
+    bool has_model = false;
 
     // pinned host
     int32_t* h_phase = nullptr;
@@ -127,6 +130,7 @@ void free_server(dd_server* s) {
     release(s->part);
     release(s->jobs);
     release(s->sch);
+    release(s->feat_counts);
     release_host(s->h_phase);
     release_host(s->h_st);
     release_host(s->h_win);
@@ -171,6 +175,7 @@ int alloc_server(dd_server* s) {
     s->job_stride = (int)(S * s->max_tasks);
     A((void**)&s->jobs, sizeof(dd::Job) * 2 * (size_t)s->job_stride);
     A((void**)&s->sch, sizeof(dd::Sched));
+    A((void**)&s->feat_counts, sizeof(int32_t) * dd::FEATURES);
     AH((void**)&s->h_phase, sizeof(int32_t) * S);
     AH((void**)&s->h_st, sizeof(dd::SolveState) * S);
     AH((void**)&s->h_win, sizeof(dd::WinIn));
@@ -221,7 +226,10 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
     q.D_lo = r.p.D_lo;
     q.D_hi = r.p.D_hi;
     q.tol = r.p.tol_D;
-    q.pad = 0.0f;
+    q.warm = r.p.warm;
+    q.D_warm = r.p.warm == DD_WARM_GIVEN ? r.p.D_warm : 0.0f;
+    q.w_warm = r.p.warm == DD_WARM_GIVEN ? r.p.w_warm : 0.0f;
+    q.pad0 = q.pad1 = 0;
     cudaError_t c = cudaMemcpyAsync(s->wins + k, s->h_win, sizeof(dd::WinIn), cudaMemcpyHostToDevice, s->stream);
     if (c != cudaSuccess) return c;
     c = cudaMemcpyAsync(s->params + k, s->h_par, sizeof(dd::WinParams), cudaMemcpyHostToDevice, s->stream);
@@ -235,6 +243,14 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
                           s->row_count + (size_t)k * s->bins, s->row_off + (size_t)k * (s->bins + 1),
                           s->cursor + (size_t)k * s->bins, s->err + k, s->stream);
     if (c != cudaSuccess) return c;
+    if (r.p.warm == DD_WARM_MODEL) {               // the model's guess for this window
+        c = cudaMemsetAsync(s->feat_counts, 0, sizeof(int32_t) * dd::FEATURES, s->stream);
+        if (c != cudaSuccess) return c;
+        c = dd::launch_features(s->g, s->wins + k, s->chunk_zero, n_chunks, s->ev, s->feat_counts, s->stream);
+        if (c != cudaSuccess) return c;
+        c = dd::launch_warm(s->g, 1, s->feat_counts, s->wins + k, s->params + k, s->model, s->stream);
+        if (c != cudaSuccess) return c;
+    }
     return dd::launch_init(s->g, 1, s->st, s->tasks, s->max_tasks, s->wins, s->params, s->jobs, s->job_stride,
                            s->sch, s->pop_k, s->qcap, s->max_rounds, 0, s->stream, k, 0);
 }
@@ -263,6 +279,8 @@ void fill(const dd::SolveState& st, const dd_events& ev, int64_t M, dd_result* o
     r.rounds = st.rounds;
     r.max_queue = st.max_queue;
     r.status = st.status;
+    r.D_warm = st.D_warm;
+    r.w_warm = st.w_warm;
     *out = r;
 }
 
@@ -396,6 +414,10 @@ int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server
     if (!s) return DD_ERR_OOM;
     dd::ctx_info(ctx, &s->g, &s->threads, &s->eval_blocks, &s->max_tasks, &s->pop_k, &s->qcap, &s->max_rounds);
     s->g.max_splits = 1;
+    if (const dd_mlp* m = dd::ctx_warm_model(ctx)) {
+        int dev = -1;
+        s->has_model = dd::mlp_device_view(m, &s->model, &dev);
+    }
     s->E = max_events;
     s->bins = s->g.n_tb * s->g.H;
     s->max_chunks = (int)((max_events + dd::CHUNK - 1) / dd::CHUNK);
@@ -453,6 +475,13 @@ int dd_serve_submit(dd_server* s, const dd_events* ev, const dd_window_params* p
     if (!d_ok(p->D_lo) || !d_ok(p->D_hi) || !(p->D_lo < p->D_hi) || !(p->tol_D >= 0.0f) || !std::isfinite(p->tol_D) ||
         !(p->gamma >= 0.0) || !std::isfinite(p->gamma))
         return DD_ERR_ARG;
+    if (p->warm == DD_WARM_GIVEN) {
+        if (!std::isfinite(p->D_warm) || !std::isfinite(p->w_warm) || !(p->w_warm > 0.0f)) return DD_ERR_ARG;
+    } else if (p->warm == DD_WARM_MODEL) {
+        if (!s->has_model) return DD_ERR_ARG;
+    } else if (p->warm != DD_WARM_NONE) {
+        return DD_ERR_ARG;
+    }
     if (ev->n > s->E) return DD_ERR_CAPACITY;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return DD_ERR_ARG;
