@@ -93,14 +93,21 @@ def load_table(path=DEFAULT_TABLE):
 
 
 def lookup(W, H, n_events, mode="single", path=DEFAULT_TABLE):
-    """Tuned knobs for this geometry and size on this GPU, or None."""
+    """Tuned knobs for this geometry and size on this GPU (the nearest tuned
+    event-count bucket of the same geometry and mode), or None."""
     try:
         name = gpu_name()
     except Exception:
         return None
-    entry = load_table(path).get(key(W, H, n_events, mode, name))
+    table = load_table(path)
+    entry = table.get(key(W, H, n_events, mode, name))
     if not entry:
-        return None
+        prefix, suffix = "%dx%d/n" % (W, H), "/%s/%s" % (mode, name)
+        near = [(abs(math.log2(int(k[len(prefix):-len(suffix)])) - math.log2(max(1, n_events))), k)
+                for k in table if k.startswith(prefix) and k.endswith(suffix)]
+        if not near:
+            return None
+        entry = table[min(near)[1]]
     return {k: entry[k] for k in ("band_rows", "threads", "pop_k", "max_splits")}
 
 
