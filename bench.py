@@ -10,6 +10,12 @@ every timed step.  Under torchrun each rank solves its own replica (windows
 are independent: replicas, weak scaling).
 
 --impl reference times the CPU oracle on the same window instead.
+
+Beside the headline, the line carries (unless --no-extras) the other
+workloads measured on the same GPU: the 256-window uneven batch
+("batch"), the learned warm start against the plain search on held-out
+windows ("learned_warm_start"), and the continuous-batching server on four
+concurrent 1280x720 descents ("serving").
 """
 import argparse
 import json
@@ -170,6 +176,47 @@ def run_reference(args):
     return 0
 
 
+def run_extras(dd, torch):
+    """The batch, learned warm start and serving workloads (bounded time)."""
+    out = {}
+    # 256 uneven windows in one batched solve
+    from synth.descent import batch_params3, batch_spec3
+    from synth.gpu import make_window_gpu
+    p = batch_params3()
+    ws = [make_window_gpu(batch_spec3(i, p)) for i in range(256)]
+    evs = [dd.Events.of(x) for x in ws]
+    n_mean = sum(x.n for x in ws) / len(ws)
+    ctx = dd.Context.tuned(640, 480, 320.0, 240.0, n_mean, mode="batch")
+    ctx.solve_batch(evs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        rc, res = ctx.solve_batch(evs)
+    dt = (time.perf_counter() - t0) / reps
+    out["batch"] = {"workload": "256 windows 640x480, N log-uniform in [5k, 200k] (mean %.0f), D in [0.05, 0.8], "
+                                "noise 10-40%%, tau 0.1-0.5 s; one batched solve" % n_mean,
+                    "solves_per_s": len(ws) / dt, "ms_per_batch": dt * 1e3, "status": rc,
+                    "nodes_expanded": sum(r["nodes_expanded"] for r in res),
+                    "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}}
+    ctx.close()
+    del ws, evs
+    # learned warm start vs plain on held-out windows
+    from paper_2209_13168_gb300 import warm_start
+    if os.path.exists(warm_start.DEFAULT_MODEL):
+        ev = warm_start.evaluate(warm_start.DEFAULT_MODEL, n_windows=1024, log=None)
+        ev["workload"] = ("held-out 640x480 windows, N log-uniform in [20k, 100k], batch mode; plain = Algorithm 1 "
+                          "from the centre, learned = from the model's guess, ideal = from the certified answer")
+        out["learned_warm_start"] = ev
+    # four concurrent descents through the server
+    from paper_2209_13168_gb300 import serve_bench
+    out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8)
+    out["serving"]["workload"] = ("4 descents at 1280x720, 189 windows each (0.2 s every 0.1 s of flight, 50k-833k "
+                                  "events), Poisson arrivals at 40 windows/s per stream (4x real time)")
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = env_int("WORLD_SIZE", 1), env_int("RANK", 0), env_int("LOCAL_RANK", 0)
@@ -188,7 +235,8 @@ def run_ours(args):
 
     w = window_config2()
     stream = torch.cuda.Stream()
-    ctx = dd.Context(w.W, w.H, w.foe_x, w.foe_y, pop_k=args.pop_k)
+    knobs = {"pop_k": args.pop_k} if args.pop_k else {}
+    ctx = dd.Context.tuned(w.W, w.H, w.foe_x, w.foe_y, w.n, mode="single", **knobs)
     ctx.set_stream(stream.cuda_stream)
     with torch.cuda.stream(stream):
         ev = dd.Events.of(w, device="cuda")
@@ -291,6 +339,10 @@ def run_ours(args):
                  "nodes_expanded": rp["nodes_expanded"], "rounds": rp["rounds"]}
         c1.close()
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(dd, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, el = oracle_rate(w, args.cpu_seconds, 5)
@@ -302,7 +354,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "pop_k": args.pop_k, "events": N,
+           "config": {"workload": WORKLOAD, "events": N,
+                      "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")},
                       "l2": "flushed before each timed step (%d MiB device write)" % args.flush_mb,
                       "inputs": "device-resident SoA", "parallelism": "replicas" if world > 1 else "single GPU"},
            "event_warps_per_s": world * r["event_warps"] * args.steps / total_s,
@@ -313,6 +366,7 @@ def run_ours(args):
                      "point_evals": r["point_evals"], "bound_evals": r["bound_evals"]},
            "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
            "clocks": clk, "plain_pop1": plain}
+    out.update(extras)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -328,12 +382,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--pop-k", type=int, default=16)
+    ap.add_argument("--pop-k", type=int, default=0, help="0: the autotuned value")
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch, warm-start and serving workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

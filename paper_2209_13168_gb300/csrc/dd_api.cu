@@ -52,7 +52,7 @@ struct dd_ctx {
     // single-window extras
     uint32_t* macc = nullptr;     // merge buffers of split jobs (zero between uses)
     int32_t* mdone = nullptr;
-    unsigned long long* mfull = nullptr;
+    dd::Partial* msums = nullptr;
     i128* keys = nullptr;
     unsigned long long *S = nullptr, *C = nullptr, *F = nullptr;
     uint32_t* iwe = nullptr;
@@ -176,7 +176,7 @@ dd::EvalArgs eval_args(dd_ctx* c, uint32_t* iwe_out, bool single) {
     a.iwe_out = iwe_out;
     a.mg.acc = single ? c->macc : nullptr;
     a.mg.done = single ? c->mdone : nullptr;
-    a.mg.full = single ? c->mfull : nullptr;
+    a.mg.sums = single ? c->msums : nullptr;
     return a;
 }
 
@@ -635,7 +635,7 @@ void dd_destroy(dd_ctx* c) {
     release(c->sch);
     release(c->macc);
     release(c->mdone);
-    release(c->mfull);
+    release(c->msums);
     release(c->keys);
     release(c->S);
     release(c->C);
@@ -713,10 +713,10 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     A((void**)&c->sch, sizeof(dd::Sched));
     A((void**)&c->macc, sizeof(uint32_t) * (size_t)c->max_tasks * M);
     A((void**)&c->mdone, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles);
-    A((void**)&c->mfull, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles);
+    A((void**)&c->msums, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles);
     if (rc == DD_OK && (cudaMemset(c->macc, 0, sizeof(uint32_t) * (size_t)c->max_tasks * M) != cudaSuccess ||
                         cudaMemset(c->mdone, 0, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles) != cudaSuccess ||
-                        cudaMemset(c->mfull, 0, sizeof(unsigned long long) * (size_t)c->max_tasks * c->g.n_tiles) !=
+                        cudaMemset(c->msums, 0, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles) !=
                             cudaSuccess))
         rc = DD_ERR_CUDA;
     A((void**)&c->keys, sizeof(i128) * c->max_tasks);

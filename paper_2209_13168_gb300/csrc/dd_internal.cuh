@@ -160,7 +160,7 @@ inline int32_t time_buckets(int32_t H) {
 struct Merge {
     uint32_t* acc;                 // [task][M] counts, zero between uses
     int32_t* done;                 // [task][tile] finished splits, zero between uses
-    unsigned long long* full;      // [task][tile] N_full sums, zero between uses
+    Partial* sums;                 // [task][tile] sums of the splits, zero between uses
 };
 
 // Everything an evaluation launch reads or writes.

@@ -312,10 +312,19 @@ __device__ __forceinline__ Seg seg_range(const Geom& g, float dx, float dy, floa
     return s;
 }
 
+// One increment of a tile cell; the sum of squares grows by 2v + 1 from the
+// cell's previous count v.
+__device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, unsigned long long& C) {
+    const uint32_t v = atomicAdd(cell, 1u);
+    S += 2u * v + 1u;
+    C++;
+}
+
 __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float dn, float rm, float sa, float sb,
-                                         int addr, int y0, int y1, uint32_t* tile) {
+                                         int addr, int y0, int y1, uint32_t* tile, unsigned long long& S,
+                                         unsigned long long& C) {
     if (mode == SEG_ONE) {
-        atomicAdd(&tile[addr], 1u);
+        bump(&tile[addr], S, C);
         return;
     }
     const bool major_x = mode == SEG_X;
@@ -329,11 +338,11 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
     const int j1 = cell_of(fn, dn, lo), j2 = cell_of(fn, dn, hi);
     if (major_x) {
         const int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), g.H - 1), y1 - 1);
-        for (int j = j0; j <= jn; j++) atomicAdd(&tile[(j - y0) * tile_pitch(g) + k], 1u);
+        for (int j = j0; j <= jn; j++) bump(&tile[(j - y0) * tile_pitch(g) + k], S, C);
     } else {
         const int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), g.W - 1);
         uint32_t* row = tile + (k - y0) * tile_pitch(g);
-        for (int j = j0; j <= jn; j++) atomicAdd(&row[j], 1u);
+        for (int j = j0; j <= jn; j++) bump(&row[j], S, C);
     }
 }
 
@@ -350,14 +359,18 @@ struct UnitPtrs {
     uint32_t* out;                // nullable: the task's image [H][W]
     uint32_t* acc;                // split jobs: the task's accumulator [H][W]
     int32_t* done;                // split jobs: finished splits per tile
-    unsigned long long* full;     // split jobs: N_full sums per tile
+    Partial* sums;                // split jobs: sums of the splits per tile
 };
 
 // One unit: split `split` of `splits` of one task's row band `ti`.  The block
 // scatters its share of the events that can reach the band's rows into the
-// shared tile.  An unsplit task reduces the tile itself; a split task adds
-// its tile into the L2 accumulator, and the last of its blocks to finish
-// reduces the accumulated band.  The tile arrives zeroed and leaves zeroed.
+// shared tile.  Each increment returns the cell's previous count v, and the
+// band's sum of squares grows by (v + 1)^2 - v^2 = 2v + 1, so S needs no pass
+// over the tile: an unsplit task only clears it.  A split task adds its tile
+// into the L2 accumulator; each addition of u onto a count w adds
+// (w + u)^2 - w^2 to S, so the splits' sums add up to the band's, and the
+// last split to finish clears the accumulated band.  The tile arrives
+// zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
                                           int* erange, int* s_last) {
@@ -392,6 +405,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         return erange[cur_b] + (f - erange[MAX_TB + cur_b]);
     };
 
+    unsigned long long S = 0, C = 0;
     if (tk.kind == TASK_POINT) {
         const float D = tk.D_lo, gg = warp_g(D, tau);
 #pragma unroll 4
@@ -401,7 +415,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
             if (uy < y0 || uy >= y1) continue;
             const int ux = cell_of(g.fx, __fsub_rn((float)v.x, g.fx), s);
-            if ((unsigned)ux < (unsigned)W) atomicAdd(&tile[(uy - y0) * P + ux], 1u);
+            if ((unsigned)ux < (unsigned)W) bump(&tile[(uy - y0) * P + ux], S, C);
         }
     } else {
         const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
@@ -447,7 +461,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             if (cmax == 0) continue;
             if (cmax <= 2) {                      // short runs: each lane walks its own
                 for (int i = 0; i < sg.count; i++)
-                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile);
+                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, C);
                 continue;
             }
             // Long runs: spread the (event, major cell) pairs over the lanes.
@@ -467,48 +481,59 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
                 const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
                 const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
-                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile);
+                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, C);
             }
         }
     }
     __syncthreads();
 
     uint32_t* out = p.out ? p.out + (size_t)y0 * W : nullptr;
-    unsigned long long S = 0, C = 0;
+    unsigned long long Cl = C;
     // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
     // take columns.
     if (splits == 1) {
         for (int r = wid; r < rows; r += nw)
             for (int c = lane; c < W; c += 32) {
-                const unsigned long long v = tile[r * P + c];
+                if (out) out[r * W + c] = tile[r * P + c];
                 tile[r * P + c] = 0u;
-                S += v * v;
-                C += v;
-                if (out) out[r * W + c] = (uint32_t)v;
             }
     } else {
         uint32_t* acc = p.acc + (size_t)y0 * W;
         // Splits of one band finish together: each starts its pass at its own
         // row so that they add into different words at a time.
         const int rot = (int)((long long)rows * split / splits);
+        S = 0;
         for (int q = wid; q < rows; q += nw) {
             const int r = q + rot < rows ? q + rot : q + rot - rows;
             for (int c = lane; c < W; c += 32) {
                 const uint32_t v = tile[r * P + c];
                 if (v) {
                     tile[r * P + c] = 0u;
-                    atomicAdd(&acc[r * W + c], v);
+                    const unsigned long long w = atomicAdd(&acc[r * W + c], v);
+                    S += (2ull * w + v) * v;
                 }
             }
         }
         __threadfence();                          // this thread's additions, before the count below
+        S = warp_sum(S);
+        Cl = warp_sum(Cl);
         full = warp_sum(full);
-        if (lane == 0) red[2][wid] = full;
+        if (lane == 0) {
+            red[0][wid] = S;
+            red[1][wid] = Cl;
+            red[2][wid] = full;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned long long f = 0;
-            for (int w = 0; w < nw; w++) f += red[2][w];
-            if (f) atomicAdd(&p.full[ti], f);
+            unsigned long long a = 0, b = 0, f = 0;
+            for (int w = 0; w < nw; w++) {
+                a += red[0][w];
+                b += red[1][w];
+                f += red[2][w];
+            }
+            atomicAdd(&p.sums[ti].S, a);
+            atomicAdd(&p.sums[ti].cells, b);
+            if (f) atomicAdd(&p.sums[ti].full, f);
             __threadfence();
             *s_last = atomicAdd(&p.done[ti], 1) == splits - 1;
         }
@@ -516,35 +541,36 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         if (!*s_last) return;                     // another split finishes the band
         __threadfence();                          // every split's additions are visible now
         for (int i = threadIdx.x; i < rows * W; i += blockDim.x) {
-            const unsigned long long v = __ldcg(&acc[i]);
-            if (v) acc[i] = 0u;
-            S += v * v;
-            C += v;
-            if (out) out[i] = (uint32_t)v;
+            if (out) out[i] = __ldcg(&acc[i]);
+            acc[i] = 0u;
         }
-        full = 0;
         if (threadIdx.x == 0) {
-            full = atomicExch(&p.full[ti], 0ull);
+            Partial q;
+            q.S = atomicExch(&p.sums[ti].S, 0ull);
+            q.cells = atomicExch(&p.sums[ti].cells, 0ull);
+            q.full = atomicExch(&p.sums[ti].full, 0ull);
             p.done[ti] = 0;
+            p.part[ti] = q;
         }
+        return;
     }
     S = warp_sum(S);
-    C = warp_sum(C);
+    const unsigned long long C64 = warp_sum(Cl);
     full = warp_sum(full);
     __syncthreads();
-    if (lane == 0) { red[0][wid] = S; red[1][wid] = C; red[2][wid] = full; }
+    if (lane == 0) { red[0][wid] = S; red[1][wid] = C64; red[2][wid] = full; }
     __syncthreads();
     if (wid == 0) {
         S = lane < nw ? red[0][lane] : 0;
-        C = lane < nw ? red[1][lane] : 0;
+        unsigned long long cs = lane < nw ? red[1][lane] : 0;
         full = lane < nw ? red[2][lane] : 0;
         S = warp_sum(S);
-        C = warp_sum(C);
+        cs = warp_sum(cs);
         full = warp_sum(full);
         if (lane == 0) {
             Partial q;
             q.S = S;
-            q.cells = C;
+            q.cells = cs;
             q.full = full;
             p.part[ti] = q;
         }
@@ -592,7 +618,7 @@ __global__ void __launch_bounds__(1024) k_eval(Geom g, EvalArgs a) {
         p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * g.W * g.H : nullptr;
         p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * g.W * g.H : nullptr;
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
-        p.full = a.mg.full ? a.mg.full + (size_t)jb.task * g.n_tiles : nullptr;
+        p.sums = a.mg.sums ? a.mg.sums + (size_t)jb.task * g.n_tiles : nullptr;
         eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last);
         __syncthreads();                          // the unit's readers are done; s_unit is set
     }

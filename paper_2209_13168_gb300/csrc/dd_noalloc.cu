@@ -162,7 +162,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     a.iwe_out = nullptr;
     a.mg.acc = nullptr;
     a.mg.done = nullptr;
-    a.mg.full = nullptr;
+    a.mg.sums = nullptr;
     dd::Task h_tasks[NA_MAX_TASKS];
     dd::Job h_jobs[NA_MAX_TASKS];
     dd::Sched h_sch;

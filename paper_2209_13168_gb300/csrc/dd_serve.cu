@@ -313,7 +313,7 @@ void loop(dd_server* s) {
     a.iwe_out = nullptr;
     a.mg.acc = nullptr;
     a.mg.done = nullptr;
-    a.mg.full = nullptr;
+    a.mg.sums = nullptr;
     for (;;) {
         std::vector<std::pair<int, uint64_t>> admits;
         int busy = 0;
