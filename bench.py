@@ -317,6 +317,17 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
     traffic = profile_traffic(kernel_hash())
+    # the scatter's other two ceilings, from the library's own probes
+    atom_peak, l2_peak = dd.dd_probe_peaks(stream.cuda_stream)
+    incr = rr["cell_increments"]
+    ev_bytes = 8 * N * (pe + be)                  # one 8-byte event record per event-warp
+    roofline_atomics = {"bound": "shared_atomics", "achieved": incr / (eval_ms_per_solve / 1e3) / 1e9,
+                        "peak": atom_peak / 1e9, "unit": "G increments/s",
+                        "frac": incr / (eval_ms_per_solve / 1e3) / atom_peak,
+                        "peak_source": "measured: dd_probe_peaks (shared atomics with return, random cells)"}
+    roofline_l2 = {"bound": "l2", "achieved": ev_bytes / (eval_ms_per_solve / 1e3) / 1e9, "peak": l2_peak / 1e9,
+                   "unit": "GB/s", "frac": ev_bytes / (eval_ms_per_solve / 1e3) / l2_peak,
+                   "peak_source": "measured: dd_probe_peaks (32 MiB L2-resident stream)"}
     roofline = {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "derived: %d SMs x %d lanes x %.0f MHz (max SM clock of measured peaks)"
@@ -365,7 +376,8 @@ def run_ours(args):
                      "nodes_expanded": r["nodes_expanded"], "rounds": r["rounds"],
                      "point_evals": r["point_evals"], "bound_evals": r["bound_evals"]},
            "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-           "clocks": clk, "plain_pop1": plain}
+           "clocks": clk, "plain_pop1": plain, "roofline_shared_atomics": roofline_atomics,
+           "roofline_l2": roofline_l2}
     out.update(extras)
     if rank == 0:
         print(json.dumps(out), flush=True)

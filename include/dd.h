@@ -67,7 +67,8 @@ typedef struct {
     int32_t pop_k;          /* intervals dequeued per BnB round (default 1 = Algorithm 1) */
     int32_t queue_capacity; /* BnB queue entries per window (default 8192)               */
     int32_t band_rows;      /* rows of the shared-memory IWE tile (default: from W)      */
-    int32_t threads;        /* threads per block of the IWE kernels (default 512)        */
+    int32_t threads;        /* threads per block of the IWE kernels, a multiple of 32    */
+                            /* up to 512 (default 512)                                    */
     int32_t max_rounds;     /* BnB round limit, DD_ERR_TIMEOUT beyond (default 1<<20)    */
     int32_t host_loop;      /* 0: each solve's rounds run as one CUDA graph with a       */
                             /*    conditional loop (no host round trips); 1: the host    */
@@ -394,6 +395,15 @@ double dd_serve_clock(void);
 #define DD_NOALLOC_SCRATCH_BYTES 18406400
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
                         int32_t nD, dd_i128* K, void* stream);
+
+/* Roofline denominators measured on the current device (no counterpart in
+ * the paper): shared-memory atomic increments per second (with the returned
+ * previous value, at random cells of a 41 KB array per block, every SM
+ * busy) and bytes per second streamed from a 32 MiB buffer resident in L2.
+ * Best of six launches each, timed with CUDA events on `stream` (NULL: the
+ * legacy default stream).  Allocates 32 MiB for the duration of the call.
+ * Errors: DD_ERR_ARG, DD_ERR_NO_DEVICE, DD_ERR_OOM, DD_ERR_CUDA. */
+int dd_probe_peaks(double* shared_atomics_per_s, double* l2_read_bytes_per_s, void* stream);
 
 /* A static description of a status code. */
 const char* dd_strerror(int status);

@@ -148,6 +148,7 @@ SIGNATURES = {
     "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "dd_contrast_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                            _P(dd_events), _VP, ctypes.c_int32, _VP, _VP]),
+    "dd_probe_peaks": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _VP]),
     "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -403,6 +404,14 @@ class Mlp:
         X, u_star = self._dev(X), self._dev(u_star)
         _check(load().dd_mlp_train_step(self.h, X.data_ptr(), u_star.data_ptr(), X.shape[0], float(lr),
                                         loss.data_ptr() if loss is not None else None), "dd_mlp_train_step")
+
+
+def dd_probe_peaks(stream_ptr=None):
+    """(shared-memory atomic increments/s, L2 read bytes/s) measured on the device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().dd_probe_peaks(ctypes.byref(a), ctypes.byref(b), _VP(stream_ptr) if stream_ptr else None),
+           "dd_probe_peaks")
+    return a.value, b.value
 
 
 def dd_contrast_noalloc(W, H, foe_x, foe_y, ev, D, stream_ptr=None):

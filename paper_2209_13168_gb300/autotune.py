@@ -22,7 +22,7 @@ DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_
 
 CANDIDATES = {
     "band_rows": [8, 16, 24, 38],
-    "threads": [256, 512, 1024],
+    "threads": [128, 256, 512],
     "pop_k": [8, 16, 32],
     "max_splits": [4, 8, 16],
 }
@@ -124,7 +124,7 @@ def main():
     table = load_table(args.out)
     cand = None
     if args.quick:
-        cand = {"band_rows": [16, 38], "threads": [512, 1024], "pop_k": [16, 32], "max_splits": [8, 16]}
+        cand = {"band_rows": [16, 38], "threads": [256, 512], "pop_k": [16, 32], "max_splits": [8, 16]}
     jobs = [("single", [window_config1()]), ("single", [window_config2()])]
     params = batch_params3()
     jobs.append(("batch", [batch_window3(i, params) for i in range(256)]))

@@ -339,12 +339,14 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
     for (int32_t j0 = 0; j0 < n; j0 += c->max_tasks) {
         const int32_t m = n - j0 < c->max_tasks ? n - j0 : c->max_tasks;
         int32_t nj = 0;
+        const int32_t cap = dd::split_cap(c->g, m * c->g.n_tiles);
         for (int32_t j = 0; j < m; j++) {
             dd::Task& t = c->h_tasks[j];
             t.D_lo = A[j0 + j];
             t.D_hi = B[j0 + j];
             t.kind = kind;
-            t.splits = kind == dd::TASK_BOUND ? dd::bound_splits(c->g, t.D_lo, t.D_hi, ev->tau) : 1;
+            const int32_t sp = dd::bound_splits(c->g, t.D_lo, t.D_hi, ev->tau);
+            t.splits = kind == dd::TASK_BOUND ? (sp < cap ? sp : cap) : 1;
         }
         for (int32_t j = m - 1; j >= 0; j--)              // heavier tasks first
             for (int32_t s = 0; s < c->h_tasks[j].splits; s++) {
@@ -666,7 +668,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     if (k.pop_k < 0 || k.pop_k > dd::MAX_POP || k.queue_capacity < 0 || k.band_rows < 0 || k.threads < 0 ||
         k.max_rounds < 0)
         return DD_ERR_ARG;
-    if (k.threads && (k.threads % 32 || k.threads > 1024)) return DD_ERR_ARG;
+    if (k.threads && (k.threads % 32 || k.threads > 512)) return DD_ERR_ARG;
     if (k.max_splits < 0 || k.max_splits > 64 || k.host_loop < 0) return DD_ERR_ARG;
     if (!k.pop_k) k.pop_k = 1;
     if (!k.queue_capacity) k.queue_capacity = 8192;
@@ -732,6 +734,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     if (rc == DD_OK && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && dd::eval_smem_setup(c->g) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && (c->eval_blocks = dd::eval_resident_blocks(c->g, c->threads)) <= 0) rc = DD_ERR_CUDA;
+    c->g.split_target = 2 * c->eval_blocks;
     if (rc == DD_OK) rc = ensure_windows(c, 1);
     if (rc != DD_OK) {
         dd_destroy(c);

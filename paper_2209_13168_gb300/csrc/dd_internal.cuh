@@ -132,7 +132,19 @@ struct Geom {
     int32_t W, H;
     float fx, fy;
     int32_t band_rows, n_tiles, n_tb, max_splits;
+    int32_t split_target;   // units a round needs before its bounds stop splitting (0: no cap)
+    int32_t pad;
 };
+
+// Splits a bound task may take in a round of `units` (task, row band) units:
+// none once the round alone fills the evaluation grid, else enough to reach
+// split_target.  A schedule choice only.
+__host__ __device__ inline int32_t split_cap(const Geom& g, int32_t units) {
+    if (g.split_target <= 0) return g.max_splits;
+    if (units >= g.split_target) return 1;
+    const int32_t c = (g.split_target + units - 1) / (units > 0 ? units : 1);
+    return c < 1 ? 1 : (c > g.max_splits ? g.max_splits : c);
+}
 
 // Row pitch of a shared-memory IWE tile: odd, so that the cells of one
 // column in consecutive rows fall in different shared-memory banks.

@@ -580,7 +580,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
 // IWE evaluation of the round's job list.  A grid of resident blocks takes
 // units (job, row band) from a counter; block 0 clears the other parity's
 // list and counter for the control blocks of this round.
-__global__ void __launch_bounds__(1024) k_eval(Geom g, EvalArgs a) {
+__global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     extern __shared__ uint32_t tile[];
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
@@ -752,13 +752,16 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
     a.splits = 1;
     tasks[0] = a;
     int nt = 1, n_jobs = 1;
+    int n_pieces = 0;
+    for (int i = 0; i + 1 < n_cut; i++) n_pieces += cut[i] < cut[i + 1];
+    const int cap = split_ok ? split_cap(g, (1 + n_pieces) * g.n_tiles) : 1;
     for (int i = 0; i + 1 < n_cut; i++) {
         if (!(cut[i] < cut[i + 1])) continue;
         Task b;                                   // bound of one piece
         b.D_lo = cut[i];
         b.D_hi = cut[i + 1];
         b.kind = TASK_BOUND;
-        b.splits = split_ok ? bound_splits(g, b.D_lo, b.D_hi, tau) : 1;
+        b.splits = split_ok ? min(cap, bound_splits(g, b.D_lo, b.D_hi, tau)) : 1;
         tasks[nt++] = b;
         n_jobs += b.splits;
     }
@@ -1151,11 +1154,12 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         // splits contributes that many jobs.
         if (s.phase != PH_DONE) {
             const int nt = s.n_tasks;
+            const int cap = split_ok ? split_cap(g, nt * g.n_tiles) : 1;
             int run = 0, base = 0;
             int total = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {
                 const int q = c0 + lane;
-                const int c = q < nt ? max(1, tasks[nt - 1 - q].splits) : 0;
+                const int c = q < nt ? max(1, min(cap, tasks[nt - 1 - q].splits)) : 0;
                 total += __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
             }
             if (lane == 0) base = atomicAdd(&sch->n_jobs[par ^ 1], total);
@@ -1163,7 +1167,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             for (int c0 = 0; c0 < nt; c0 += 32) {
                 const int q = c0 + lane;
                 const int t = nt - 1 - q;
-                const int c = q < nt ? max(1, tasks[t].splits) : 0;
+                const int c = q < nt ? max(1, min(cap, tasks[t].splits)) : 0;
                 const int incl = warp_incl_scan(c);
                 for (int k = 0; k < c; k++) {
                     Job j;

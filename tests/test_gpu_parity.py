@@ -167,7 +167,7 @@ def test_ragged_tiles_and_thread_counts():
     rng = np.random.default_rng(1)
     Ds = rng.uniform(-1, 1, 20).astype(np.float32)
     lo, hi = intervals(rng, 12, w.tau)
-    for kw in ({}, {"band_rows": 1}, {"band_rows": 7, "threads": 64}, {"band_rows": 61, "threads": 1024},
+    for kw in ({}, {"band_rows": 1}, {"band_rows": 7, "threads": 64}, {"band_rows": 61, "threads": 512},
                {"band_rows": 5, "threads": 96, "host_loop": 1}):
         check_contrast(w, Ds, want_iwe=True, **kw)
         check_bound(w, lo, hi, want_iwe=True, **kw)

@@ -267,3 +267,36 @@ def test_warm_start_argument_errors():
     r = ctx.solve(ev)
     assert r["D_warm"] == 0.0 and r["w_warm"] == 0.0
     ctx.close()
+
+
+def test_trained_model_gains_over_the_plain_search():
+    # The committed model (trained on 200k windows labelled by the exact
+    # solver) against Algorithm 1 from the centre on held-out windows: fewer
+    # rounds and nodes in total, and every pair of certificates consistent
+    # (each K_hat within the other's certified gap; identical where both are
+    # exact).
+    from paper_2209_13168_gb300 import warm_start
+    from synth.descent import WARM_EVAL_SEED
+    from synth.gpu import make_window_gpu
+    specs = warm_start.window_specs(128, WARM_EVAL_SEED + 50_000)
+    ws = [make_window_gpu(s) for s in specs]
+    evs = [dd.Events.of(w) for w in ws]
+    ctx = dd.Context(640, 480, 320.0, 240.0, pop_k=16, band_rows=38, threads=512)
+    m = dd.Mlp(path=warm_start.DEFAULT_MODEL)
+    ctx.set_warm_model(m)
+    rc0, plain = ctx.solve_batch(evs, [(-1.0, 1.0, 1e-4, 0.0)] * len(evs))
+    rc1, learned = ctx.solve_batch(evs, [(-1.0, 1.0, 1e-4, 0.0, "model")] * len(evs))
+    assert rc0 == dd.DD_OK and rc1 == dd.DD_OK
+    for a, b in zip(plain, learned):
+        assert a["K_hat"] <= b["K_hat"] + b["gap_K"] and b["K_hat"] <= a["K_hat"] + a["gap_K"]
+        if a["gap_K"] == 0 and b["gap_K"] == 0:
+            assert a["K_hat"] == b["K_hat"]
+    rounds = (sum(r["rounds"] for r in plain), sum(r["rounds"] for r in learned))
+    nodes = (sum(r["nodes_expanded"] for r in plain), sum(r["nodes_expanded"] for r in learned))
+    assert rounds[1] < 0.95 * rounds[0], rounds
+    assert nodes[1] < nodes[0], nodes
+    # the guesses are informative: most lie within their half-width of D*
+    inside = sum(abs(b["D_warm"] - a["D_star"]) <= b["w_warm"] for a, b in zip(plain, learned))
+    assert inside >= 0.8 * len(ws)
+    ctx.close()
+    m.close()
