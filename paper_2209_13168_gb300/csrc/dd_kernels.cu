@@ -313,8 +313,9 @@ __device__ __forceinline__ Seg seg_range(const Geom& g, float dx, float dy, floa
 }
 
 // One increment of a tile cell; the sum of squares grows by 2v + 1 from the
-// cell's previous count v.
-__device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, unsigned long long& C) {
+// cell's previous count v.  C counts increments (32 bits: callers fold it
+// into 64 bits often enough that it cannot wrap).
+__device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, uint32_t& C) {
     const uint32_t v = atomicAdd(cell, 1u);
     S += 2u * v + 1u;
     C++;
@@ -322,7 +323,7 @@ __device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, unsi
 
 __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float dn, float rm, float sa, float sb,
                                          int addr, int y0, int y1, uint32_t* tile, unsigned long long& S,
-                                         unsigned long long& C) {
+                                         uint32_t& C) {
     if (mode == SEG_ONE) {
         bump(&tile[addr], S, C);
         return;
@@ -398,30 +399,39 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     const int f_begin = (int)((long long)all * split / splits);
     const int total = (int)((long long)all * (split + 1) / splits);
     // Event index of position f of the concatenated runs.  Each thread visits
-    // increasing positions, so its bucket cursor only moves forward.
-    int cur_b = 0;
+    // increasing positions, so its cursor (the first position of the next run
+    // and the current run's offset from positions to event indices) only
+    // moves forward; positions stay below erange[MAX_TB + n_tb].
+    int cur_b = 0, next_f = erange[MAX_TB + 1], delta = erange[0] - erange[MAX_TB];
     auto event_at = [&](int f) {
-        while (cur_b + 1 < g.n_tb && f >= erange[MAX_TB + cur_b + 1]) cur_b++;
-        return erange[cur_b] + (f - erange[MAX_TB + cur_b]);
+        while (f >= next_f) {
+            cur_b++;
+            delta = erange[cur_b] - erange[MAX_TB + cur_b];
+            next_f = erange[MAX_TB + cur_b + 1];
+        }
+        return f + delta;
     };
 
     unsigned long long S = 0, C = 0;
     if (tk.kind == TASK_POINT) {
         const float D = tk.D_lo, gg = warp_g(D, tau);
+        uint32_t Ct = 0;                          // at most one increment per event
 #pragma unroll 4
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
             const Ev v = p.ev[event_at(f)];
             const float s = warp_s(D, v.t, gg);
             const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
-            if (uy < y0 || uy >= y1) continue;
+            if ((unsigned)(uy - y0) >= (unsigned)rows) continue;
             const int ux = cell_of(g.fx, __fsub_rn((float)v.x, g.fx), s);
-            if ((unsigned)ux < (unsigned)W) bump(&tile[(uy - y0) * P + ux], S, C);
+            if ((unsigned)ux < (unsigned)W) bump(&tile[(uy - y0) * P + ux], S, Ct);
         }
+        C = Ct;
     } else {
         const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
         // Warps take 32 positions at a time, one event per lane.
         for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
             const int f = base + lane;
+            uint32_t Ci = 0;                      // this pass's increments (folded below)
             Seg sg;
             sg.mode = SEG_NONE;
             sg.k0 = sg.count = sg.addr = 0;
@@ -439,18 +449,15 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
                     const float dx = __fsub_rn((float)v.x, g.fx);
                     const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
+                    const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
                     // Eq. (19): both end cells in the frame; counted by the tile of row ya.
-                    if (xa >= 0 && xa < W && ya >= 0 && ya < g.H && xb >= 0 && xb < W && yb >= 0 && yb < g.H &&
-                        ya >= y0 && ya < y1)
+                    if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
+                        ya_here)
                         full++;
                     if (xa == xb && ya == yb) {
                         // Both ends in one pixel: each cell coordinate is
                         // monotone in s, so the segment covers that pixel only.
-                        if (xa >= 0 && xa < W && ya >= y0 && ya < y1) {
-                            sg.mode = SEG_ONE;
-                            sg.count = 1;
-                            sg.addr = (ya - y0) * P + xa;
-                        }
+                        if ((unsigned)xa < (unsigned)W && ya_here) bump(&tile[(ya - y0) * P + xa], S, Ci);
                     } else {
                         const float2 r = p.rcp[e];
                         sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
@@ -458,10 +465,10 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 }
             }
             const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
-            if (cmax == 0) continue;
             if (cmax <= 2) {                      // short runs: each lane walks its own
                 for (int i = 0; i < sg.count; i++)
-                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, C);
+                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
+                C += Ci;
                 continue;
             }
             // Long runs: spread the (event, major cell) pairs over the lanes.
@@ -481,8 +488,9 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
                 const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
                 const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
-                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, C);
+                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
             }
+            C += Ci;
         }
     }
     __syncthreads();
