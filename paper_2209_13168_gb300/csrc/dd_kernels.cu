@@ -350,6 +350,8 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
 
 
 constexpr int MAX_TB = 8;    // time buckets of the event sort
+constexpr int QUEUE = 64;    // queued long-segment events per warp (a power of two, >= 63)
+constexpr int MAX_WARPS = 16;   // warps of a k_eval block (at most 512 threads)
 
 // Where one unit reads and writes.
 struct UnitPtrs {
@@ -374,7 +376,7 @@ struct UnitPtrs {
 // zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
-                                          int* erange, int* s_last) {
+                                          int* erange, int* s_last, int* queue) {
     const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -428,50 +430,40 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         C = Ct;
     } else {
         const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
-        // Warps take 32 positions at a time, one event per lane.
-        for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
-            const int f = base + lane;
-            uint32_t Ci = 0;                      // this pass's increments (folded below)
+        // End scales and end cells of event e's segment (the same binary32
+        // values whenever they are recomputed).
+        auto ends = [&](int e, float& dx, float& dy, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
+            const Ev v = p.ev[e];
+            dy = __fsub_rn((float)v.y, g.fy);
+            dx = __fsub_rn((float)v.x, g.fx);
+            const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+            sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+            sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+            ya = cell_of(g.fy, dy, sa);
+            yb = cell_of(g.fy, dy, sb);
+            xa = cell_of(g.fx, dx, sa);
+            xb = cell_of(g.fx, dx, sb);
+        };
+        // The cells of up to 32 segments, one event per lane (`valid`, with
+        // its end scales and cells): short runs walked by their own lane, long
+        // runs spread over the warp as (event, major cell) pairs.
+        auto walk = [&](int e, bool valid, float dx, float dy, float sa, float sb, int xa, int ya, int xb, int yb) {
+            uint32_t Ci = 0;
             Seg sg;
             sg.mode = SEG_NONE;
             sg.k0 = sg.count = sg.addr = 0;
             sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
-            if (f < total) {
-                const int e = event_at(f);
-                const Ev v = p.ev[e];
-                const float dy = __fsub_rn((float)v.y, g.fy);
-                const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-                const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-                const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-                const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
-                // Every covered cell lies between the rows of the two end
-                // cells (each cell coordinate is monotone in s).
-                if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
-                    const float dx = __fsub_rn((float)v.x, g.fx);
-                    const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
-                    const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
-                    // Eq. (19): both end cells in the frame; counted by the tile of row ya.
-                    if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
-                        ya_here)
-                        full++;
-                    if (xa == xb && ya == yb) {
-                        // Both ends in one pixel: each cell coordinate is
-                        // monotone in s, so the segment covers that pixel only.
-                        if ((unsigned)xa < (unsigned)W && ya_here) bump(&tile[(ya - y0) * P + xa], S, Ci);
-                    } else {
-                        const float2 r = p.rcp[e];
-                        sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
-                    }
-                }
+            if (valid) {
+                const float2 r = p.rcp[e];
+                sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
             }
             const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
-            if (cmax <= 2) {                      // short runs: each lane walks its own
+            if (cmax <= 2) {
                 for (int i = 0; i < sg.count; i++)
                     seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
                 C += Ci;
-                continue;
+                return;
             }
-            // Long runs: spread the (event, major cell) pairs over the lanes.
             const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
             const int tot = __shfl_sync(0xffffffffu, incl, 31);
             for (int c0 = 0; c0 < tot; c0 += 32) {
@@ -491,6 +483,69 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
             }
             C += Ci;
+        };
+        // A queued event's segment, recomputed (the same binary32 values).
+        auto walk_queued = [&](int e, bool valid) {
+            float dx = 0.0f, dy = 0.0f, sa = 0.0f, sb = 0.0f;
+            int xa = 0, ya = 0, xb = 0, yb = 0;
+            if (valid) ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+            walk(e, valid, dx, dy, sa, sb, xa, ya, xb, yb);
+        };
+        // Warps take 32 positions at a time, one event per lane.  A segment
+        // within one pixel is counted at once; an event whose segment spans
+        // more pixels is queued (a ring of 64 event indices per warp), and
+        // every 32 queued events are walked together, so the walk runs on
+        // full warps.
+        int* q = queue + wid * QUEUE;
+        int q_head = 0, q_tail = 0;
+        for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
+            const int f = base + lane;
+            bool pend = false;
+            int e = 0;
+            if (f < total) {
+                e = event_at(f);
+                float dx, dy, sa, sb;
+                int xa, ya, xb, yb;
+                ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+                // Every covered cell lies between the rows of the two end
+                // cells (each cell coordinate is monotone in s).
+                if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                    const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
+                    // Eq. (19): both end cells in the frame; counted by the tile of row ya.
+                    if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
+                        ya_here)
+                        full++;
+                    if (xa == xb && ya == yb) {
+                        // Both ends in one pixel: each cell coordinate is
+                        // monotone in s, so the segment covers that pixel only.
+                        if ((unsigned)xa < (unsigned)W && ya_here) {
+                            uint32_t Ci = 0;
+                            bump(&tile[(ya - y0) * P + xa], S, Ci);
+                            C += Ci;
+                        }
+                    } else {
+                        pend = true;
+                    }
+                }
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, pend);
+            if (pend) q[(q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1)] = e;
+            q_tail += __popc(pm);
+            if (q_tail - q_head >= 32) {
+                __syncwarp();                     // the queued indices are visible to the warp
+                const int ew = q[(q_head + lane) & (QUEUE - 1)];
+                __syncwarp();                     // read before the next pass may overwrite
+                q_head += 32;
+                walk_queued(ew, true);
+            }
+        }
+        while (q_tail > q_head) {                 // the rest of the queue
+            const int n = min(32, q_tail - q_head);
+            __syncwarp();
+            const int ew = lane < n ? q[(q_head + lane) & (QUEUE - 1)] : 0;
+            __syncwarp();
+            q_head += n;
+            walk_queued(ew, lane < n);
         }
     }
     __syncthreads();
@@ -590,6 +645,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
 // list and counter for the control blocks of this round.
 __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     extern __shared__ uint32_t tile[];
+    __shared__ int queue[MAX_WARPS * QUEUE];
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
     __shared__ int s_unit, s_last;
@@ -627,7 +683,7 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * g.W * g.H : nullptr;
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
         p.sums = a.mg.sums ? a.mg.sums + (size_t)jb.task * g.n_tiles : nullptr;
-        eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last);
+        eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last, queue);
         __syncthreads();                          // the unit's readers are done; s_unit is set
     }
 }
