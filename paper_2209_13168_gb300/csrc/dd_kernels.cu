@@ -312,20 +312,28 @@ __device__ __forceinline__ Seg seg_range(const Geom& g, float dx, float dy, floa
     return s;
 }
 
-// One increment of a tile cell; the sum of squares grows by 2v + 1 from the
-// cell's previous count v.  C counts increments (32 bits: callers fold it
-// into 64 bits often enough that it cannot wrap).
+// One increment of a tile cell.  Sparse images (at most a few increments per
+// cell): the sum of squares grows by 2v + 1 from the cell's previous count v
+// and C counts increments (32 bits: callers fold it into 64 bits often
+// enough that it cannot wrap).  Dense images (many increments per cell): the
+// increment alone, the sums taken from the tile afterwards.
+template <bool DENSE>
 __device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, uint32_t& C) {
-    const uint32_t v = atomicAdd(cell, 1u);
-    S += 2u * v + 1u;
-    C++;
+    if (DENSE) {
+        atomicAdd(cell, 1u);
+    } else {
+        const uint32_t v = atomicAdd(cell, 1u);
+        S += 2u * v + 1u;
+        C++;
+    }
 }
 
+template <bool DENSE>
 __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float dn, float rm, float sa, float sb,
                                          int addr, int y0, int y1, uint32_t* tile, unsigned long long& S,
                                          uint32_t& C) {
     if (mode == SEG_ONE) {
-        bump(&tile[addr], S, C);
+        bump<DENSE>(&tile[addr], S, C);
         return;
     }
     const bool major_x = mode == SEG_X;
@@ -339,13 +347,38 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
     const int j1 = cell_of(fn, dn, lo), j2 = cell_of(fn, dn, hi);
     if (major_x) {
         const int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), g.H - 1), y1 - 1);
-        for (int j = j0; j <= jn; j++) bump(&tile[(j - y0) * tile_pitch(g) + k], S, C);
+        for (int j = j0; j <= jn; j++) bump<DENSE>(&tile[(j - y0) * tile_pitch(g) + k], S, C);
     } else {
         const int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), g.W - 1);
         uint32_t* row = tile + (k - y0) * tile_pitch(g);
-        for (int j = j0; j <= jn; j++) bump(&row[j], S, C);
+        for (int j = j0; j <= jn; j++) bump<DENSE>(&row[j], S, C);
     }
 }
+
+// Position-to-event cursor over a unit's candidate runs (erange: first
+// event of each bucket's run, then each run's offset in the concatenation).
+// Each thread visits increasing positions, so the cursor (the first
+// position of the next run and the current run's offset from positions to
+// event indices) only moves forward; positions stay below
+// erange[MAX_TB + n_tb].
+struct Cursor {
+    const int* erange;
+    int cur_b, next_f, delta;
+    __device__ __forceinline__ Cursor(const int* er, int max_tb) : erange(er), cur_b(0) {
+        next_f = er[max_tb + 1];
+        delta = er[0] - er[max_tb];
+        mtb = max_tb;
+    }
+    int mtb;
+    __device__ __forceinline__ int at(int f) {
+        while (f >= next_f) {
+            cur_b++;
+            delta = erange[cur_b] - erange[mtb + cur_b];
+            next_f = erange[mtb + cur_b + 1];
+        }
+        return f + delta;
+    }
+};
 
 
 
@@ -365,15 +398,143 @@ struct UnitPtrs {
     Partial* sums;                // split jobs: sums of the splits per tile
 };
 
+// Bound images with at least this many covered cells per event (estimated
+// as in bound_splits) are dense: their increments skip the returned count
+// and the tile's sums are taken in one pass afterwards.
+constexpr float DENSE_CELLS = 4.0f;
+
+// Eqs. (16) and (19) for the unit's share of events, positions [f_begin,
+// total): Hbar into the tile, N_full into `full`, and (sparse) S and C.
+template <bool DENSE>
+__device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, const Task& tk, float tau, uint32_t* tile,
+                                           int* queue, int y0, int y1, int f_begin, int total, Cursor& cur,
+                                           unsigned long long& S, unsigned long long& C, unsigned long long& full) {
+    const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
+    // End scales and end cells of event e's segment (the same binary32
+    // values whenever they are recomputed).
+    auto ends = [&](int e, float& dx, float& dy, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
+        const Ev v = p.ev[e];
+        dy = __fsub_rn((float)v.y, g.fy);
+        dx = __fsub_rn((float)v.x, g.fx);
+        const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+        sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+        sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+        ya = cell_of(g.fy, dy, sa);
+        yb = cell_of(g.fy, dy, sb);
+        xa = cell_of(g.fx, dx, sa);
+        xb = cell_of(g.fx, dx, sb);
+    };
+    // The cells of up to 32 queued segments, one event per lane (`valid`):
+    // short runs walked by their own lane, long runs spread over the warp as
+    // (event, major cell) pairs.
+    auto walk = [&](int e, bool valid) {
+        uint32_t Ci = 0;
+        Seg sg;
+        sg.mode = SEG_NONE;
+        sg.k0 = sg.count = sg.addr = 0;
+        sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
+        if (valid) {
+            float dx, dy, sa, sb;
+            int xa, ya, xb, yb;
+            ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+            const float2 r = p.rcp[e];
+            sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+        }
+        const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
+        if (cmax <= 2) {
+            for (int i = 0; i < sg.count; i++)
+                seg_cell<DENSE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
+            C += Ci;
+            return;
+        }
+        const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        for (int c0 = 0; c0 < tot; c0 += 32) {
+            const int gi = c0 + lane;
+            int o = 0;                            // owner: first lane whose inclusive sum exceeds gi
+            for (int step = 16; step > 0; step >>= 1) {
+                const int probe = __shfl_sync(0xffffffffu, incl, o + step - 1);
+                if (probe <= gi) o += step;
+            }
+            const int om = __shfl_sync(0xffffffffu, sg.mode, o);
+            const int ok = __shfl_sync(0xffffffffu, sg.k0 - excl, o);
+            const int oa = __shfl_sync(0xffffffffu, sg.addr, o);
+            const float odn = __shfl_sync(0xffffffffu, sg.dn, o);
+            const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
+            const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
+            const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
+            if (gi < tot) seg_cell<DENSE>(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
+        }
+        C += Ci;
+    };
+    // Warps take 32 positions at a time, one event per lane.  A segment
+    // within one pixel is counted at once; an event whose segment spans more
+    // pixels is queued (a ring of 64 event indices per warp), and every 32
+    // queued events are walked together, so the walk runs on full warps.
+    int* q = queue + wid * QUEUE;
+    int q_head = 0, q_tail = 0;
+    for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
+        const int f = base + lane;
+        bool pend = false;
+        int e = 0;
+        if (f < total) {
+            e = cur.at(f);
+            float dx, dy, sa, sb;
+            int xa, ya, xb, yb;
+            ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+            // Every covered cell lies between the rows of the two end cells
+            // (each cell coordinate is monotone in s).
+            if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
+                // Eq. (19): both end cells in the frame; counted by the tile of row ya.
+                if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
+                    ya_here)
+                    full++;
+                if (xa == xb && ya == yb) {
+                    // Both ends in one pixel: each cell coordinate is monotone
+                    // in s, so the segment covers that pixel only.
+                    if ((unsigned)xa < (unsigned)W && ya_here) {
+                        uint32_t Ci = 0;
+                        bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
+                        C += Ci;
+                    }
+                } else {
+                    pend = true;
+                }
+            }
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, pend);
+        if (pend) q[(q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1)] = e;
+        q_tail += __popc(pm);
+        if (q_tail - q_head >= 32) {
+            __syncwarp();                         // the queued indices are visible to the warp
+            const int ew = q[(q_head + lane) & (QUEUE - 1)];
+            __syncwarp();                         // read before the next pass may overwrite
+            q_head += 32;
+            walk(ew, true);
+        }
+    }
+    while (q_tail > q_head) {                     // the rest of the queue
+        const int n = min(32, q_tail - q_head);
+        __syncwarp();
+        const int ew = lane < n ? q[(q_head + lane) & (QUEUE - 1)] : 0;
+        __syncwarp();
+        q_head += n;
+        walk(ew, lane < n);
+    }
+}
+
 // One unit: split `split` of `splits` of one task's row band `ti`.  The block
 // scatters its share of the events that can reach the band's rows into the
-// shared tile.  Each increment returns the cell's previous count v, and the
-// band's sum of squares grows by (v + 1)^2 - v^2 = 2v + 1, so S needs no pass
-// over the tile: an unsplit task only clears it.  A split task adds its tile
-// into the L2 accumulator; each addition of u onto a count w adds
-// (w + u)^2 - w^2 to S, so the splits' sums add up to the band's, and the
-// last split to finish clears the accumulated band.  The tile arrives
-// zeroed and leaves zeroed.
+// shared tile.  Sparse images: each increment returns the cell's previous
+// count v and the band's sum of squares grows by (v + 1)^2 - v^2 = 2v + 1,
+// so the tile is only cleared afterwards; dense bound images: one pass over
+// the tile takes S and C and clears it.  A split task adds its tile into the
+// L2 accumulator; each addition of u onto a count w adds (w + u)^2 - w^2 to
+// S, so the splits' sums add up to the band's, and the last split to finish
+// clears the accumulated band.  The tile arrives zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
                                           int* erange, int* s_last, int* queue) {
@@ -400,153 +561,32 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     const int all = erange[MAX_TB + g.n_tb];
     const int f_begin = (int)((long long)all * split / splits);
     const int total = (int)((long long)all * (split + 1) / splits);
-    // Event index of position f of the concatenated runs.  Each thread visits
-    // increasing positions, so its cursor (the first position of the next run
-    // and the current run's offset from positions to event indices) only
-    // moves forward; positions stay below erange[MAX_TB + n_tb].
-    int cur_b = 0, next_f = erange[MAX_TB + 1], delta = erange[0] - erange[MAX_TB];
-    auto event_at = [&](int f) {
-        while (f >= next_f) {
-            cur_b++;
-            delta = erange[cur_b] - erange[MAX_TB + cur_b];
-            next_f = erange[MAX_TB + cur_b + 1];
-        }
-        return f + delta;
-    };
+    Cursor cur(erange, MAX_TB);
 
     unsigned long long S = 0, C = 0;
+    bool dense = false;
     if (tk.kind == TASK_POINT) {
         const float D = tk.D_lo, gg = warp_g(D, tau);
         uint32_t Ct = 0;                          // at most one increment per event
 #pragma unroll 4
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
-            const Ev v = p.ev[event_at(f)];
+            const Ev v = p.ev[cur.at(f)];
             const float s = warp_s(D, v.t, gg);
             const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
             if ((unsigned)(uy - y0) >= (unsigned)rows) continue;
             const int ux = cell_of(g.fx, __fsub_rn((float)v.x, g.fx), s);
-            if ((unsigned)ux < (unsigned)W) bump(&tile[(uy - y0) * P + ux], S, Ct);
+            if ((unsigned)ux < (unsigned)W) bump<false>(&tile[(uy - y0) * P + ux], S, Ct);
         }
         C = Ct;
     } else {
-        const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
-        // End scales and end cells of event e's segment (the same binary32
-        // values whenever they are recomputed).
-        auto ends = [&](int e, float& dx, float& dy, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
-            const Ev v = p.ev[e];
-            dy = __fsub_rn((float)v.y, g.fy);
-            dx = __fsub_rn((float)v.x, g.fx);
-            const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-            sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-            sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-            ya = cell_of(g.fy, dy, sa);
-            yb = cell_of(g.fy, dy, sb);
-            xa = cell_of(g.fx, dx, sa);
-            xb = cell_of(g.fx, dx, sb);
-        };
-        // The cells of up to 32 segments, one event per lane (`valid`, with
-        // its end scales and cells): short runs walked by their own lane, long
-        // runs spread over the warp as (event, major cell) pairs.
-        auto walk = [&](int e, bool valid, float dx, float dy, float sa, float sb, int xa, int ya, int xb, int yb) {
-            uint32_t Ci = 0;
-            Seg sg;
-            sg.mode = SEG_NONE;
-            sg.k0 = sg.count = sg.addr = 0;
-            sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
-            if (valid) {
-                const float2 r = p.rcp[e];
-                sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
-            }
-            const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
-            if (cmax <= 2) {
-                for (int i = 0; i < sg.count; i++)
-                    seg_cell(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
-                C += Ci;
-                return;
-            }
-            const int incl = warp_incl_scan(sg.count), excl = incl - sg.count;
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            for (int c0 = 0; c0 < tot; c0 += 32) {
-                const int gi = c0 + lane;
-                int o = 0;                        // owner: first lane whose inclusive sum exceeds gi
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int probe = __shfl_sync(0xffffffffu, incl, o + step - 1);
-                    if (probe <= gi) o += step;
-                }
-                const int om = __shfl_sync(0xffffffffu, sg.mode, o);
-                const int ok = __shfl_sync(0xffffffffu, sg.k0 - excl, o);
-                const int oa = __shfl_sync(0xffffffffu, sg.addr, o);
-                const float odn = __shfl_sync(0xffffffffu, sg.dn, o);
-                const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
-                const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
-                const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
-                if (gi < tot) seg_cell(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
-            }
-            C += Ci;
-        };
-        // A queued event's segment, recomputed (the same binary32 values).
-        auto walk_queued = [&](int e, bool valid) {
-            float dx = 0.0f, dy = 0.0f, sa = 0.0f, sb = 0.0f;
-            int xa = 0, ya = 0, xb = 0, yb = 0;
-            if (valid) ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
-            walk(e, valid, dx, dy, sa, sb, xa, ya, xb, yb);
-        };
-        // Warps take 32 positions at a time, one event per lane.  A segment
-        // within one pixel is counted at once; an event whose segment spans
-        // more pixels is queued (a ring of 64 event indices per warp), and
-        // every 32 queued events are walked together, so the walk runs on
-        // full warps.
-        int* q = queue + wid * QUEUE;
-        int q_head = 0, q_tail = 0;
-        for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
-            const int f = base + lane;
-            bool pend = false;
-            int e = 0;
-            if (f < total) {
-                e = event_at(f);
-                float dx, dy, sa, sb;
-                int xa, ya, xb, yb;
-                ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
-                // Every covered cell lies between the rows of the two end
-                // cells (each cell coordinate is monotone in s).
-                if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
-                    const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
-                    // Eq. (19): both end cells in the frame; counted by the tile of row ya.
-                    if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
-                        ya_here)
-                        full++;
-                    if (xa == xb && ya == yb) {
-                        // Both ends in one pixel: each cell coordinate is
-                        // monotone in s, so the segment covers that pixel only.
-                        if ((unsigned)xa < (unsigned)W && ya_here) {
-                            uint32_t Ci = 0;
-                            bump(&tile[(ya - y0) * P + xa], S, Ci);
-                            C += Ci;
-                        }
-                    } else {
-                        pend = true;
-                    }
-                }
-            }
-            const unsigned pm = __ballot_sync(0xffffffffu, pend);
-            if (pend) q[(q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1)] = e;
-            q_tail += __popc(pm);
-            if (q_tail - q_head >= 32) {
-                __syncwarp();                     // the queued indices are visible to the warp
-                const int ew = q[(q_head + lane) & (QUEUE - 1)];
-                __syncwarp();                     // read before the next pass may overwrite
-                q_head += 32;
-                walk_queued(ew, true);
-            }
-        }
-        while (q_tail > q_head) {                 // the rest of the queue
-            const int n = min(32, q_tail - q_head);
-            __syncwarp();
-            const int ew = lane < n ? q[(q_head + lane) & (QUEUE - 1)] : 0;
-            __syncwarp();
-            q_head += n;
-            walk_queued(ew, lane < n);
-        }
+        // The scale change at t = 0 times a typical offset, (W + H)/4 (the
+        // estimate bound_splits uses): covered cells per event.
+        const float gl = 1.0f / (1.0f - tk.D_lo * tau), gh = 1.0f / (1.0f - tk.D_hi * tau);
+        dense = 1.0f + fabsf(gh - gl) * 0.25f * (float)(g.W + g.H) >= DENSE_CELLS;
+        if (dense)
+            bound_pass<true>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
+        else
+            bound_pass<false>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
     }
     __syncthreads();
 
@@ -555,17 +595,29 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
     // take columns.
     if (splits == 1) {
-        for (int r = wid; r < rows; r += nw)
-            for (int c = lane; c < W; c += 32) {
-                if (out) out[r * W + c] = tile[r * P + c];
-                tile[r * P + c] = 0u;
-            }
+        if (dense) {
+            S = Cl = 0;
+            for (int r = wid; r < rows; r += nw)
+                for (int c = lane; c < W; c += 32) {
+                    const uint32_t v = tile[r * P + c];
+                    if (out) out[r * W + c] = v;
+                    tile[r * P + c] = 0u;
+                    S += (unsigned long long)v * v;
+                    Cl += v;
+                }
+        } else {
+            for (int r = wid; r < rows; r += nw)
+                for (int c = lane; c < W; c += 32) {
+                    if (out) out[r * W + c] = tile[r * P + c];
+                    tile[r * P + c] = 0u;
+                }
+        }
     } else {
         uint32_t* acc = p.acc + (size_t)y0 * W;
         // Splits of one band finish together: each starts its pass at its own
         // row so that they add into different words at a time.
         const int rot = (int)((long long)rows * split / splits);
-        S = 0;
+        S = Cl = 0;
         for (int q = wid; q < rows; q += nw) {
             const int r = q + rot < rows ? q + rot : q + rot - rows;
             for (int c = lane; c < W; c += 32) {
@@ -574,6 +626,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                     tile[r * P + c] = 0u;
                     const unsigned long long w = atomicAdd(&acc[r * W + c], v);
                     S += (2ull * w + v) * v;
+                    Cl += v;
                 }
             }
         }
