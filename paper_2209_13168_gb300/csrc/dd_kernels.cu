@@ -481,12 +481,17 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
         int e = 0;
         if (f < total) {
             e = cur.at(f);
-            float dx, dy, sa, sb;
-            int xa, ya, xb, yb;
-            ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+            const Ev v = p.ev[e];
+            const float dy = __fsub_rn((float)v.y, g.fy);
+            const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+            const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+            const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+            const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
             // Every covered cell lies between the rows of the two end cells
             // (each cell coordinate is monotone in s).
             if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                const float dx = __fsub_rn((float)v.x, g.fx);
+                const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
                 const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
                 // Eq. (19): both end cells in the frame; counted by the tile of row ya.
                 if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
@@ -985,20 +990,29 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     const int64_t M = s.M;
     const int n_tasks = s.n_tasks;
 
-    for (int t = wid; t < n_tasks; t += nw) {
-        unsigned long long S = 0, C = 0, F = 0;
-        for (int i = lane; i < g.n_tiles; i += 32) {
-            const Partial p = part[t * g.n_tiles + i];
-            S += p.S;
-            C += p.cells;
-            F += p.full;
+    // Each warp reduces the row-band partials of four tasks at a time (their
+    // loads issued together).
+    for (int t0 = 4 * wid; t0 < n_tasks; t0 += 4 * nw) {
+        unsigned long long S[4], C[4], F[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            S[u] = C[u] = F[u] = 0;
+            if (t0 + u < n_tasks)
+                for (int i = lane; i < g.n_tiles; i += 32) {
+                    const Partial p = part[(t0 + u) * g.n_tiles + i];
+                    S[u] += p.S;
+                    C[u] += p.cells;
+                    F[u] += p.full;
+                }
         }
-        S = warp_sum(S);
-        C = warp_sum(C);
-        F = warp_sum(F);
-        if (lane == 0) {
-            key[t] = key_of(M, S, tasks[t].kind == TASK_POINT ? C : F);
-            cells[t] = C;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const unsigned long long s_ = warp_sum(S[u]), c_ = warp_sum(C[u]), f_ = warp_sum(F[u]);
+            const int t = t0 + u;
+            if (lane == 0 && t < n_tasks) {
+                key[t] = key_of(M, s_, tasks[t].kind == TASK_POINT ? c_ : f_);
+                cells[t] = c_;
+            }
         }
     }
     __syncthreads();
