@@ -600,22 +600,42 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
     // take columns.
     if (splits == 1) {
-        if (dense) {
-            S = Cl = 0;
+        if (out) {
+            if (dense) S = Cl = 0;
             for (int r = wid; r < rows; r += nw)
                 for (int c = lane; c < W; c += 32) {
                     const uint32_t v = tile[r * P + c];
-                    if (out) out[r * W + c] = v;
+                    out[r * W + c] = v;
                     tile[r * P + c] = 0u;
+                    if (dense) {
+                        S += (unsigned long long)v * v;
+                        Cl += v;
+                    }
+                }
+        } else {
+            // The band's rows are contiguous in the tile (the padding column
+            // of an odd pitch stays zero): 16-byte words, then the tail.
+            const int words = rows * P, quads = words >> 2;
+            uint4* t4 = reinterpret_cast<uint4*>(tile);
+            if (dense) {
+                S = Cl = 0;
+                for (int i = threadIdx.x; i < quads; i += blockDim.x) {
+                    const uint4 v = t4[i];
+                    t4[i] = make_uint4(0u, 0u, 0u, 0u);
+                    S += (unsigned long long)v.x * v.x + (unsigned long long)v.y * v.y +
+                         (unsigned long long)v.z * v.z + (unsigned long long)v.w * v.w;
+                    Cl += (unsigned long long)v.x + v.y + v.z + v.w;
+                }
+                for (int i = 4 * quads + threadIdx.x; i < words; i += blockDim.x) {
+                    const uint32_t v = tile[i];
+                    tile[i] = 0u;
                     S += (unsigned long long)v * v;
                     Cl += v;
                 }
-        } else {
-            for (int r = wid; r < rows; r += nw)
-                for (int c = lane; c < W; c += 32) {
-                    if (out) out[r * W + c] = tile[r * P + c];
-                    tile[r * P + c] = 0u;
-                }
+            } else {
+                for (int i = threadIdx.x; i < quads; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+                for (int i = 4 * quads + threadIdx.x; i < words; i += blockDim.x) tile[i] = 0u;
+            }
         }
     } else {
         uint32_t* acc = p.acc + (size_t)y0 * W;
@@ -702,7 +722,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
 // units (job, row band) from a counter; block 0 clears the other parity's
 // list and counter for the control blocks of this round.
 __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
-    extern __shared__ uint32_t tile[];
+    extern __shared__ __align__(16) uint32_t tile[];
     __shared__ int queue[MAX_WARPS * QUEUE];
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
