@@ -106,6 +106,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (every rank passes its own)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank solves its own replica of the workload)."""
+    return world * units_per_rank / seconds
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -266,14 +282,10 @@ def run_ours(args):
     st = ctx.stats()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     r = results[-1]
     assert all(x["K_hat"] == r["K_hat"] and x["D_star"] == r["D_star"] for x in results)
-    value = world * args.steps / total_s
+    value = whole_job_rate(args.steps, world, total_s)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -288,14 +300,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(args.steps):
             rh = ctx.solve(hev)
-        el = time.perf_counter() - t0
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         sh = ctx.stats()
         assert rh["K_hat"] == r["K_hat"]
-        if dist:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * args.steps / el, "unit": UNIT,
+        e2e = {"value": whole_job_rate(args.steps, world, el), "unit": UNIT,
                "h2d_bytes_per_step": sh["h2d_bytes"] // args.steps,
                "d2h_bytes_per_step": sh["d2h_bytes"] // args.steps}
 

@@ -88,11 +88,13 @@ def test_batch_reports_a_malformed_window_and_solves_the_others():
 
 
 def test_uneven_256_window_batch_sampled_against_oracle():
-    # The 256-window workload (640x480, N log-uniform in [5k, 200k]): every
+    # The 256-window workload (640x480, N log-uniform in [5k, 200k]) in the
+    # configuration bench.py times (the autotuned batch knobs): every 17th
     # window against its single-window GPU solve, a sample against the oracle.
     params = batch_params3()
     ws = [batch_window3(i, params) for i in range(256)]
-    ctx = dd.Context(640, 480, 320.0, 240.0, pop_k=8)
+    ctx = dd.Context.tuned(640, 480, 320.0, 240.0, sum(w.n for w in ws) / len(ws), mode="batch")
+    pop_k = ctx.cfg.pop_k
     evs = [dd.Events.of(w, device="cuda") for w in ws]
     rc, res = ctx.solve_batch(evs)
     assert rc == dd.DD_OK
@@ -102,7 +104,7 @@ def test_uneven_256_window_batch_sampled_against_oracle():
             assert one[k] == res[i][k], (i, k)
     order = np.argsort(params[0])
     for i in list(order[:3]) + [int(order[128])]:
-        want = O.solve(O.Window.of(ws[i]), -1.0, 1.0, 1e-4, 0.0, 8)
+        want = O.solve(O.Window.of(ws[i]), -1.0, 1.0, 1e-4, 0.0, pop_k)
         for k in KEYS:
             assert res[i][k] == want[k], (i, k)
     for i in range(256):

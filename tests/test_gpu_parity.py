@@ -134,6 +134,23 @@ def test_solve_config2(c2, pop_k):
     assert abs(r["D_star"] - 0.35) <= 0.02
 
 
+def test_solve_config2_in_the_benchmark_configuration(c2):
+    # The context bench.py times: the autotuned knobs for this geometry and
+    # size (pop width, band rows, threads, split cap), solved as one graph.
+    ctx = dd.Context.tuned(c2.W, c2.H, c2.foe_x, c2.foe_y, c2.n, mode="single")
+    pop_k = ctx.cfg.pop_k
+    ev = dd.Events.of(c2, device="cuda")
+    got = ctx.solve(ev, -1.0, 1.0, 1e-4, 0.0, trace_cap=4096)
+    plain = ctx.solve(ev)                         # the graph path, as timed
+    want = O.solve(O.Window.of(c2), -1.0, 1.0, 1e-4, 0.0, pop_k, trace_cap=4096)
+    for k in ("D_star", "D_end", "K_hat", "gap_K", "nodes_expanded", "point_evals", "bound_evals",
+              "event_warps", "cell_increments", "bound_increments", "rounds", "max_queue"):
+        assert got[k] == want[k], (k, got[k], want[k])
+        assert plain[k] == want[k], (k, plain[k], want[k])
+    assert got["trace"] == want["trace"]
+    ctx.close()
+
+
 def test_solve_with_gamma_and_narrow_range(c1):
     check_solve(c1, 1, gamma=0.025)
     check_solve(c1, 2, D_lo=0.15, D_hi=0.25, tol=1e-5)
