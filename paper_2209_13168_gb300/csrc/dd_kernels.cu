@@ -217,7 +217,8 @@ cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_window
 // An event at row y can reach the rows only if (y - FOE_y) s meets them for
 // some s in that range; the rows that can are a contiguous range of the
 // bucket's row-sorted events.  Binary32 with margins far above its rounding
-// error (1e-4 relative on s, 1e-3 of a bucket in t, one row): a superset.
+// error (1e-4 relative on s, 1e-3 of a bucket in t, 1/16 pixel on the band's
+// edges): a superset.
 __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float Dl, float Dh, float tau,
                                    float bscale, int b, int y0, int y1, int& e0, int& e1) {
     const float tl = fmaxf(0.0f, __fdividef((float)b - 1e-3f, bscale));
@@ -235,7 +236,10 @@ __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float 
     const float B = (float)(y1 - 1) + 0.5625f - g.fy;
     const float dylo = __fdividef(A, A >= 0.0f ? smax : smin);
     const float dyhi = __fdividef(B, B >= 0.0f ? smin : smax);
-    const float rl = floorf(g.fy + dylo) - 1.0f, rh = ceilf(g.fy + dyhi) + 1.0f;
+    // The margins above exceed the few-ulp error of this arithmetic, and
+    // rounding a bound that is off by less than a row outward to an integer
+    // row never drops a row the exact bound admits.
+    const float rl = floorf(g.fy + dylo), rh = ceilf(g.fy + dyhi);
     if (rh < 0.0f || rl > (float)(g.H - 1)) {
         e0 = e1 = 0;
         return;

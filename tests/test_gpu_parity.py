@@ -191,6 +191,22 @@ def test_ragged_tiles_and_thread_counts():
         check_solve(w, 3, trace=True, **kw)
 
 
+@pytest.mark.parametrize("band_rows", [1, 3, 16])
+def test_band_candidates_at_the_ends_of_the_domain(band_rows):
+    # Which events a row band reads is decided from binary32 bounds with
+    # margins: at the ends of the domain (D tau from -50 to 0.745), with a
+    # non-integer FOE and dense events, every image must still equal the
+    # oracle's.
+    w = make_window(200, 150, 99.37, 74.81, 16000, 800, 4000, 0.6, 0.5, 77)
+    tau = w.tau
+    Ds = np.array([-100.0, -10.0, -1.0, 0.0, 0.5, 1.0, 1.4, 0.745 / tau], np.float32)
+    lo = np.array([-100.0, -2.0, 1.2, 1.48, 0.0], np.float32)
+    hi = np.array([-99.0, 1.49, 1.49, 0.745 / tau, 1e-3], np.float32)
+    for want_iwe in (True, False):            # images copied out, or only keys
+        check_contrast(w, Ds, want_iwe, band_rows=band_rows)
+        check_bound(w, lo, hi, want_iwe, band_rows=band_rows)
+
+
 def test_degenerate_windows():
     empty = make_window(40, 30, 20.0, 15.0, 0, 1, 0, 0.3, 0.5, seed=1)
     check_solve(empty, 1)
