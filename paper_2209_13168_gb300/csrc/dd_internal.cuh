@@ -12,10 +12,12 @@ namespace dd {
 
 typedef __int128 i128;
 
-// One event after ingest: pixel coordinates and the time since t0.
-struct __align__(8) Ev {
-    int16_t x, y;
-    float t;
+// One event after ingest: its offsets from the FOE as the warp uses them
+// (binary32 x - FOE_x and y - FOE_y) and its time since t0 (binary32
+// t - t0); one 16-byte load.
+struct __align__(16) Ev {
+    float dx, dy, t;
+    int32_t pad;
 };
 
 enum TaskKind : int32_t { TASK_POINT = 0, TASK_BOUND = 1 };

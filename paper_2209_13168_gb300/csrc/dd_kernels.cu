@@ -186,11 +186,12 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
         const int key = event_key(g, yi, tr, bscale);
         const int pos = base[key] + atomicAdd(&h[key], 1);
         Ev e;
-        e.x = (int16_t)xi;
-        e.y = (int16_t)yi;
+        e.dx = __fsub_rn((float)xi, g.fx);
+        e.dy = __fsub_rn((float)yi, g.fy);
         e.t = tr;
+        e.pad = 0;
         o[pos] = e;
-        rc[pos] = make_float2(__frcp_rn(__fsub_rn((float)xi, g.fx)), __frcp_rn(__fsub_rn((float)yi, g.fy)));
+        rc[pos] = make_float2(__frcp_rn(e.dx), __frcp_rn(e.dy));
     }
 }
 
@@ -420,8 +421,8 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
     // values whenever they are recomputed).
     auto ends = [&](int e, float& dx, float& dy, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
         const Ev v = p.ev[e];
-        dy = __fsub_rn((float)v.y, g.fy);
-        dx = __fsub_rn((float)v.x, g.fx);
+        dy = v.dy;
+        dx = v.dx;
         const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
         sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
         sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
@@ -486,7 +487,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
         if (f < total) {
             e = cur.at(f);
             const Ev v = p.ev[e];
-            const float dy = __fsub_rn((float)v.y, g.fy);
+            const float dy = v.dy;
             const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
             const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
             const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
@@ -494,7 +495,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
             // Every covered cell lies between the rows of the two end cells
             // (each cell coordinate is monotone in s).
             if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
-                const float dx = __fsub_rn((float)v.x, g.fx);
+                const float dx = v.dx;
                 const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
                 const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
                 // Eq. (19): both end cells in the frame; counted by the tile of row ya.
@@ -581,9 +582,9 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
             const Ev v = p.ev[cur.at(f)];
             const float s = warp_s(D, v.t, gg);
-            const int uy = cell_of(g.fy, __fsub_rn((float)v.y, g.fy), s);
+            const int uy = cell_of(g.fy, v.dy, s);
             if ((unsigned)(uy - y0) >= (unsigned)rows) continue;
-            const int ux = cell_of(g.fx, __fsub_rn((float)v.x, g.fx), s);
+            const int ux = cell_of(g.fx, v.dx, s);
             if ((unsigned)ux < (unsigned)W) bump<false>(&tile[(uy - y0) * P + ux], S, Ct);
         }
         C = Ct;

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(Geom g, const WinIn* 
     const Ev* e = ev + win.ev_off;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const Ev v = e[i];
-        const float dx = __fsub_rn((float)v.x, g.fx), dy = __fsub_rn((float)v.y, g.fy);
+        const float dx = v.dx, dy = v.dy;
         const float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
         const float u = R2 > 0.0f ? __fdiv_rn(r2, R2) : 0.0f;
         int rb = (int)floorf(__fmul_rn(__fsqrt_rn(u), (float)FEAT_R));

@@ -37,7 +37,7 @@ constexpr size_t OFF_C = align256(OFF_S + sizeof(unsigned long long) * NA_MAX_TA
 constexpr size_t OFF_F = align256(OFF_C + sizeof(unsigned long long) * NA_MAX_TASKS);
 constexpr size_t SCRATCH_BYTES = align256(OFF_F + sizeof(unsigned long long) * NA_MAX_TASKS);
 static_assert(SCRATCH_BYTES == DD_NOALLOC_SCRATCH_BYTES, "dd.h states the static scratch size");
-static_assert(sizeof(dd::Partial) == 24 && sizeof(dd::Task) == 16 && sizeof(dd::Ev) == 8, "layout");
+static_assert(sizeof(dd::Partial) == 24 && sizeof(dd::Task) == 16 && sizeof(dd::Ev) == 16, "layout");
 
 // The scratch itself.  In host code `g_scratch` is only a stand-in symbol:
 // its device address comes from cudaGetSymbolAddress, once per device.
