@@ -410,42 +410,34 @@ constexpr float DENSE_CELLS = 4.0f;
 
 // Eqs. (16) and (19) for the unit's share of events, positions [f_begin,
 // total): Hbar into the tile, N_full into `full`, and (sparse) S and C.
+// Per-warp rings of queued long segments (see bound_pass).
+struct SegQueue {
+    int e[MAX_WARPS * QUEUE];
+    float sa[MAX_WARPS * QUEUE], sb[MAX_WARPS * QUEUE];
+    int x[MAX_WARPS * QUEUE], y[MAX_WARPS * QUEUE];
+};
+
 template <bool DENSE>
 __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, const Task& tk, float tau, uint32_t* tile,
-                                           int* queue, int y0, int y1, int f_begin, int total, Cursor& cur,
+                                           SegQueue& queue, int y0, int y1, int f_begin, int total, Cursor& cur,
                                            unsigned long long& S, unsigned long long& C, unsigned long long& full) {
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
-    // End scales and end cells of event e's segment (the same binary32
-    // values whenever they are recomputed).
-    auto ends = [&](int e, float& dx, float& dy, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
-        const Ev v = p.ev[e];
-        dy = v.dy;
-        dx = v.dx;
-        const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-        sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-        sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-        ya = cell_of(g.fy, dy, sa);
-        yb = cell_of(g.fy, dy, sb);
-        xa = cell_of(g.fx, dx, sa);
-        xb = cell_of(g.fx, dx, sb);
-    };
-    // The cells of up to 32 queued segments, one event per lane (`valid`):
-    // short runs walked by their own lane, long runs spread over the warp as
+    // The cells of up to 32 queued segments, one event per lane (`valid`,
+    // with the end scales and end cells computed when it was queued): short
+    // runs walked by their own lane, long runs spread over the warp as
     // (event, major cell) pairs.
-    auto walk = [&](int e, bool valid) {
+    auto walk = [&](int e, bool valid, float sa, float sb, int xa, int ya, int xb, int yb) {
         uint32_t Ci = 0;
         Seg sg;
         sg.mode = SEG_NONE;
         sg.k0 = sg.count = sg.addr = 0;
         sg.dn = sg.rm = sg.sa = sg.sb = 0.0f;
         if (valid) {
-            float dx, dy, sa, sb;
-            int xa, ya, xb, yb;
-            ends(e, dx, dy, sa, sb, xa, ya, xb, yb);
+            const Ev v = p.ev[e];
             const float2 r = p.rcp[e];
-            sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+            sg = seg_range(g, v.dx, v.dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
         }
         const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
         if (cmax <= 2) {
@@ -476,27 +468,43 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
     };
     // Warps take 32 positions at a time, one event per lane.  A segment
     // within one pixel is counted at once; an event whose segment spans more
-    // pixels is queued (a ring of 64 event indices per warp), and every 32
-    // queued events are walked together, so the walk runs on full warps.
-    int* q = queue + wid * QUEUE;
+    // pixels is queued with its end scales and end cells (a ring of 64 entries
+    // per warp; cells packed as two 16-bit halves, their range being under
+    // 2^15 in magnitude), and every 32 queued events are walked together, so
+    // the walk runs on full warps.
+    const int qb = wid * QUEUE;
     int q_head = 0, q_tail = 0;
+    auto take = [&](int i, int& e, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
+        const int k = qb + (i & (QUEUE - 1));
+        e = queue.e[k];
+        sa = queue.sa[k];
+        sb = queue.sb[k];
+        const int px = queue.x[k], py = queue.y[k];
+        xa = (int)(short)(px & 0xFFFF);
+        xb = px >> 16;
+        ya = (int)(short)(py & 0xFFFF);
+        yb = py >> 16;
+    };
     for (int base = f_begin + wid * 32; base < total; base += nw * 32) {
         const int f = base + lane;
         bool pend = false;
-        int e = 0;
+        int e = 0, xa = 0, xb = 0, ya = 0, yb = 0;
+        float sa = 0.0f, sb = 0.0f;
         if (f < total) {
             e = cur.at(f);
             const Ev v = p.ev[e];
             const float dy = v.dy;
             const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
-            const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
-            const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-            const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
+            sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+            sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+            ya = cell_of(g.fy, dy, sa);
+            yb = cell_of(g.fy, dy, sb);
             // Every covered cell lies between the rows of the two end cells
             // (each cell coordinate is monotone in s).
             if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
                 const float dx = v.dx;
-                const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
+                xa = cell_of(g.fx, dx, sa);
+                xb = cell_of(g.fx, dx, sb);
                 const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
                 // Eq. (19): both end cells in the frame; counted by the tile of row ya.
                 if ((unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
@@ -516,23 +524,32 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
             }
         }
         const unsigned pm = __ballot_sync(0xffffffffu, pend);
-        if (pend) q[(q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1)] = e;
+        if (pend) {
+            const int k = qb + ((q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1));
+            queue.e[k] = e;
+            queue.sa[k] = sa;
+            queue.sb[k] = sb;
+            queue.x[k] = (xa & 0xFFFF) | (xb << 16);
+            queue.y[k] = (ya & 0xFFFF) | (yb << 16);
+        }
         q_tail += __popc(pm);
         if (q_tail - q_head >= 32) {
-            __syncwarp();                         // the queued indices are visible to the warp
-            const int ew = q[(q_head + lane) & (QUEUE - 1)];
+            __syncwarp();                         // the queued entries are visible to the warp
+            take(q_head + lane, e, sa, sb, xa, ya, xb, yb);
             __syncwarp();                         // read before the next pass may overwrite
             q_head += 32;
-            walk(ew, true);
+            walk(e, true, sa, sb, xa, ya, xb, yb);
         }
     }
     while (q_tail > q_head) {                     // the rest of the queue
         const int n = min(32, q_tail - q_head);
+        int e = 0, xa = 0, xb = 0, ya = 0, yb = 0;
+        float sa = 0.0f, sb = 0.0f;
         __syncwarp();
-        const int ew = lane < n ? q[(q_head + lane) & (QUEUE - 1)] : 0;
+        if (lane < n) take(q_head + lane, e, sa, sb, xa, ya, xb, yb);
         __syncwarp();
         q_head += n;
-        walk(ew, lane < n);
+        walk(e, lane < n, sa, sb, xa, ya, xb, yb);
     }
 }
 
@@ -547,7 +564,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
 // clears the accumulated band.  The tile arrives zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
-                                          int* erange, int* s_last, int* queue) {
+                                          int* erange, int* s_last, SegQueue& queue) {
     const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -728,7 +745,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
 // list and counter for the control blocks of this round.
 __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     extern __shared__ __align__(16) uint32_t tile[];
-    __shared__ int queue[MAX_WARPS * QUEUE];
+    __shared__ SegQueue queue;
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
     __shared__ int s_unit, s_last;
