@@ -761,14 +761,16 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     const Job* jobs = a.jobs + (size_t)par * a.job_stride;
     const int tile_words = g.band_rows * tile_pitch(g);
     const int bins1 = g.n_tb * g.H + 1;
-    if (threadIdx.x == 0) s_unit = atomicAdd(work, 1);
+    // Block b starts with unit b; later units come from the counter, which
+    // numbers them from gridDim.x on.
+    if (threadIdx.x == 0) s_unit = blockIdx.x;
     for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
     __syncthreads();
     for (;;) {
         const int u = s_unit;
         if (u >= n_units) break;
         __syncthreads();                          // every thread has read s_unit
-        if (threadIdx.x == 0) s_unit = atomicAdd(work, 1);   // the next unit, fetched early
+        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(work, 1);   // the next unit, fetched early
         const int j = u / g.n_tiles, ti = u - j * g.n_tiles;
         const Job jb = jobs[j];
         const int64_t ev_off = a.wins[jb.win].ev_off;
