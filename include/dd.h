@@ -392,7 +392,7 @@ double dd_serve_clock(void);
  * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
  * DD_ERR_CUDA. */
 #define DD_NOALLOC_MAX_EVENTS (1 << 20)
-#define DD_NOALLOC_SCRATCH_BYTES 26795008
+#define DD_NOALLOC_SCRATCH_BYTES 25223680
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
                         int32_t nD, dd_i128* K, void* stream);
 

@@ -233,7 +233,7 @@ int ensure_windows(dd_ctx* c, int nw) {
     A((void**)&c->st, sizeof(dd::SolveState) * (size_t)cap);
     A((void**)&c->queues, sizeof(dd::Node) * 2 * (size_t)c->cfg.queue_capacity * cap);
     A((void**)&c->tasks, sizeof(dd::Task) * (size_t)c->max_tasks * cap);
-    A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * c->g.n_tiles * cap);
+    A((void**)&c->part, sizeof(dd::Partial) * (size_t)c->max_tasks * cap);
     A((void**)&c->jobs, sizeof(dd::Job) * 2 * (size_t)js);
     AH((void**)&c->h_st, sizeof(dd::SolveState) * (size_t)cap);
     AH((void**)&c->h_wins, sizeof(dd::WinIn) * (size_t)cap);
@@ -361,6 +361,7 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
         DD_TRY(copy(c, c->tasks, c->h_tasks, sizeof(dd::Task) * m, cudaMemcpyHostToDevice));
         DD_TRY(copy(c, c->jobs, c->h_jobs, sizeof(dd::Job) * nj, cudaMemcpyHostToDevice));
         DD_TRY(copy(c, c->sch, c->h_sch, sizeof(dd::Sched), cudaMemcpyHostToDevice));
+        DD_TRY(cudaMemsetAsync(c->part, 0, sizeof(dd::Partial) * m, c->stream));   // the tasks' sums start at zero
         uint32_t* iw = nullptr;
         if (iwe) {
             size_t need = (size_t)m * M;
@@ -525,9 +526,9 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
         c->stats.kernel_launches++;
     }
     DD_TRY(cudaMemsetAsync(c->sch, 0, sizeof(dd::Sched), c->stream));
-    DD_TRY(dd::launch_init(c->g, nw, c->st, c->tasks, c->max_tasks, c->wins, c->params, c->jobs, c->job_stride,
-                           c->sch, c->cfg.pop_k, c->cfg.queue_capacity, c->cfg.max_rounds, (int32_t)trace_cap,
-                           c->stream));
+    DD_TRY(dd::launch_init(c->g, nw, c->st, c->tasks, c->max_tasks, c->part, c->wins, c->params, c->jobs,
+                           c->job_stride, c->sch, c->cfg.pop_k, c->cfg.queue_capacity, c->cfg.max_rounds,
+                           (int32_t)trace_cap, c->stream));
     c->stats.kernel_launches++;
     dd::TraceRec* tr_dev = trace_cap > 0 ? c->trace : nullptr;
     const bool graph = !c->cfg.host_loop && !c->timing;

@@ -36,7 +36,7 @@ struct Job {
     int32_t win, task, split, splits;
 };
 
-// Per (window, task, row band) partial sums of one IWE tile.
+// Sums of one task's IWE: per task, over all its row bands.
 struct Partial {
     unsigned long long S;      // sum of squared counts
     unsigned long long cells;  // sum of counts (N_in for a point, increments for a bound)
@@ -188,7 +188,9 @@ struct EvalArgs {
     const Job* jobs;               // two lists of job_stride entries
     int32_t job_stride;
     Sched* sch;
-    Partial* part;                 // [(win * task_stride + task) * n_tiles + tile]
+    Partial* part;                 // [win * task_stride + task]: the task's sums over its row
+                                   // bands, accumulated by atomics; zero before the evaluation,
+                                   // cleared by their reader
     uint32_t* iwe_out;             // nullable: [task][M] (single window)
     Merge mg;
 };
@@ -199,19 +201,19 @@ cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_window
                           int32_t* cursor, int32_t* err, cudaStream_t s);
 cudaError_t launch_eval(const Geom& g, const EvalArgs& a, int threads, int grid_blocks, cudaStream_t s);
 int eval_resident_blocks(const Geom& g, int threads);
-cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part, i128* key,
+cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, Partial* part, i128* key,
                         unsigned long long* S, unsigned long long* cells, unsigned long long* full,
                         cudaStream_t s);
 // Windows w0 .. w0 + n_windows - 1 start a search; split_ok < 0: split bound
 // tasks only when n_windows == 1.
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
-                        const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
-                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s,
-                        int32_t w0 = 0, int32_t split_ok = -1);
+                        Partial* part, const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride,
+                        Sched* sch, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
+                        cudaStream_t s, int32_t w0 = 0, int32_t split_ok = -1);
 // One control block per window 0 .. n_windows - 1; phase_out (nullable)
 // receives each window's phase after the round.
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
-                           int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
+                           int32_t task_stride, Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
                            int32_t use_loop, cudaStream_t s, int32_t split_ok = -1, int32_t* phase_out = nullptr);
 

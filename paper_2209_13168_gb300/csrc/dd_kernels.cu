@@ -396,7 +396,7 @@ struct UnitPtrs {
     const Ev* ev;                 // the window's sorted events
     const float2* rcp;
     const int32_t* row_off;       // the window's bin offsets
-    Partial* part;                // the task's partials [n_tiles]
+    Partial* part;                // the task's sums (atomic accumulation over its row bands)
     uint32_t* out;                // nullable: the task's image [H][W]
     uint32_t* acc;                // split jobs: the task's accumulator [H][W]
     int32_t* done;                // split jobs: finished splits per tile
@@ -708,12 +708,13 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             acc[i] = 0u;
         }
         if (threadIdx.x == 0) {
-            Partial q;
-            q.S = atomicExch(&p.sums[ti].S, 0ull);
-            q.cells = atomicExch(&p.sums[ti].cells, 0ull);
-            q.full = atomicExch(&p.sums[ti].full, 0ull);
+            const unsigned long long qS = atomicExch(&p.sums[ti].S, 0ull);
+            const unsigned long long qC = atomicExch(&p.sums[ti].cells, 0ull);
+            const unsigned long long qF = atomicExch(&p.sums[ti].full, 0ull);
             p.done[ti] = 0;
-            p.part[ti] = q;
+            if (qS) atomicAdd(&p.part->S, qS);
+            if (qC) atomicAdd(&p.part->cells, qC);
+            if (qF) atomicAdd(&p.part->full, qF);
         }
         return;
     }
@@ -730,12 +731,10 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         S = warp_sum(S);
         cs = warp_sum(cs);
         full = warp_sum(full);
-        if (lane == 0) {
-            Partial q;
-            q.S = S;
-            q.cells = cs;
-            q.full = full;
-            p.part[ti] = q;
+        if (lane == 0) {                          // the band's sums into the task's
+            if (S) atomicAdd(&p.part->S, S);
+            if (cs) atomicAdd(&p.part->cells, cs);
+            if (full) atomicAdd(&p.part->full, full);
         }
     }
 }
@@ -780,7 +779,7 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         p.ev = a.ev + ev_off;
         p.rcp = a.rcp + ev_off;
         p.row_off = a.row_off + (size_t)jb.win * bins1;
-        p.part = a.part + ((size_t)jb.win * a.task_stride + jb.task) * g.n_tiles;
+        p.part = a.part + ((size_t)jb.win * a.task_stride + jb.task);
         p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * g.W * g.H : nullptr;
         p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * g.W * g.H : nullptr;
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
@@ -814,35 +813,24 @@ __device__ __forceinline__ i128 key_of(int64_t M, unsigned long long S, unsigned
     return (i128)M * (i128)S - (i128)N * (i128)N;
 }
 
-__global__ void k_keys(Geom g, const Task* tasks, int32_t n_tasks, const Partial* part, i128* key,
+__global__ void k_keys(Geom g, const Task* tasks, int32_t n_tasks, Partial* part, i128* key,
                        unsigned long long* S_out, unsigned long long* C_out, unsigned long long* F_out) {
-    const int t = blockIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tasks) return;
-    unsigned long long S = 0, C = 0, F = 0;
-    for (int i = threadIdx.x; i < g.n_tiles; i += 32) {
-        const Partial p = part[t * g.n_tiles + i];
-        S += p.S;
-        C += p.cells;
-        F += p.full;
-    }
-    S = warp_sum(S);
-    C = warp_sum(C);
-    F = warp_sum(F);
-    if (threadIdx.x == 0) {
-        const int64_t M = (int64_t)g.W * g.H;
-        const unsigned long long N = tasks[t].kind == TASK_POINT ? C : F;
-        key[t] = key_of(M, S, N);
-        S_out[t] = S;
-        C_out[t] = C;
-        F_out[t] = F;
-    }
+    const Partial p = part[t];
+    part[t] = Partial{0, 0, 0};                   // cleared for the next evaluation
+    const int64_t M = (int64_t)g.W * g.H;
+    key[t] = key_of(M, p.S, tasks[t].kind == TASK_POINT ? p.cells : p.full);
+    S_out[t] = p.S;
+    C_out[t] = p.cells;
+    F_out[t] = p.full;
 }
 
-cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, const Partial* part, i128* key,
+cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, Partial* part, i128* key,
                         unsigned long long* S, unsigned long long* cells, unsigned long long* full,
                         cudaStream_t s) {
     if (n_tasks <= 0) return cudaSuccess;
-    k_keys<<<n_tasks, 32, 0, s>>>(g, tasks, n_tasks, part, key, S, cells, full);
+    k_keys<<<(n_tasks + 63) / 64, 64, 0, s>>>(g, tasks, n_tasks, part, key, S, cells, full);
     return cudaGetLastError();
 }
 
@@ -855,11 +843,13 @@ __device__ __forceinline__ float centre(float lo, float hi) {
 // next evaluation reads.  `split_ok`: bound tasks may be split (single-window
 // searches).
 __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all, Task* tasks_all,
-                       int32_t task_stride, const WinIn* wins, const WinParams* params, Job* jobs_all,
-                       int32_t job_stride, Sched* sch, int32_t K_pop, int32_t qcap, int64_t max_rounds,
-                       int32_t trace_cap) {
-    if (threadIdx.x != 0) return;
+                       int32_t task_stride, Partial* part_all, const WinIn* wins, const WinParams* params,
+                       Job* jobs_all, int32_t job_stride, Sched* sch, int32_t K_pop, int32_t qcap,
+                       int64_t max_rounds, int32_t trace_cap) {
     const int w = w0 + blockIdx.x;
+    for (int i = threadIdx.x; i < task_stride; i += blockDim.x)   // the window's task sums start at zero
+        part_all[(size_t)w * task_stride + i] = Partial{0, 0, 0};
+    if (threadIdx.x != 0) return;
     const int par = sch->round & 1;
     Job* jobs = jobs_all + (size_t)par * job_stride;
     SolveState* st = st_all + w;
@@ -952,12 +942,12 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
 }
 
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
-                        const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride, Sched* sch,
-                        int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap, cudaStream_t s,
-                        int32_t w0, int32_t split_ok) {
+                        Partial* part, const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride,
+                        Sched* sch, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
+                        cudaStream_t s, int32_t w0, int32_t split_ok) {
     if (split_ok < 0) split_ok = n_windows == 1;
-    k_init<<<n_windows, 32, 0, s>>>(g, split_ok, w0, st, tasks, task_stride, wins, params, jobs, job_stride, sch,
-                                    K_pop, qcap, max_rounds, trace_cap);
+    k_init<<<n_windows, 32, 0, s>>>(g, split_ok, w0, st, tasks, task_stride, part, wins, params, jobs, job_stride,
+                                    sch, K_pop, qcap, max_rounds, trace_cap);
     return cudaGetLastError();
 }
 
@@ -1006,7 +996,7 @@ __device__ __forceinline__ i128 warp_max_i128(i128 v) {
 // graph loop condition.
 __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windows, SolveState* st_all,
                                                         Node* queues, Task* tasks_all, int32_t task_stride,
-                                                        const Partial* part_all, const int32_t* err_all,
+                                                        Partial* part_all, const int32_t* err_all,
                                                         TraceRec* trace, Job* jobs_all, int32_t job_stride,
                                                         Sched* sch, cudaGraphConditionalHandle loop,
                                                         int32_t use_loop, int32_t split_ok, int32_t* phase_out) {
@@ -1021,7 +1011,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     const int par = sch->round & 1;
     SolveState* st = st_all + w;
     Task* tasks = tasks_all + (size_t)w * task_stride;
-    const Partial* part = part_all + (size_t)w * task_stride * g.n_tiles;
+    Partial* part = part_all + (size_t)w * task_stride;
     Job* jobs = jobs_all + (size_t)(par ^ 1) * job_stride;
     static_assert(sizeof(SolveState) % 16 == 0, "state is copied as int4");
     for (int i = tid; i < (int)(sizeof(SolveState) / 16); i += blockDim.x)
@@ -1034,30 +1024,13 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     const int64_t M = s.M;
     const int n_tasks = s.n_tasks;
 
-    // Each warp reduces the row-band partials of four tasks at a time (their
-    // loads issued together).
-    for (int t0 = 4 * wid; t0 < n_tasks; t0 += 4 * nw) {
-        unsigned long long S[4], C[4], F[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            S[u] = C[u] = F[u] = 0;
-            if (t0 + u < n_tasks)
-                for (int i = lane; i < g.n_tiles; i += 32) {
-                    const Partial p = part[(t0 + u) * g.n_tiles + i];
-                    S[u] += p.S;
-                    C[u] += p.cells;
-                    F[u] += p.full;
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const unsigned long long s_ = warp_sum(S[u]), c_ = warp_sum(C[u]), f_ = warp_sum(F[u]);
-            const int t = t0 + u;
-            if (lane == 0 && t < n_tasks) {
-                key[t] = key_of(M, s_, tasks[t].kind == TASK_POINT ? c_ : f_);
-                cells[t] = c_;
-            }
-        }
+    // Each task's sums (accumulated by the evaluation over its row bands),
+    // read and cleared for the next round.
+    for (int t = tid; t < n_tasks; t += blockDim.x) {
+        const Partial q = part[t];
+        part[t] = Partial{0, 0, 0};
+        key[t] = key_of(M, q.S, tasks[t].kind == TASK_POINT ? q.cells : q.full);
+        cells[t] = q.cells;
     }
     __syncthreads();
 
@@ -1378,7 +1351,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
 }
 
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
-                           int32_t task_stride, const Partial* part, const int32_t* err, TraceRec* trace,
+                           int32_t task_stride, Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
                            int32_t use_loop, cudaStream_t s, int32_t split_ok, int32_t* phase_out) {
     if (split_ok < 0) split_ok = n_windows == 1;

@@ -31,7 +31,7 @@ constexpr size_t OFF_SCHED = align256(OFF_CHUNKS + sizeof(int32_t) * NA_MAX_CHUN
 constexpr size_t OFF_JOBS = align256(OFF_SCHED + sizeof(dd::Sched));
 constexpr size_t OFF_TASKS = align256(OFF_JOBS + sizeof(dd::Job) * 2 * NA_MAX_TASKS);
 constexpr size_t OFF_PART = align256(OFF_TASKS + sizeof(dd::Task) * NA_MAX_TASKS);
-constexpr size_t OFF_KEYS = align256(OFF_PART + sizeof(dd::Partial) * NA_MAX_TASKS * NA_MAX_TILES);
+constexpr size_t OFF_KEYS = align256(OFF_PART + sizeof(dd::Partial) * NA_MAX_TASKS);
 constexpr size_t OFF_S = align256(OFF_KEYS + sizeof(dd::i128) * NA_MAX_TASKS);
 constexpr size_t OFF_C = align256(OFF_S + sizeof(unsigned long long) * NA_MAX_TASKS);
 constexpr size_t OFF_F = align256(OFF_C + sizeof(unsigned long long) * NA_MAX_TASKS);
@@ -128,8 +128,8 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     unsigned long long* F = (unsigned long long*)(base + OFF_F);
 
     // The window descriptor and chunk map go in from host stack buffers; the
-    // ingest clears the bin counts and the error flag itself, and every live
-    // (task, tile) unit overwrites its partial, so nothing else needs zeroing.
+    // ingest clears the bin counts and the error flag itself; the tasks' sums
+    // are cleared before each evaluation (and again by their reader).
     dd::WinIn h_win;
     h_win.x = ev->x;
     h_win.y = ev->y;
@@ -190,6 +190,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
                 cudaMemcpyAsync(jobs, h_jobs, sizeof(dd::Job) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
                 cudaMemcpyAsync(sch, &h_sch, sizeof(h_sch), cudaMemcpyHostToDevice, s) != cudaSuccess)
                 return DD_ERR_CUDA;
+            if (cudaMemsetAsync(part, 0, sizeof(dd::Partial) * m, s) != cudaSuccess) return DD_ERR_CUDA;
             if (dd::launch_eval(g, a, 512, grid, s) != cudaSuccess) return DD_ERR_CUDA;
             if (dd::launch_keys(g, tasks, m, part, keys, S, C, F, s) != cudaSuccess) return DD_ERR_CUDA;
             if (cudaMemcpyAsync(h_keys, keys, sizeof(dd::i128) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess)

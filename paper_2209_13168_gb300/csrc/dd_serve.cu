@@ -143,7 +143,7 @@ size_t slot_bytes(const dd_server* s) {
     return (size_t)s->E * (sizeof(dd::Ev) + sizeof(float2) + 2 * sizeof(int16_t) + sizeof(float)) +
            sizeof(int32_t) * (3 * (size_t)s->bins + 1) + sizeof(dd::SolveState) +
            sizeof(dd::Node) * 2 * (size_t)s->qcap + sizeof(dd::Task) * (size_t)s->max_tasks +
-           sizeof(dd::Partial) * (size_t)s->max_tasks * s->g.n_tiles + sizeof(dd::Job) * 2 * (size_t)s->max_tasks;
+           sizeof(dd::Partial) * (size_t)s->max_tasks + sizeof(dd::Job) * 2 * (size_t)s->max_tasks;
 }
 
 int alloc_server(dd_server* s) {
@@ -171,7 +171,7 @@ int alloc_server(dd_server* s) {
     A((void**)&s->st, sizeof(dd::SolveState) * S);
     A((void**)&s->queues, sizeof(dd::Node) * 2 * (size_t)s->qcap * S);
     A((void**)&s->tasks, sizeof(dd::Task) * (size_t)s->max_tasks * S);
-    A((void**)&s->part, sizeof(dd::Partial) * (size_t)s->max_tasks * s->g.n_tiles * S);
+    A((void**)&s->part, sizeof(dd::Partial) * (size_t)s->max_tasks * S);
     s->job_stride = (int)(S * s->max_tasks);
     A((void**)&s->jobs, sizeof(dd::Job) * 2 * (size_t)s->job_stride);
     A((void**)&s->sch, sizeof(dd::Sched));
@@ -251,8 +251,8 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
         c = dd::launch_warm(s->g, 1, s->feat_counts, s->wins + k, s->params + k, s->model, s->stream);
         if (c != cudaSuccess) return c;
     }
-    return dd::launch_init(s->g, 1, s->st, s->tasks, s->max_tasks, s->wins, s->params, s->jobs, s->job_stride,
-                           s->sch, s->pop_k, s->qcap, s->max_rounds, 0, s->stream, k, 0);
+    return dd::launch_init(s->g, 1, s->st, s->tasks, s->max_tasks, s->part, s->wins, s->params, s->jobs,
+                           s->job_stride, s->sch, s->pop_k, s->qcap, s->max_rounds, 0, s->stream, k, 0);
 }
 
 void fill(const dd::SolveState& st, const dd_events& ev, int64_t M, dd_result* out) {
