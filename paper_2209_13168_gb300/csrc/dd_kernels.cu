@@ -718,24 +718,14 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         }
         return;
     }
+    // Each warp adds its share of the band's sums to the task's.
     S = warp_sum(S);
     const unsigned long long C64 = warp_sum(Cl);
     full = warp_sum(full);
-    __syncthreads();
-    if (lane == 0) { red[0][wid] = S; red[1][wid] = C64; red[2][wid] = full; }
-    __syncthreads();
-    if (wid == 0) {
-        S = lane < nw ? red[0][lane] : 0;
-        unsigned long long cs = lane < nw ? red[1][lane] : 0;
-        full = lane < nw ? red[2][lane] : 0;
-        S = warp_sum(S);
-        cs = warp_sum(cs);
-        full = warp_sum(full);
-        if (lane == 0) {                          // the band's sums into the task's
-            if (S) atomicAdd(&p.part->S, S);
-            if (cs) atomicAdd(&p.part->cells, cs);
-            if (full) atomicAdd(&p.part->full, full);
-        }
+    if (lane == 0) {
+        if (S) atomicAdd(&p.part->S, S);
+        if (C64) atomicAdd(&p.part->cells, C64);
+        if (full) atomicAdd(&p.part->full, full);
     }
 }
 
