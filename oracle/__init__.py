@@ -17,6 +17,8 @@ What each function follows (paper: McLeod et al., arXiv 2209.13168):
   mlp_forward_f64, mlp_loss_f64  the same network in binary64, its training
                   loss and backprop gradient
   warm_map        network outputs -> (D_warm, w_warm)
+  resample        the paper's fast mode: coordinates scaled to a coarser frame,
+                  a random share of the events kept
   grid_max        exhaustive dense grid (brute force)
   sweep_max       exact breakpoint sweep (brute force)
   fp64_disagreements  the same warp in binary64, diagnostic only
@@ -117,6 +119,11 @@ def lib():
         L.or_warm_map.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, P(ctypes.c_float),
                                   P(ctypes.c_float)]
         L.or_warm_map.restype = None
+        L.or_resample.argtypes = [P(_Win), ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_resample.restype = ctypes.c_int64
+        L.or_resample_foe.argtypes = [P(_Win), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_float)]
+        L.or_resample_foe.restype = None
         L.or_grid_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, ctypes.c_float, P(_I128),
                                   P(ctypes.c_float), P(ctypes.c_int64)]
         L.or_sweep_max.argtypes = [P(_Win), ctypes.c_float, ctypes.c_float, P(_I128), P(ctypes.c_float),
@@ -284,3 +291,15 @@ def warm_map(u, l, tau):
     d, w = ctypes.c_float(), ctypes.c_float()
     lib().or_warm_map(u, l, tau, ctypes.byref(d), ctypes.byref(w))
     return d.value, w.value
+
+
+def resample(win, W2, H2, keep, seed):
+    """The fast mode's window: (Window on W2 x H2 with the scaled FOE)."""
+    n = win.x.size
+    x2 = np.zeros(max(n, 1), np.int16)
+    y2 = np.zeros(max(n, 1), np.int16)
+    t2 = np.zeros(max(n, 1), np.float32)
+    m = lib().or_resample(ctypes.byref(win.c), W2, H2, keep, seed, x2.ctypes.data, y2.ctypes.data, t2.ctypes.data)
+    fx, fy = ctypes.c_float(), ctypes.c_float()
+    lib().or_resample_foe(ctypes.byref(win.c), W2, H2, ctypes.byref(fx), ctypes.byref(fy))
+    return Window(W2, H2, fx.value, fy.value, x2[:m], y2[:m], t2[:m], win.c.t0, win.c.tau)

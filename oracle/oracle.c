@@ -758,3 +758,47 @@ void or_warm_map(float u, float l, float tau, float* D_warm, float* w_warm) {
     if (v > 1.0f) v = 1.0f;
     *w_warm = ldexpf(1.0f, (int)floorf(v)) / tau;
 }
+
+/* ------------------------------------------------ resized and resampled */
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output i of the sequence
+ * seeded with `state0` is the finaliser applied to state0 + (i + 1) * G. */
+static uint64_t sm64(uint64_t state0, uint64_t i) {
+    uint64_t z = state0 + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* The paper's fast mode (Sec. 6, the resized and resampled sequences): event
+ * coordinates scaled to a W2 x H2 frame and a random share `keep` of the
+ * events kept.  Reading: a scaled coordinate goes to the nearest coarse pixel
+ * centre, x2 = floor(x k + 1/2) with k = W2/W (binary32), clamped to the
+ * frame; event i is kept when the top 24 bits of SplitMix64 output i of key
+ * SplitMix64(seed, 0) fall below floor(keep 2^24).  Kept events keep their
+ * order and times.  Returns the kept count (x2, y2, t2 have room for n). */
+int64_t or_resample(const or_window* w, int32_t W2, int32_t H2, float keep, uint64_t seed, int16_t* x2, int16_t* y2,
+                    float* t2) {
+    const float kx = (float)W2 / (float)w->W, ky = (float)H2 / (float)w->H;
+    const uint64_t key = sm64(seed, 0);
+    const uint64_t thr = (uint64_t)floor((double)keep * 16777216.0);
+    int64_t m = 0;
+    for (int64_t i = 0; i < w->n; i++) {
+        if ((sm64(key, (uint64_t)i) >> 40) >= thr) continue;
+        int32_t cx = (int32_t)floorf((float)w->x[i] * kx + 0.5f);
+        int32_t cy = (int32_t)floorf((float)w->y[i] * ky + 0.5f);
+        if (cx > W2 - 1) cx = W2 - 1;
+        if (cy > H2 - 1) cy = H2 - 1;
+        x2[m] = (int16_t)cx;
+        y2[m] = (int16_t)cy;
+        t2[m] = w->t[i];
+        m++;
+    }
+    return m;
+}
+
+/* The FOE in the coarse frame: foe k (binary32). */
+void or_resample_foe(const or_window* w, int32_t W2, int32_t H2, float* fx2, float* fy2) {
+    *fx2 = w->foe_x * ((float)W2 / (float)w->W);
+    *fy2 = w->foe_y * ((float)H2 / (float)w->H);
+}

@@ -91,6 +91,11 @@ void or_mlp_forward_f64(const double* params, const double* x, double* h1, doubl
 double or_mlp_loss_f64(const double* params, const double* X, const double* u_star, int64_t B, double* grad);
 void or_warm_map(float u, float l, float tau, float* D_warm, float* w_warm);
 
+/* Fast mode: coordinates scaled to W2 x H2, a random share `keep` kept. */
+int64_t or_resample(const or_window* w, int32_t W2, int32_t H2, float keep, uint64_t seed, int16_t* x2, int16_t* y2,
+                    float* t2);
+void or_resample_foe(const or_window* w, int32_t W2, int32_t H2, float* fx2, float* fy2);
+
 #ifdef __cplusplus
 }
 #endif
