@@ -210,6 +210,27 @@ int dd_solve_trace(dd_ctx* ctx, const dd_events* ev, float D_lo, float D_hi, flo
 int dd_solve_window(dd_ctx* ctx, const dd_events* ev, const dd_window_params* p, dd_result* out,
                     dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len);
 
+/* The paper's fast mode (Sec. 6, the resized and resampled sequences): the
+ * events of a W x H window with their coordinates scaled to a W2 x H2 frame
+ * and a random share `keep` (in [0, 1]) of them kept -- an ordinary window
+ * for a context of the coarse frame, whose FOE dd_resample_foe gives.
+ * Event i goes to the nearest coarse pixel centre, floor(x (W2/W) + 1/2) in
+ * binary32 (likewise y), clamped to the frame, and is kept when the top 24
+ * bits of output i of SplitMix64 with key SplitMix64(seed, 0) fall below
+ * floor(keep 2^24).  Kept events keep their order and times.
+ *   in           events of the fine frame (host or device, as dd_events)
+ *   x_out, y_out, t_out  DEVICE arrays with room for in->n events
+ *   n_out        receives the kept count (host)
+ * Runs on the context's stream and synchronises it.  Errors: DD_ERR_ARG
+ * (sizes outside 1..4096, keep outside [0, 1], events outside the fine
+ * frame), DD_ERR_OOM, DD_ERR_CUDA. */
+int dd_resample(dd_ctx* ctx, const dd_events* in, int32_t W, int32_t H, int32_t W2, int32_t H2, float keep,
+                uint64_t seed, int16_t* x_out, int16_t* y_out, float* t_out, int64_t* n_out);
+
+/* The FOE of the coarse frame: foe (W2/W), foe (H2/H) in binary32. */
+int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
+                    float* foe_y2);
+
 /* Counters of one context since dd_create or the last dd_reset_stats. */
 typedef struct {
     int64_t kernel_launches;  /* kernels this library launched                      */

@@ -8,7 +8,8 @@ missing or fails to load, every entry point raises.
 The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
 dd_solve_trace, dd_solve_window, dd_solve_batch, dd_features, dd_set_warm_model,
 dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing, dd_destroy,
-dd_strerror, the dd_serve_* and dd_mlp_* families); ``Context``, ``Server``
+dd_strerror, dd_resample, dd_resample_foe, dd_probe_peaks, the dd_serve_* and
+dd_mlp_* families); ``Context``, ``Server``
 and ``Mlp`` wrap them for numpy arrays (host events) and torch CUDA tensors
 (device events, features, training batches).
 
@@ -149,6 +150,11 @@ SIGNATURES = {
     "dd_contrast_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                            _P(dd_events), _VP, ctypes.c_int32, _VP, _VP]),
     "dd_probe_peaks": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _VP]),
+    "dd_resample": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _VP, _VP, _VP,
+                                   _P(ctypes.c_int64)]),
+    "dd_resample_foe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -414,6 +420,26 @@ def dd_probe_peaks(stream_ptr=None):
     return a.value, b.value
 
 
+def dd_resample_foe(W, H, foe_x, foe_y, W2, H2):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(load().dd_resample_foe(W, H, foe_x, foe_y, W2, H2, ctypes.byref(a), ctypes.byref(b)), "dd_resample_foe")
+    return a.value, b.value
+
+
+def dd_resample(h, ev, W, H, W2, H2, keep=0.25, seed=0):
+    """The fast mode's window of events `ev` (W x H): torch CUDA tensors
+    (x, y, t) of the kept events on the W2 x H2 frame."""
+    import torch
+    n = int(ev.c.n)
+    x = torch.empty(max(n, 1), dtype=torch.int16, device="cuda")
+    y = torch.empty(max(n, 1), dtype=torch.int16, device="cuda")
+    t = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    m = ctypes.c_int64()
+    _check(load().dd_resample(h, ctypes.byref(ev.c), W, H, W2, H2, float(keep), int(seed), x.data_ptr(),
+                              y.data_ptr(), t.data_ptr(), ctypes.byref(m)), "dd_resample")
+    return x[:m.value], y[:m.value], t[:m.value]
+
+
 def dd_contrast_noalloc(W, H, foe_x, foe_y, ev, D, stream_ptr=None):
     """Keys K[j] of dd_contrast without a context and without allocating
     device memory (events must be device tensors); see include/dd.h."""
@@ -550,6 +576,12 @@ class Context:
 
     def features(self, evs):
         return dd_features(self.h, evs)
+
+    def resample(self, ev, W, H, keep=0.25, seed=0):
+        """Events `ev` of a W x H window in this context's (coarser) frame:
+        the fast mode's pre-pass (dd_resample); returns Events on the device."""
+        x, y, t = dd_resample(self.h, ev, W, H, self.W, self.H, keep, seed)
+        return Events(x.contiguous(), y.contiguous(), t.contiguous(), ev.c.t0, ev.c.tau)
 
     def set_warm_model(self, mlp):
         """The model DD_WARM_MODEL windows start from (None clears); keep it alive."""

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libdd.so")
-SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_serve.cu", "dd_noalloc.cu", "dd_mlp.cu", "dd_probe.cu"]
+SOURCES = ["dd_kernels.cu", "dd_api.cu", "dd_serve.cu", "dd_noalloc.cu", "dd_mlp.cu", "dd_probe.cu", "dd_fast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
            "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]

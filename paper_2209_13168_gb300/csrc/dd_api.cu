@@ -43,6 +43,12 @@ struct dd_ctx {
     int64_t chunk_cap = 0;
     int32_t n_chunks = 0;         // ingest chunks of the last call
 
+    // fast mode scratch
+    int32_t* rs_counts = nullptr;
+    int64_t* rs_offsets = nullptr;
+    int32_t* rs_err = nullptr;
+    int64_t rs_cap = 0;
+
     // learned warm start
     dd_mlp* warm_model = nullptr;
     int32_t* feat_counts = nullptr;   // [window][128]
@@ -462,6 +468,9 @@ void fill_result(const dd::SolveState& s, const dd_events& ev, int64_t M, dd_res
 int feature_counts(dd_ctx* c, int nw) {
     if (nw > c->feat_cap) {
         release(c->feat_counts);
+    release(c->rs_counts);
+    release(c->rs_offsets);
+    release(c->rs_err);
         c->feat_cap = 0;
         DD_TRY(cudaMalloc((void**)&c->feat_counts, sizeof(int32_t) * dd::FEATURES * (size_t)nw));
         c->feat_cap = nw;
@@ -841,6 +850,69 @@ int dd_features(dd_ctx* c, const dd_events* windows, int32_t n_windows, float* f
     DD_TRY(sync(c));
     for (int w = 0; w < n_windows; w++)
         if (c->h_err[w]) return DD_ERR_ARG;
+    return DD_OK;
+}
+
+int dd_resample(dd_ctx* c, const dd_events* in, int32_t W, int32_t H, int32_t W2, int32_t H2, float keep,
+                uint64_t seed, int16_t* x_out, int16_t* y_out, float* t_out, int64_t* n_out) {
+    if (!c || !n_out || W < 1 || H < 1 || W > 4096 || H > 4096 || W2 < 1 || H2 < 1 || W2 > 4096 || H2 > 4096)
+        return DD_ERR_ARG;
+    if (!std::isfinite(keep) || !(keep >= 0.0f) || !(keep <= 1.0f)) return DD_ERR_ARG;
+    int rc = check_events(in);
+    if (rc) return rc;
+    if (in->n > 0 && (!x_out || !y_out || !t_out)) return DD_ERR_ARG;
+    const int16_t* x = in->x;
+    const int16_t* y = in->y;
+    const float* t = in->t;
+    if (!in->device_ptrs && in->n > 0) {          // host arrays: through the context's staging buffers
+        if (in->n > c->in_cap) {
+            release(c->in_x);
+            release(c->in_y);
+            release(c->in_t);
+            c->in_cap = 0;
+            const int64_t nc = in->n + in->n / 4;
+            DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
+            DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
+            DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
+            c->in_cap = nc;
+        }
+        DD_TRY(copy(c, c->in_x, in->x, sizeof(int16_t) * in->n, cudaMemcpyHostToDevice));
+        DD_TRY(copy(c, c->in_y, in->y, sizeof(int16_t) * in->n, cudaMemcpyHostToDevice));
+        DD_TRY(copy(c, c->in_t, in->t, sizeof(float) * in->n, cudaMemcpyHostToDevice));
+        x = c->in_x;
+        y = c->in_y;
+        t = c->in_t;
+    }
+    const int64_t nb = dd::resample_blocks(in->n);
+    if (nb + 1 > c->rs_cap) {
+        release(c->rs_counts);
+        release(c->rs_offsets);
+        release(c->rs_err);
+        c->rs_cap = 0;
+        const int64_t cap = nb + 1 < 64 ? 64 : nb + 1;
+        DD_TRY(cudaMalloc((void**)&c->rs_counts, sizeof(int32_t) * cap));
+        DD_TRY(cudaMalloc((void**)&c->rs_offsets, sizeof(int64_t) * cap));
+        DD_TRY(cudaMalloc((void**)&c->rs_err, sizeof(int32_t)));
+        c->rs_cap = cap;
+    }
+    DD_TRY(dd::launch_resample(x, y, t, in->n, W, H, W2, H2, keep, seed, x_out, y_out, t_out, c->rs_counts,
+                               c->rs_offsets, c->rs_err, c->stream));
+    c->stats.kernel_launches += nb ? 3 : 0;
+    int64_t m = 0;
+    int32_t bad = 0;
+    DD_TRY(copy(c, &m, c->rs_offsets + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    DD_TRY(copy(c, &bad, c->rs_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    DD_TRY(sync(c));
+    if (bad) return DD_ERR_ARG;
+    *n_out = m;
+    return DD_OK;
+}
+
+int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
+                    float* foe_y2) {
+    if (W < 1 || H < 1 || W2 < 1 || H2 < 1 || !foe_x2 || !foe_y2) return DD_ERR_ARG;
+    *foe_x2 = foe_x * ((float)W2 / (float)W);
+    *foe_y2 = foe_y * ((float)H2 / (float)H);
     return DD_OK;
 }
 

@@ -230,6 +230,15 @@ bool mlp_device_view(const struct ::dd_mlp* m, MlpDev* out, int* device);
 cudaError_t launch_feature_norm(int32_t n_windows, const int32_t* counts, const WinIn* wins, float* feat,
                                 cudaStream_t s);
 
+// Fast mode (dd_fast.cu): n events scaled from W x H to W2 x H2, the kept
+// share compacted in order into x2/y2/t2; counts [resample_blocks(n)],
+// offsets [resample_blocks(n) + 1] (offsets[last] = kept count), err set on
+// events outside the fine frame.
+int32_t resample_blocks(int64_t n);
+cudaError_t launch_resample(const int16_t* x, const int16_t* y, const float* t, int64_t n, int32_t W, int32_t H,
+                            int32_t W2, int32_t H2, float keep, uint64_t seed, int16_t* x2, int16_t* y2, float* t2,
+                            int32_t* counts, int64_t* offsets, int32_t* err, cudaStream_t s);
+
 // Context accessors for the serving engine (dd_serve.cu).
 void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks,
               int32_t* pop_k, int32_t* queue_capacity, int64_t* max_rounds);
