@@ -14,8 +14,9 @@ are independent: replicas, weak scaling).
 Beside the headline, the line carries (unless --no-extras) the other
 workloads measured on the same GPU: the 256-window uneven batch
 ("batch"), the learned warm start against the plain search on held-out
-windows ("learned_warm_start"), and the continuous-batching server on four
-concurrent 1280x720 descents ("serving").
+windows ("learned_warm_start"), the paper's resized-and-resampled fast mode
+against full resolution ("fast_mode"), and the continuous-batching server on
+four concurrent 1280x720 descents ("serving").
 """
 import argparse
 import json
@@ -224,6 +225,14 @@ def run_extras(dd, torch):
         ev["workload"] = ("held-out 640x480 windows, N log-uniform in [20k, 100k], batch mode; plain = Algorithm 1 "
                           "from the centre, learned = from the model's guess, ideal = from the certified answer")
         out["learned_warm_start"] = ev
+    # the paper's fast mode (resized and resampled) against full resolution
+    from paper_2209_13168_gb300 import fast_mode
+    ws = fast_mode.descent_windows(step=20)
+    out["fast_mode"] = {"workload": "every 20th window of a 1280x720 descent (D 0.05-0.83, 50k-833k events), "
+                                    "full resolution vs 160x90 with a quarter of the events",
+                        "exact": fast_mode.evaluate(ws, 160, 90, reps=2),
+                        "gamma_0.025": fast_mode.evaluate(ws, 160, 90, reps=2, gamma=0.025)}
+    del ws
     # four concurrent descents through the server
     from paper_2209_13168_gb300 import serve_bench
     out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8)
