@@ -15,7 +15,8 @@ Beside the headline, the line carries (unless --no-extras) the other
 workloads measured on the same GPU: the 256-window uneven batch
 ("batch"), the learned warm start against the plain search on held-out
 windows ("learned_warm_start"), the paper's resized-and-resampled fast mode
-against full resolution ("fast_mode"), and the continuous-batching server on
+against full resolution ("fast_mode"), a whole descent as one event stream
+solved window by window ("stream"), and the continuous-batching server on
 four concurrent 1280x720 descents ("serving").
 """
 import argparse
@@ -233,6 +234,11 @@ def run_extras(dd, torch):
                         "exact": fast_mode.evaluate(ws, 160, 90, reps=2),
                         "gamma_0.025": fast_mode.evaluate(ws, 160, 90, reps=2, gamma=0.025)}
     del ws
+    # the stream-wise estimation: one descent, window by window, in one launch
+    from paper_2209_13168_gb300 import stream as stream_mode
+    out["stream"] = stream_mode.evaluate(0)
+    out["stream"]["workload"] = ("one continuous 1280x720 descent stream (19 s, D = 1/(20 - t)), windows of 0.2 s "
+                                 "every 0.1 s solved in one batched launch; time to contact 1/D_end vs 20 - t_end")
     # four concurrent descents through the server
     from paper_2209_13168_gb300 import serve_bench
     out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8)

@@ -227,6 +227,22 @@ int dd_solve_window(dd_ctx* ctx, const dd_events* ev, const dd_window_params* p,
 int dd_resample(dd_ctx* ctx, const dd_events* in, int32_t W, int32_t H, int32_t W2, int32_t H2, float keep,
                 uint64_t seed, int16_t* x_out, int16_t* y_out, float* t_out, int64_t* n_out);
 
+/* The stream-wise estimation of Sec. 4.4: the divergence of a time-sorted
+ * event stream, window by window.  Window k covers [t0_k, t0_k + tau] with
+ * t0_k = (float)(t_start + k hop): the events whose (t - t0_k) lies in
+ * [0, tau] in binary32 (the test dd_solve applies), found by binary search
+ * and read in place (a device stream is not copied), solved together as one
+ * dd_solve_batch with the same params for every window.
+ *   stream   events sorted by t (host or device), its t0/tau ignored
+ *   out[k]   window k's result (status per window, as dd_solve_batch)
+ *   ttc[k]   (nullable) its time to contact at the window's end, 1/D_end in
+ *            seconds; infinity when D_end <= 0 or the window failed
+ *   first[k] (nullable) index of window k's first event in the stream
+ * Returns as dd_solve_batch.  Errors: DD_ERR_ARG (tau <= 0, hop <= 0,
+ * n_windows < 1, non-finite t_start), and dd_solve_batch's. */
+int dd_stream_solve(dd_ctx* ctx, const dd_events* stream, double t_start, float tau, double hop, int32_t n_windows,
+                    const dd_window_params* params, dd_result* out, float* ttc, int64_t* first);
+
 /* The FOE of the coarse frame: foe (W2/W), foe (H2/H) in binary32. */
 int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
                     float* foe_y2);

@@ -8,7 +8,7 @@ missing or fails to load, every entry point raises.
 The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
 dd_solve_trace, dd_solve_window, dd_solve_batch, dd_features, dd_set_warm_model,
 dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing, dd_destroy,
-dd_strerror, dd_resample, dd_resample_foe, dd_probe_peaks, the dd_serve_* and
+dd_strerror, dd_resample, dd_resample_foe, dd_stream_solve, dd_probe_peaks, the dd_serve_* and
 dd_mlp_* families); ``Context``, ``Server``
 and ``Mlp`` wrap them for numpy arrays (host events) and torch CUDA tensors
 (device events, features, training batches).
@@ -153,6 +153,8 @@ SIGNATURES = {
     "dd_resample": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _VP, _VP, _VP,
                                    _P(ctypes.c_int64)]),
+    "dd_stream_solve": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_double, ctypes.c_float, ctypes.c_double,
+                                       ctypes.c_int32, _P(dd_window_params), _P(dd_result), _VP, _VP]),
     "dd_resample_foe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -420,6 +422,21 @@ def dd_probe_peaks(stream_ptr=None):
     return a.value, b.value
 
 
+def dd_stream_solve(h, stream, t_start, tau, hop, n_windows, params=(-1.0, 1.0, 1e-4, 0.0)):
+    """Windows of a time-sorted stream (Events): (status, [results], ttc[k], first[k])."""
+    n = int(n_windows)
+    R = (dd_result * n)()
+    ttc = np.zeros(n, np.float32)
+    first = np.zeros(n, np.int64)
+    p = window_params(params)
+    rc = load().dd_stream_solve(h, ctypes.byref(stream.c), float(t_start), float(tau), float(hop), n, ctypes.byref(p),
+                                R, ttc.ctypes.data, first.ctypes.data)
+    res = [R[i].as_dict() for i in range(n)]
+    if rc != DD_OK and all(r["status"] == DD_OK for r in res):
+        raise DDError(rc, "dd_stream_solve")
+    return rc, res, ttc, first
+
+
 def dd_resample_foe(W, H, foe_x, foe_y, W2, H2):
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(load().dd_resample_foe(W, H, foe_x, foe_y, W2, H2, ctypes.byref(a), ctypes.byref(b)), "dd_resample_foe")
@@ -582,6 +599,10 @@ class Context:
         the fast mode's pre-pass (dd_resample); returns Events on the device."""
         x, y, t = dd_resample(self.h, ev, W, H, self.W, self.H, keep, seed)
         return Events(x.contiguous(), y.contiguous(), t.contiguous(), ev.c.t0, ev.c.tau)
+
+    def stream_solve(self, stream, t_start, tau, hop, n_windows, params=(-1.0, 1.0, 1e-4, 0.0)):
+        """The stream-wise estimation (dd_stream_solve): windows of `stream`."""
+        return dd_stream_solve(self.h, stream, t_start, tau, hop, n_windows, params)
 
     def set_warm_model(self, mlp):
         """The model DD_WARM_MODEL windows start from (None clears); keep it alive."""

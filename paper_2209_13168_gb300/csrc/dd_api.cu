@@ -908,6 +908,69 @@ int dd_resample(dd_ctx* c, const dd_events* in, int32_t W, int32_t H, int32_t W2
     return DD_OK;
 }
 
+int dd_stream_solve(dd_ctx* c, const dd_events* stream, double t_start, float tau, double hop, int32_t n_windows,
+                    const dd_window_params* params, dd_result* out, float* ttc, int64_t* first) {
+    if (!c || !stream || !params || !out || n_windows < 1 || !std::isfinite(t_start) || !std::isfinite(hop) ||
+        !(hop > 0.0) || !std::isfinite(tau) || !(tau > 0.0f))
+        return DD_ERR_ARG;
+    if (stream->n < 0 || (stream->n > 0 && (!stream->x || !stream->y || !stream->t))) return DD_ERR_ARG;
+    // The stream's windows: first event and count of each (device search,
+    // or host search for host arrays, with the same binary32 test).
+    std::vector<int64_t> f((size_t)n_windows), cnt((size_t)n_windows);
+    std::vector<float> t0((size_t)n_windows);
+    if (stream->device_ptrs) {
+        int64_t* d = nullptr;
+        DD_TRY(cudaMallocAsync((void**)&d, sizeof(int64_t) * 2 * n_windows + sizeof(float) * n_windows, c->stream));
+        cudaError_t e = dd::launch_stream_bounds(stream->t, stream->n, t_start, hop, tau, n_windows, d,
+                                                 d + n_windows, (float*)(d + 2 * n_windows), c->stream);
+        c->stats.kernel_launches++;
+        if (e == cudaSuccess) e = copy(c, f.data(), d, sizeof(int64_t) * n_windows, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = copy(c, cnt.data(), d + n_windows, sizeof(int64_t) * n_windows, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = copy(c, t0.data(), d + 2 * n_windows, sizeof(float) * n_windows, cudaMemcpyDeviceToHost);
+        cudaError_t e2 = cudaFreeAsync(d, c->stream);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = sync(c);
+        DD_TRY(e);
+    } else {
+        for (int32_t k = 0; k < n_windows; k++) {
+            const float w0 = (float)(t_start + hop * (double)k);
+            int64_t lo = 0, hi = stream->n;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (stream->t[mid] - w0 >= 0.0f) hi = mid;
+                else lo = mid + 1;
+            }
+            int64_t a = lo, b = stream->n;
+            while (a < b) {
+                const int64_t mid = a + (b - a) / 2;
+                if (stream->t[mid] - w0 > tau) b = mid;
+                else a = mid + 1;
+            }
+            f[k] = lo;
+            cnt[k] = a - lo;
+            t0[k] = w0;
+        }
+    }
+    std::vector<dd_events> ws((size_t)n_windows);
+    std::vector<dd_window_params> ps((size_t)n_windows, *params);
+    for (int32_t k = 0; k < n_windows; k++) {
+        dd_events& e = ws[k];
+        e.x = stream->x + f[k];
+        e.y = stream->y + f[k];
+        e.t = stream->t + f[k];
+        e.n = cnt[k];
+        e.t0 = t0[k];
+        e.tau = tau;
+        e.device_ptrs = stream->device_ptrs;
+        if (first) first[k] = f[k];
+    }
+    const int rc = solve_impl(c, ws.data(), n_windows, ps.data(), out, nullptr, 0, nullptr);
+    if (ttc)
+        for (int32_t k = 0; k < n_windows; k++)   // time to contact at the window's end: 1/D_end
+            ttc[k] = out[k].status == DD_OK && out[k].D_end > 0.0f ? 1.0f / out[k].D_end : INFINITY;
+    return rc;
+}
+
 int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
                     float* foe_y2) {
     if (W < 1 || H < 1 || W2 < 1 || H2 < 1 || !foe_x2 || !foe_y2) return DD_ERR_ARG;

@@ -1,8 +1,8 @@
-// The paper's fast mode on the device (Sec. 6, the resized and resampled
-// sequences): the events of a window with their coordinates scaled to a
-// coarser frame and a random share of them kept, compacted in their order.
-// A pre-pass: its output is an ordinary window for a context of the coarse
-// frame.
+// Pre-passes over event streams: the paper's fast mode (Sec. 6, the resized
+// and resampled sequences: the events of a window with their coordinates
+// scaled to a coarser frame and a random share of them kept, compacted in
+// their order), and the windows of a time-sorted stream (Sec. 4.4: the
+// stream taken batch by batch).
 //
 // Event i goes to the nearest coarse pixel centre, floor(x k + 1/2) with
 // k = W2/W in binary32, clamped to the frame, and is kept when the top 24
@@ -126,7 +126,41 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_write(Rs r, const int64_t* of
     }
 }
 
+// Window k of a time-sorted stream: the events with (t - t0_k) in [0, tau]
+// (binary32 subtraction, the test ingest applies), t0_k = t_start + k hop in
+// binary64 rounded to binary32.  (t - t0) is monotone in t, so both ends are
+// binary searches: first[k] = first event with t - t0 >= 0, count[k] = the
+// events before the first with t - t0 > tau.
+__global__ void k_stream_bounds(const float* t, int64_t n, double t_start, double hop, float tau, int32_t n_windows,
+                                int64_t* first, int64_t* count, float* t0_out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_windows) return;
+    const float t0 = (float)(t_start + hop * (double)k);
+    int64_t lo = 0, hi = n;                       // first i with t[i] - t0 >= 0
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (__fsub_rn(t[mid], t0) >= 0.0f) hi = mid;
+        else lo = mid + 1;
+    }
+    int64_t a = lo, b = n;                        // first i with t[i] - t0 > tau
+    while (a < b) {
+        const int64_t mid = a + (b - a) / 2;
+        if (__fsub_rn(t[mid], t0) > tau) b = mid;
+        else a = mid + 1;
+    }
+    first[k] = lo;
+    count[k] = a - lo;
+    t0_out[k] = t0;
+}
+
 }  // namespace
+
+cudaError_t launch_stream_bounds(const float* t, int64_t n, double t_start, double hop, float tau, int32_t n_windows,
+                                 int64_t* first, int64_t* count, float* t0, cudaStream_t s) {
+    if (n_windows <= 0) return cudaSuccess;
+    k_stream_bounds<<<(n_windows + 127) / 128, 128, 0, s>>>(t, n, t_start, hop, tau, n_windows, first, count, t0);
+    return cudaGetLastError();
+}
 
 int32_t resample_blocks(int64_t n) { return (int32_t)((n + RS_CHUNK - 1) / RS_CHUNK); }
 

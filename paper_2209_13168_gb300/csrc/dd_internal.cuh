@@ -239,6 +239,12 @@ cudaError_t launch_resample(const int16_t* x, const int16_t* y, const float* t, 
                             int32_t W2, int32_t H2, float keep, uint64_t seed, int16_t* x2, int16_t* y2, float* t2,
                             int32_t* counts, int64_t* offsets, int32_t* err, cudaStream_t s);
 
+// Windows of a time-sorted stream (dd_fast.cu): for k < n_windows, the
+// events with (t - t0_k) in [0, tau], t0_k = (float)(t_start + k hop): the
+// first index and the count of them, and t0_k.
+cudaError_t launch_stream_bounds(const float* t, int64_t n, double t_start, double hop, float tau, int32_t n_windows,
+                                 int64_t* first, int64_t* count, float* t0, cudaStream_t s);
+
 // Context accessors for the serving engine (dd_serve.cu).
 void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks,
               int32_t* pop_k, int32_t* queue_capacity, int64_t* max_rounds);

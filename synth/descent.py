@@ -197,6 +197,34 @@ def serve_spec5(stream, w, n_scale=1.0):
     return (1280, 720, 640.0, 360.0, n_sig, max(1, n_sig // 35), n_noise, D, 0.2, 5000 + 1000 * stream + w)
 
 
+def stream_slot_spec5(stream, k, n_scale=1.0):
+    """make_window arguments and start time of 0.1 s slot k of descent
+    `stream` as one continuous event stream: the serving descent's model at
+    t_k = 0.1 k (D = 1/(20 - t_k)), half the events of a 0.2 s window.  A
+    scene point of the slot moves as in the descent from t_k on, so
+    consecutive slots continue one constant-velocity descent."""
+    tk = 0.1 * k
+    D = 1.0 / (20.0 - tk)
+    N = int((50_000 + (1_000_000 - 50_000) * (D - 0.05) / 0.95) * n_scale) // 2
+    n_noise = int(round(0.15 * N))
+    n_sig = N - n_noise
+    return (1280, 720, 640.0, 360.0, n_sig, max(1, n_sig // 35), n_noise, D, 0.1, 7_000_000 + 1000 * stream + k), tk
+
+
+def stream_events5(stream, k0, k1, n_scale=1.0):
+    """numpy (x, y, t) of slots k0..k1-1 of descent `stream`, sorted by time."""
+    xs, ys, ts = [], [], []
+    for k in range(k0, k1):
+        spec, tk = stream_slot_spec5(stream, k, n_scale)
+        w = make_window(*spec, t0=tk)
+        xs.append(w.x)
+        ys.append(w.y)
+        ts.append(w.t)
+    x, y, t = np.concatenate(xs), np.concatenate(ys), np.concatenate(ts)
+    o = np.argsort(t, kind="stable")
+    return x[o], y[o], t[o]
+
+
 def serve_config5(stream, w, n_scale=1.0):
     """Window w of descent `stream` of the serving workload (serve_spec5)."""
     return make_window(*serve_spec5(stream, w, n_scale))

@@ -68,3 +68,22 @@ def make_window_gpu(spec, device="cuda", stream=None):
     if rc != 0:
         raise RuntimeError("synth_window_gpu failed (%d)" % rc)
     return GpuWindow(spec, x, y, t)
+
+
+def make_stream_gpu(stream, k0, k1, n_scale=1.0):
+    """The continuous descent stream (slots k0..k1-1 of synth.descent.
+    stream_slot_spec5) generated on the GPU: torch CUDA tensors (x, y, t)
+    sorted by time; times shifted as make_window(t0=...) shifts them
+    (binary64 sum rounded to binary32)."""
+    import torch
+    from .descent import stream_slot_spec5
+    xs, ys, ts = [], [], []
+    for k in range(k0, k1):
+        spec, tk = stream_slot_spec5(stream, k, n_scale)
+        w = make_window_gpu(spec)
+        xs.append(w.x)
+        ys.append(w.y)
+        ts.append((w.t.double() + tk).float())
+    x, y, t = torch.cat(xs), torch.cat(ys), torch.cat(ts)
+    t, o = torch.sort(t, stable=True)
+    return x[o].contiguous(), y[o].contiguous(), t.contiguous()
