@@ -54,7 +54,7 @@ class _Win(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("foe_x", ctypes.c_float),
                 ("foe_y", ctypes.c_float), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("t", ctypes.c_void_p), ("n", ctypes.c_int64), ("t0", ctypes.c_float),
-                ("tau", ctypes.c_float)]
+                ("tau", ctypes.c_float), ("t_ref", ctypes.c_float)]
 
 
 class _I128(ctypes.Structure):
@@ -144,18 +144,20 @@ def _check(rc):
 class Window:
     """Keeps the SoA arrays alive and exposes the C struct."""
 
-    def __init__(self, W, H, foe_x, foe_y, x, y, t, t0=0.0, tau=0.5):
+    def __init__(self, W, H, foe_x, foe_y, x, y, t, t0=0.0, tau=0.5, t_ref=None):
+        """t_ref: the time (since t0) the warp maps events to; None = tau (the paper's)."""
         self.x = np.ascontiguousarray(x, dtype=np.int16)
         self.y = np.ascontiguousarray(y, dtype=np.int16)
         self.t = np.ascontiguousarray(t, dtype=np.float32)
         self.W, self.H = int(W), int(H)
         self.c = _Win(int(W), int(H), float(foe_x), float(foe_y), self.x.ctypes.data,
-                      self.y.ctypes.data, self.t.ctypes.data, int(self.x.size), float(t0), float(tau))
+                      self.y.ctypes.data, self.t.ctypes.data, int(self.x.size), float(t0), float(tau),
+                      float(np.float32(tau)) if t_ref is None else float(t_ref))
 
     @classmethod
-    def of(cls, w):
+    def of(cls, w, t_ref=None):
         """From a synth.Window."""
-        return cls(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, w.t0, w.tau)
+        return cls(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, w.t0, w.tau, t_ref)
 
     @property
     def M(self):
@@ -302,4 +304,4 @@ def resample(win, W2, H2, keep, seed):
     m = lib().or_resample(ctypes.byref(win.c), W2, H2, keep, seed, x2.ctypes.data, y2.ctypes.data, t2.ctypes.data)
     fx, fy = ctypes.c_float(), ctypes.c_float()
     lib().or_resample_foe(ctypes.byref(win.c), W2, H2, ctypes.byref(fx), ctypes.byref(fy))
-    return Window(W2, H2, fx.value, fy.value, x2[:m], y2[:m], t2[:m], win.c.t0, win.c.tau)
+    return Window(W2, H2, fx.value, fy.value, x2[:m], y2[:m], t2[:m], win.c.t0, win.c.tau, win.c.t_ref)

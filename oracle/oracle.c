@@ -43,6 +43,7 @@ int or_validate(const or_window* w, float D_lo, float D_hi) {
     if (!isfinite(w->foe_x) || !isfinite(w->foe_y) || w->foe_x < 0.0f || w->foe_y < 0.0f ||
         w->foe_x > (float)w->W || w->foe_y > (float)w->H) return OR_ERR_ARG;
     if (!isfinite(w->tau) || !(w->tau > 0.0f) || !isfinite(w->t0)) return OR_ERR_ARG;
+    if (!(w->t_ref >= 0.0f) || !(w->t_ref <= w->tau)) return OR_ERR_ARG;
     if (!d_ok(D_lo, w->tau) || !d_ok(D_hi, w->tau) || !(D_lo <= D_hi)) return OR_ERR_ARG;
     /* Events come from a W x H sensor: pixel coordinates inside the frame. */
     for (int64_t i = 0; i < w->n; i++) {
@@ -58,7 +59,8 @@ int or_validate(const or_window* w, float D_lo, float D_hi) {
 /* Eq. (11) with Z0 = 1 and nu = -D: the event keeps its direction from the
  * FOE and its offset is scaled by s_i(D) = (1 - D t_i) / (1 - D tau).
  * Evaluated as g = 1/(1 - D*tau) once per hypothesis, then
- * s_i = (1 - D*t_i) * g. */
+ * s_i = (1 - D*t_i) * g.  Warping to another reference time t_ref replaces
+ * tau by t_ref in g (t_ref = 0: g = 1, the scale 1 - D t_i is linear in D). */
 static float warp_g(float D, float tau) {
     float q = 1.0f - D * tau;
     return 1.0f / q;
@@ -75,7 +77,7 @@ static int32_t cell(float foe, float d, float s) {
 }
 
 void or_warp_cells(const or_window* w, float D, int32_t* ux, int32_t* uy) {
-    float g = warp_g(D, w->tau);
+    float g = warp_g(D, w->t_ref);
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float s = warp_s(D, w->t[i] - w->t0, g);
@@ -88,8 +90,8 @@ void or_warp_cells(const or_window* w, float D, int32_t* ux, int32_t* uy) {
  * different pixel than the binary32 warp.  Diagnostic only. */
 int64_t or_fp64_disagreements(const or_window* w, float D) {
     int64_t bad = 0;
-    float g = warp_g(D, w->tau);
-    double Dd = D, tau = w->tau;
+    float g = warp_g(D, w->t_ref);
+    double Dd = D, tau = w->t_ref;
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float s = warp_s(D, w->t[i] - w->t0, g);
@@ -127,7 +129,7 @@ static void sums(const uint32_t* img, int64_t M, uint64_t* S, int64_t* N) {
 static void iwe_point(const or_window* w, float D, uint32_t* img) {
     int64_t M = (int64_t)w->W * w->H;
     memset(img, 0, (size_t)M * sizeof(uint32_t));
-    float g = warp_g(D, w->tau);
+    float g = warp_g(D, w->t_ref);
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float s = warp_s(D, w->t[i] - w->t0, g);
@@ -241,7 +243,7 @@ static i128 eval_bound(const or_window* w, float D_lo, float D_hi, uint32_t* img
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float sa, sb;
-        scale_interval(D_lo, D_hi, w->t[i] - w->t0, w->tau, &sa, &sb);
+        scale_interval(D_lo, D_hi, w->t[i] - w->t0, w->t_ref, &sa, &sb);
         nf += segment(w, dx, dy, sa, sb, img);
     }
     sums(img, M, Sb, n_cells);
@@ -551,7 +553,7 @@ int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, flo
     if (rc) return rc;
     double* bp = NULL;
     int64_t nb = 0, cap = 0;
-    double tau = w->tau;
+    double tau = w->t_ref;                        /* the warp's reference time */
     for (int64_t i = 0; i < w->n; i++) {
         double ti = (double)(w->t[i] - w->t0);
         for (int ax = 0; ax < 2; ax++) {

@@ -13,7 +13,9 @@
  * Parametrisation (reading of Sec. 4.1): the search variable is D = -nu, the
  * divergence at the window start with Z0 = 1, positive while approaching.
  * The warp of Eq. (11) to t = tau becomes
- *     x' = FOE + (x - FOE) * (1 - D t) / (1 - D tau).
+ *     x' = FOE + (x - FOE) * (1 - D t) / (1 - D tau);
+ * or_window.t_ref generalises the reference time (tau in the paper):
+ *     x' = FOE + (x - FOE) * (1 - D t) / (1 - D t_ref).
  *
  * Parity pins: see the module docstring of oracle/__init__.py and the tests
  * under tests/test_oracle_*.py.  Every function here is pinned.
@@ -33,6 +35,8 @@ typedef struct {
     const float *t;          /* event times [n], in [t0, t0 + tau]                 */
     int64_t n;
     float t0, tau;
+    float t_ref;             /* time (since t0) the warp maps events to, in [0, tau]: */
+                             /* the paper's tau, or 0 (the start of the window)       */
 } or_window;
 
 typedef struct { uint64_t lo; int64_t hi; } or_i128;   /* two's complement, little end first */
