@@ -74,7 +74,9 @@ typedef struct {
                             /*    conditional loop (no host round trips); 1: the host    */
                             /*    launches the rounds in batches and polls for the end   */
     int32_t max_splits;     /* most blocks that share one row band of a bound (default 16) */
-    int32_t reserved[1];
+    int32_t warp_to_start;  /* 0: events warped to the window's end (Eq. 11, the paper's  */
+                            /*    reference time tau); 1: to its start (reference time 0: */
+                            /*    x' = FOE + (x - FOE)(1 - D t), linear in D)             */
 } dd_config;
 
 /* One window of events in structure-of-arrays form. */

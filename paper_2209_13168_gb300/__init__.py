@@ -50,7 +50,7 @@ class dd_i128(ctypes.Structure):
 class dd_config(ctypes.Structure):
     _fields_ = [("pop_k", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("band_rows", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("max_splits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("max_splits", ctypes.c_int32), ("warp_to_start", ctypes.c_int32)]
 
 
 class dd_events(ctypes.Structure):
@@ -528,9 +528,10 @@ class Context:
     """A dd_ctx for one frame geometry (W x H, FOE)."""
 
     def __init__(self, W, H, foe_x, foe_y, pop_k=0, queue_capacity=0, band_rows=0, threads=0, max_rounds=0,
-                 host_loop=0, max_splits=0):
+                 host_loop=0, max_splits=0, warp_to_start=0):
         self.W, self.H = int(W), int(H)
-        self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds, host_loop, max_splits)
+        self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds, host_loop, max_splits,
+                             warp_to_start)
         self.h = dd_create(self.W, self.H, float(foe_x), float(foe_y), self.cfg)
 
     @property

@@ -680,6 +680,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
         return DD_ERR_ARG;
     if (k.threads && (k.threads % 32 || k.threads > 512)) return DD_ERR_ARG;
     if (k.max_splits < 0 || k.max_splits > 64 || k.host_loop < 0) return DD_ERR_ARG;
+    if (k.warp_to_start != 0 && k.warp_to_start != 1) return DD_ERR_ARG;
     if (!k.pop_k) k.pop_k = 1;
     if (!k.queue_capacity) k.queue_capacity = 8192;
     if (!k.max_rounds) k.max_rounds = 1 << 20;
@@ -712,6 +713,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     c->g.n_tiles = (H + rows - 1) / rows;
     c->g.n_tb = dd::time_buckets(H);
     c->g.max_splits = k.max_splits ? k.max_splits : 16;
+    c->g.ref0 = k.warp_to_start ? 1 : 0;
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
     c->cfg.threads = c->threads;
     c->cfg.band_rows = rows;

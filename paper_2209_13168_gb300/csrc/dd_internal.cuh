@@ -135,8 +135,11 @@ struct Geom {
     float fx, fy;
     int32_t band_rows, n_tiles, n_tb, max_splits;
     int32_t split_target;   // units a round needs before its bounds stop splitting (0: no cap)
-    int32_t pad;
+    int32_t ref0;           // 1: the warp maps events to the window's start (t_ref = 0), not its end
 };
+
+// The warp's reference time for a window of length tau.
+__host__ __device__ inline float warp_tref(const Geom& g, float tau) { return g.ref0 ? 0.0f : tau; }
 
 // Splits a bound task may take in a round of `units` (task, row band) units:
 // none once the round alone fills the evaluation grid, else enough to reach

@@ -9,7 +9,8 @@
 //
 // Arithmetic contract.  The warp is evaluated in IEEE binary32 with one
 // rounding per operation, in this order, with no contraction into FMA:
-//     g = 1/(1 - D*tau);  s = (1 - D*t)*g;  cell = floor((FOE + d*s) + 1/2).
+//     g = 1/(1 - D*t_ref);  s = (1 - D*t)*g;  cell = floor((FOE + d*s) + 1/2),
+// t_ref = tau (the window's end, the paper's warp) or 0 (its start).
 // __fmul_rn/__fadd_rn/__fsub_rn/__frcp_rn are never contracted.  The pixel a
 // warped event lands in is an integer decided by that arithmetic, and all
 // later work (counts, sums of squares, keys) is exact integer arithmetic, so
@@ -224,10 +225,11 @@ __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float 
                                    float bscale, int b, int y0, int y1, int& e0, int& e1) {
     const float tl = fmaxf(0.0f, __fdividef((float)b - 1e-3f, bscale));
     const float th = fminf(tau, __fdividef((float)b + 1.001f, bscale));
+    const float tref = warp_tref(g, tau);
     float smin = 3.0e38f, smax = -3.0e38f;
     for (int i = 0; i < 4; i++) {
         const float D = (i & 1) ? Dh : Dl, t = (i & 2) ? th : tl;
-        const float s = __fdividef(1.0f - D * t, 1.0f - D * tau);
+        const float s = __fdividef(1.0f - D * t, 1.0f - D * tref);
         smin = fminf(smin, s);
         smax = fmaxf(smax, s);
     }
@@ -423,7 +425,8 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
                                            unsigned long long& S, unsigned long long& C, unsigned long long& full) {
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tau), gh = warp_g(Dh, tau);
+    const float tref = warp_tref(g, tau);
+    const float Dl = tk.D_lo, Dh = tk.D_hi, gl = warp_g(Dl, tref), gh = warp_g(Dh, tref);
     // The cells of up to 32 queued segments, one event per lane (`valid`,
     // with the end scales and end cells computed when it was queued): short
     // runs walked by their own lane, long runs spread over the warp as
@@ -593,7 +596,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     unsigned long long S = 0, C = 0;
     bool dense = false;
     if (tk.kind == TASK_POINT) {
-        const float D = tk.D_lo, gg = warp_g(D, tau);
+        const float D = tk.D_lo, gg = warp_g(D, warp_tref(g, tau));
         uint32_t Ct = 0;                          // at most one increment per event
 #pragma unroll 4
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {

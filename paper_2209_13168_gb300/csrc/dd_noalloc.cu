@@ -105,7 +105,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     g.n_tb = dd::time_buckets(H);
     g.max_splits = 1;
     g.split_target = 0;
-    g.pad = 0;
+    g.ref0 = 0;
     if (g.n_tiles > NA_MAX_TILES) return DD_ERR_CAPACITY;
     if (dd::eval_smem_setup(g) != cudaSuccess) return DD_ERR_CUDA;
 
