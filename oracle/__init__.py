@@ -54,7 +54,7 @@ class _Win(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("foe_x", ctypes.c_float),
                 ("foe_y", ctypes.c_float), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("t", ctypes.c_void_p), ("n", ctypes.c_int64), ("t0", ctypes.c_float),
-                ("tau", ctypes.c_float), ("t_ref", ctypes.c_float)]
+                ("tau", ctypes.c_float), ("t_ref", ctypes.c_float), ("p", ctypes.c_void_p)]
 
 
 class _I128(ctypes.Structure):
@@ -144,24 +144,32 @@ def _check(rc):
 class Window:
     """Keeps the SoA arrays alive and exposes the C struct."""
 
-    def __init__(self, W, H, foe_x, foe_y, x, y, t, t0=0.0, tau=0.5, t_ref=None):
-        """t_ref: the time (since t0) the warp maps events to; None = tau (the paper's)."""
+    def __init__(self, W, H, foe_x, foe_y, x, y, t, t0=0.0, tau=0.5, t_ref=None, p=None):
+        """t_ref: the time (since t0) the warp maps events to; None = tau (the paper's).
+        p: event polarities (int8) for the per-polarity objective; None = unused."""
         self.x = np.ascontiguousarray(x, dtype=np.int16)
         self.y = np.ascontiguousarray(y, dtype=np.int16)
         self.t = np.ascontiguousarray(t, dtype=np.float32)
+        self.p = None if p is None else np.ascontiguousarray(p, dtype=np.int8)
         self.W, self.H = int(W), int(H)
+        self.planes = 1 if p is None else 2
         self.c = _Win(int(W), int(H), float(foe_x), float(foe_y), self.x.ctypes.data,
                       self.y.ctypes.data, self.t.ctypes.data, int(self.x.size), float(t0), float(tau),
-                      float(np.float32(tau)) if t_ref is None else float(t_ref))
+                      float(np.float32(tau)) if t_ref is None else float(t_ref),
+                      None if p is None else self.p.ctypes.data)
 
     @classmethod
-    def of(cls, w, t_ref=None):
-        """From a synth.Window."""
-        return cls(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, w.t0, w.tau, t_ref)
+    def of(cls, w, t_ref=None, polarity=False):
+        """From a synth.Window; polarity=True uses its polarities."""
+        return cls(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, w.t0, w.tau, t_ref, w.p if polarity else None)
 
     @property
     def M(self):
         return self.W * self.H
+
+    def image(self, img):
+        """A flat image buffer as [H][W], or [2][H][W] with polarity planes."""
+        return img.reshape(self.H, self.W) if self.planes == 1 else img.reshape(2, self.H, self.W)
 
 
 def validate(win, D_lo, D_hi):
@@ -194,19 +202,19 @@ def scale_interval(D_lo, D_hi, t_rel, tau):
 def contrast(win, D, want_iwe=False):
     """(K, S, N_in, iwe-or-None) at hypothesis D."""
     k, s, n = _I128(), ctypes.c_uint64(), ctypes.c_int64()
-    img = np.zeros(win.M, np.uint32) if want_iwe else None
+    img = np.zeros(win.planes * win.M, np.uint32) if want_iwe else None
     _check(lib().or_contrast(ctypes.byref(win.c), D, ctypes.byref(k), ctypes.byref(s), ctypes.byref(n),
                              img.ctypes.data if want_iwe else None))
-    return k.value(), int(s.value), int(n.value), (img.reshape(win.H, win.W) if want_iwe else None)
+    return k.value(), int(s.value), int(n.value), (win.image(img) if want_iwe else None)
 
 
 def bound(win, D_lo, D_hi, want_iwe=False):
     """(Kbar, Sbar, N_full, iwe-or-None) over [D_lo, D_hi]."""
     k, s, n = _I128(), ctypes.c_uint64(), ctypes.c_int64()
-    img = np.zeros(win.M, np.uint32) if want_iwe else None
+    img = np.zeros(win.planes * win.M, np.uint32) if want_iwe else None
     _check(lib().or_bound(ctypes.byref(win.c), D_lo, D_hi, ctypes.byref(k), ctypes.byref(s),
                           ctypes.byref(n), img.ctypes.data if want_iwe else None))
-    return k.value(), int(s.value), int(n.value), (img.reshape(win.H, win.W) if want_iwe else None)
+    return k.value(), int(s.value), int(n.value), (win.image(img) if want_iwe else None)
 
 
 def solve(win, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, K_pop=1, trace_cap=0, warm=None):

@@ -115,6 +115,15 @@ static i128 key(int64_t M, uint64_t S, int64_t N) {
     return (i128)M * (i128)S - (i128)N * (i128)N;
 }
 
+/* Polarity (the paper leaves it out of Eq. (12) and notes it could be used):
+ * with or_window.p given, each polarity gets its own image H_p of M pixels
+ * and the objective is C_on + C_off, so
+ *     M^2 (C_on + C_off) = M (S_on + S_off) - N_on^2 - N_off^2.
+ * Each plane is an image of non-negative counts, so Eqs. (14)-(19) bound it
+ * plane by plane and the bounds add. */
+static int32_t planes(const or_window* w) { return w->p ? 2 : 1; }
+static int64_t plane_of(const or_window* w, int64_t i) { return (w->p && w->p[i] <= 0) ? 1 : 0; }
+
 static void sums(const uint32_t* img, int64_t M, uint64_t* S, int64_t* N) {
     uint64_t s = 0;
     int64_t n = 0;
@@ -126,29 +135,45 @@ static void sums(const uint32_t* img, int64_t M, uint64_t* S, int64_t* N) {
     *N = n;
 }
 
+/* Eq. (13) over the planes of img: K = sum_p (M S_p - N_p^2); S, N totals. */
+static i128 plane_key(const or_window* w, const uint32_t* img, uint64_t* S, int64_t* N) {
+    int64_t M = (int64_t)w->W * w->H;
+    i128 k = 0;
+    *S = 0;
+    *N = 0;
+    for (int32_t p = 0; p < planes(w); p++) {
+        uint64_t s;
+        int64_t n;
+        sums(img + p * M, M, &s, &n);
+        k += key(M, s, n);
+        *S += s;
+        *N += n;
+    }
+    return k;
+}
+
 static void iwe_point(const or_window* w, float D, uint32_t* img) {
     int64_t M = (int64_t)w->W * w->H;
-    memset(img, 0, (size_t)M * sizeof(uint32_t));
+    memset(img, 0, (size_t)(planes(w) * M) * sizeof(uint32_t));
     float g = warp_g(D, w->t_ref);
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float s = warp_s(D, w->t[i] - w->t0, g);
         int32_t ux = cell(w->foe_x, dx, s), uy = cell(w->foe_y, dy, s);
-        if (ux >= 0 && ux < w->W && uy >= 0 && uy < w->H) img[(int64_t)uy * w->W + ux] += 1;
+        if (ux >= 0 && ux < w->W && uy >= 0 && uy < w->H) img[plane_of(w, i) * M + (int64_t)uy * w->W + ux] += 1;
     }
 }
 
 static i128 eval_point(const or_window* w, float D, uint32_t* img, uint64_t* S, int64_t* N) {
     iwe_point(w, D, img);
-    sums(img, (int64_t)w->W * w->H, S, N);
-    return key((int64_t)w->W * w->H, *S, *N);
+    return plane_key(w, img, S, N);
 }
 
 int or_contrast(const or_window* w, float D, or_i128* K, uint64_t* S, int64_t* N_in, uint32_t* iwe) {
     int rc = or_validate(w, D, D);
     if (rc) return rc;
     int64_t M = (int64_t)w->W * w->H;
-    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)(planes(w) * M) * sizeof(uint32_t));
     if (!img) return OR_ERR_OOM;
     uint64_t s;
     int64_t n;
@@ -234,21 +259,33 @@ static int segment(const or_window* w, float dx, float dy, float sa, float sb, u
 
 /* Eqs. (14)-(19): Kbar = M * Sbar - N_full^2 with Sbar = sum_u Hbar(u)^2
  * (Eq. (18)) and N_full = M * mu_lower (Eq. (19)).  Since Sbar >= S(D) and
- * 0 <= N_full <= N_in(D) for every D in the interval, Kbar >= K(D). */
+ * 0 <= N_full <= N_in(D) for every D in the interval, Kbar >= K(D).  With
+ * polarity planes, per plane: Kbar = sum_p (M Sbar_p - N_full,p^2). */
 static i128 eval_bound(const or_window* w, float D_lo, float D_hi, uint32_t* img, uint64_t* Sb,
                        int64_t* Nfull, int64_t* n_cells) {
     int64_t M = (int64_t)w->W * w->H;
-    memset(img, 0, (size_t)M * sizeof(uint32_t));
-    int64_t nf = 0;
+    memset(img, 0, (size_t)(planes(w) * M) * sizeof(uint32_t));
+    int64_t nf[2] = {0, 0};
     for (int64_t i = 0; i < w->n; i++) {
         float dx = (float)w->x[i] - w->foe_x, dy = (float)w->y[i] - w->foe_y;
         float sa, sb;
         scale_interval(D_lo, D_hi, w->t[i] - w->t0, w->t_ref, &sa, &sb);
-        nf += segment(w, dx, dy, sa, sb, img);
+        int64_t p = plane_of(w, i);
+        nf[p] += segment(w, dx, dy, sa, sb, img + p * M);
     }
-    sums(img, M, Sb, n_cells);
-    *Nfull = nf;
-    return key(M, *Sb, nf);
+    i128 k = 0;
+    *Sb = 0;
+    *n_cells = 0;
+    for (int32_t p = 0; p < planes(w); p++) {
+        uint64_t s;
+        int64_t c;
+        sums(img + p * M, M, &s, &c);
+        k += key(M, s, nf[p]);
+        *Sb += s;
+        *n_cells += c;
+    }
+    *Nfull = nf[0] + nf[1];
+    return k;
 }
 
 int or_bound(const or_window* w, float D_lo, float D_hi, or_i128* Kbar, uint64_t* Sbar,
@@ -256,7 +293,7 @@ int or_bound(const or_window* w, float D_lo, float D_hi, or_i128* Kbar, uint64_t
     int rc = or_validate(w, D_lo, D_hi);
     if (rc) return rc;
     int64_t M = (int64_t)w->W * w->H;
-    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    uint32_t* img = iwe ? iwe : (uint32_t*)malloc((size_t)(planes(w) * M) * sizeof(uint32_t));
     if (!img) return OR_ERR_OOM;
     uint64_t s;
     int64_t nf, nc;
@@ -364,7 +401,7 @@ int or_solve_warm(const or_window* w, float D_lo, float D_hi, float tol_D, doubl
         return OR_ERR_ARG;
     const int64_t M = (int64_t)w->W * w->H;
     const i128 gamma_K = (i128)floor(gamma * (double)M * (double)M);
-    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    uint32_t* img = (uint32_t*)malloc((size_t)(planes(w) * M) * sizeof(uint32_t));
     node* pop = (node*)malloc((size_t)K_pop * sizeof(node));
     i128* kc = (i128*)malloc((size_t)K_pop * sizeof(i128));
     float* dc = (float*)malloc((size_t)K_pop * sizeof(float));
@@ -504,7 +541,7 @@ int or_grid_max(const or_window* w, float D_lo, float D_hi, float h, or_i128* K_
     if (rc) return rc;
     if (!(h > 0.0f)) return OR_ERR_ARG;
     int64_t M = (int64_t)w->W * w->H;
-    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    uint32_t* img = (uint32_t*)malloc((size_t)(planes(w) * M) * sizeof(uint32_t));
     if (!img) return OR_ERR_OOM;
     int64_t steps = (int64_t)floor(((double)D_hi - (double)D_lo) / (double)h);
     i128 best = 0;
@@ -576,7 +613,7 @@ int or_sweep_max(const or_window* w, float D_lo, float D_hi, or_i128* K_max, flo
     add_bp(&bp, &nb, &cap, D_hi);
     qsort(bp, (size_t)nb, sizeof(double), cmp_double);
     int64_t M = (int64_t)w->W * w->H;
-    uint32_t* img = (uint32_t*)malloc((size_t)M * sizeof(uint32_t));
+    uint32_t* img = (uint32_t*)malloc((size_t)(planes(w) * M) * sizeof(uint32_t));
     if (!img) { free(bp); return OR_ERR_OOM; }
     i128 best = 0;
     float bd = D_lo;

@@ -16,6 +16,9 @@
  *     x' = FOE + (x - FOE) * (1 - D t) / (1 - D tau);
  * or_window.t_ref generalises the reference time (tau in the paper):
  *     x' = FOE + (x - FOE) * (1 - D t) / (1 - D t_ref).
+ * or_window.p, when given, splits the image of warped events into one plane
+ * per polarity; the objective is the sum of the planes' contrasts, and images
+ * (iwe arguments) hold both planes, plane 0 first (2 W H cells).
  *
  * Parity pins: see the module docstring of oracle/__init__.py and the tests
  * under tests/test_oracle_*.py.  Every function here is pinned.
@@ -37,6 +40,9 @@ typedef struct {
     float t0, tau;
     float t_ref;             /* time (since t0) the warp maps events to, in [0, tau]: */
                              /* the paper's tau, or 0 (the start of the window)       */
+    const int8_t *p;         /* event polarities [n], or NULL: polarity unused (the   */
+                             /* paper's objective); else one image per polarity      */
+                             /* (plane 0: p > 0, plane 1: p <= 0), contrasts added   */
 } or_window;
 
 typedef struct { uint64_t lo; int64_t hi; } or_i128;   /* two's complement, little end first */

@@ -9,8 +9,10 @@ of expansion as
 
 with D the divergence at the window start (positive while approaching).  Each
 signal event samples one point at a random time and is rounded to the nearest
-pixel centre; noise events are uniform in space and time.  Events are returned
-sorted by time, as a camera emits them.
+pixel centre; noise events are uniform in space and time.  A scene point is
+brighter or darker than its surround with equal odds, and all its events carry
+that polarity (+1 / -1); noise events draw theirs one by one.  Events are
+returned sorted by time, as a camera emits them.
 
 Every random number comes from the counter-based SplitMix64 stream in
 ``synth.rng``, addressed by (seed, stream, counter), so any window can be
@@ -23,7 +25,7 @@ import numpy as np
 
 from .rng import stream_key, uniform01
 
-_S_POINT, _S_TIME, _S_NOISE, _S_POL, _S_PARAM = 1, 2, 3, 4, 5
+_S_POINT, _S_TIME, _S_NOISE, _S_POL, _S_PARAM, _S_NOISE_POL = 1, 2, 3, 4, 5, 6
 _MAX_ATTEMPTS = 64     # point redraws before giving up
 _TRIES = 8             # time redraws per event before the point is redrawn
 
@@ -38,7 +40,7 @@ class Window:
     x: np.ndarray          # int16 [N]
     y: np.ndarray          # int16 [N]
     t: np.ndarray          # float32 [N], in [t0, t0 + tau]
-    p: np.ndarray          # int8 [N], +1 / -1 (not read by the estimator)
+    p: np.ndarray          # int8 [N], +1 / -1 (read only by the per-polarity objective)
     t0: float
     tau: float
     D_true: float
@@ -52,9 +54,13 @@ class Window:
         return int(self.x.shape[0])
 
 
+def _polarity(u):
+    return np.where(u < 0.5, 1, -1).astype(np.int8)
+
+
 def _signal(W, H, fx, fy, n_signal, n_points, D, tau, seed):
     if n_signal == 0:
-        return (np.zeros(0, np.int16),) * 2 + (np.zeros(0, np.float32),)
+        return (np.zeros(0, np.int16),) * 2 + (np.zeros(0, np.float32), np.zeros(0, np.int8))
     n_points = max(1, min(n_points, n_signal))
     base, extra = divmod(n_signal, n_points)
     e_max = base + (1 if extra else 0)
@@ -95,30 +101,31 @@ def _signal(W, H, fx, fy, n_signal, n_points, D, tau, seed):
     if pending.size:
         raise RuntimeError("synthetic scene: %d points never fit in the frame" % pending.size)
     mask = j[None, :] < counts[:, None]
-    return xs[mask].astype(np.int16), ys[mask].astype(np.int16), ts[mask]
+    pol = _polarity(uniform01(stream_key(seed, _S_POL), np.arange(n_points, dtype=np.uint64)))
+    return xs[mask].astype(np.int16), ys[mask].astype(np.int16), ts[mask], np.repeat(pol, counts)
 
 
 def make_window(W, H, foe_x, foe_y, n_signal, n_points, n_noise, D, tau, seed, t0=0.0):
     """Generate one window; see the module docstring for the model."""
     if not (1.0 - D * tau > 0.0):
         raise ValueError("D*tau must stay below 1")
-    sx, sy, st = _signal(W, H, float(foe_x), float(foe_y), int(n_signal), int(n_points), float(D),
-                         float(tau), seed)
+    sx, sy, st, sp = _signal(W, H, float(foe_x), float(foe_y), int(n_signal), int(n_points), float(D),
+                             float(tau), seed)
     kn = stream_key(seed, _S_NOISE)
     c = np.arange(int(n_noise), dtype=np.uint64)
     nx = np.minimum(np.floor(uniform01(kn, 3 * c) * W), W - 1).astype(np.int16)
     ny = np.minimum(np.floor(uniform01(kn, 3 * c + 1) * H), H - 1).astype(np.int16)
     tau32 = np.float32(tau)
     nt = np.minimum((uniform01(kn, 3 * c + 2) * float(tau32)).astype(np.float32), tau32)
+    npol = _polarity(uniform01(stream_key(seed, _S_NOISE_POL), c))
     x = np.concatenate([sx, nx])
     y = np.concatenate([sy, ny])
     t = np.concatenate([st, nt])
+    p = np.concatenate([sp, npol])
     order = np.argsort(t, kind="stable")
-    x, y, t = x[order], y[order], t[order]
+    x, y, t, p = x[order], y[order], t[order], p[order]
     if t0 != 0.0:
         t = (t.astype(np.float64) + t0).astype(np.float32)
-    kpol = stream_key(seed, _S_POL)
-    p = np.where(uniform01(kpol, np.arange(x.size, dtype=np.uint64)) < 0.5, -1, 1).astype(np.int8)
     return Window(W=W, H=H, foe_x=float(foe_x), foe_y=float(foe_y), x=np.ascontiguousarray(x),
                   y=np.ascontiguousarray(y), t=np.ascontiguousarray(t), p=p, t0=float(t0),
                   tau=float(np.float32(tau)), D_true=float(D), n_signal=int(n_signal),

@@ -5,7 +5,8 @@
 // the same counters and applies the same scene model in binary64, so a
 // window is identical, event for event, to make_window()'s; only the order
 // of events differs (points first, then noise; the estimator's results do
-// not depend on event order).  Polarity is not generated.
+// not depend on event order).  Polarities (optional output) follow the same
+// model: one per scene point, one per noise event.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -33,13 +34,15 @@ struct Params {
     double fx, fy, D;
     float tau;
     int64_t n_signal, n_points, n_noise;
-    uint64_t kp, kt, kn;
+    uint64_t kp, kt, kn, kpol, knpol;
     int64_t base, extra, e_max;
 };
 
 // One thread per scene point: redraw the point until every one of its events
 // finds an in-frame time within TRIES draws, then write its events.
-__global__ void k_points(Params p, int16_t* x, int16_t* y, float* t, int32_t* failed) {
+__device__ inline int8_t polarity(double u) { return u < 0.5 ? (int8_t)1 : (int8_t)-1; }
+
+__global__ void k_points(Params p, int16_t* x, int16_t* y, float* t, int8_t* pol, int32_t* failed) {
     const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pt >= p.n_points) return;
     const int64_t cnt = p.base + (pt < p.extra ? 1 : 0);
@@ -66,12 +69,18 @@ __global__ void k_points(Params p, int16_t* x, int16_t* y, float* t, int32_t* fa
             }
             ok = found;
         }
-        if (ok) return;
+        if (ok) {
+            if (pol) {
+                const int8_t v = polarity(u01(p.kpol, (uint64_t)pt));
+                for (int64_t j = 0; j < cnt; j++) pol[out0 + j] = v;
+            }
+            return;
+        }
     }
     atomicAdd(failed, 1);
 }
 
-__global__ void k_noise(Params p, int16_t* x, int16_t* y, float* t) {
+__global__ void k_noise(Params p, int16_t* x, int16_t* y, float* t, int8_t* pol) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_noise) return;
     const uint64_t c = (uint64_t)i;
@@ -84,19 +93,21 @@ __global__ void k_noise(Params p, int16_t* x, int16_t* y, float* t) {
     x[o] = (int16_t)nx;
     y[o] = (int16_t)ny;
     t[o] = tf;
+    if (pol) pol[o] = polarity(u01(p.knpol, c));
 }
 
 }  // namespace
 
 extern "C" {
 
-// Generate one window into device arrays x, y, t of n_signal + n_noise
-// entries (signal events of point p first, then noise), on `stream`.
+// Generate one window into device arrays x, y, t (and polarities p, when
+// not null) of n_signal + n_noise entries (signal events of point p first,
+// then noise), on `stream`.
 // Returns 0, or -1 for bad arguments, -2 for a CUDA error, -3 if some point
 // never fit in the frame.  Synchronises the stream.
 int synth_window_gpu(int32_t W, int32_t H, double foe_x, double foe_y, int64_t n_signal, int64_t n_points,
                      int64_t n_noise, double D, double tau, uint64_t seed, int16_t* x, int16_t* y, float* t,
-                     void* stream) {
+                     int8_t* pol, void* stream) {
     if (W < 1 || H < 1 || n_signal < 0 || n_noise < 0 || !(1.0 - D * tau > 0.0)) return -1;
     cudaStream_t s = (cudaStream_t)stream;
     Params p;
@@ -111,6 +122,8 @@ int synth_window_gpu(int32_t W, int32_t H, double foe_x, double foe_y, int64_t n
     p.kp = stream_key(seed, 1);
     p.kt = stream_key(seed, 2);
     p.kn = stream_key(seed, 3);
+    p.kpol = stream_key(seed, 4);
+    p.knpol = stream_key(seed, 6);
     int32_t* failed = nullptr;
     if (cudaMallocAsync((void**)&failed, sizeof(int32_t), s) != cudaSuccess) return -2;
     if (cudaMemsetAsync(failed, 0, sizeof(int32_t), s) != cudaSuccess) return -2;
@@ -121,9 +134,9 @@ int synth_window_gpu(int32_t W, int32_t H, double foe_x, double foe_y, int64_t n
         p.base = n_signal / np;
         p.extra = n_signal % np;
         p.e_max = p.base + (p.extra ? 1 : 0);
-        k_points<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(p, x, y, t, failed);
+        k_points<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(p, x, y, t, pol, failed);
     }
-    if (n_noise > 0) k_noise<<<(unsigned)((n_noise + 255) / 256), 256, 0, s>>>(p, x, y, t);
+    if (n_noise > 0) k_noise<<<(unsigned)((n_noise + 255) / 256), 256, 0, s>>>(p, x, y, t, pol);
     int32_t h_failed = 0;
     if (cudaMemcpyAsync(&h_failed, failed, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -2;
     if (cudaFreeAsync(failed, s) != cudaSuccess) return -2;

@@ -32,7 +32,7 @@ def lib():
         L.synth_window_gpu.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
-                                       ctypes.c_void_p, ctypes.c_void_p]
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.synth_window_gpu.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -41,33 +41,36 @@ def lib():
 class GpuWindow:
     """A window whose SoA events live in torch CUDA tensors."""
 
-    def __init__(self, spec, x, y, t):
+    def __init__(self, spec, x, y, t, p=None):
         (self.W, self.H, self.foe_x, self.foe_y, self.n_signal, self.n_points, self.n_noise, self.D_true,
          tau, self.seed) = spec
         import numpy as np
         self.tau = float(np.float32(tau))
         self.t0 = 0.0
-        self.x, self.y, self.t = x, y, t
+        self.x, self.y, self.t, self.p = x, y, t, p
 
     @property
     def n(self):
         return int(self.x.shape[0])
 
 
-def make_window_gpu(spec, device="cuda", stream=None):
-    """Generate make_window(*spec) on the GPU; returns a GpuWindow."""
+def make_window_gpu(spec, device="cuda", stream=None, polarity=False):
+    """Generate make_window(*spec) on the GPU; returns a GpuWindow (with
+    its int8 polarities in .p when polarity=True, else .p = None)."""
     import torch
     W, H, fx, fy, n_sig, n_pts, n_noise, D, tau, seed = spec
     n = int(n_sig) + int(n_noise)
     x = torch.empty(n, dtype=torch.int16, device=device)
     y = torch.empty(n, dtype=torch.int16, device=device)
     t = torch.empty(n, dtype=torch.float32, device=device)
+    p = torch.empty(n, dtype=torch.int8, device=device) if polarity else None
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     rc = lib().synth_window_gpu(int(W), int(H), float(fx), float(fy), int(n_sig), int(n_pts), int(n_noise), float(D),
-                                float(tau), int(seed), x.data_ptr(), y.data_ptr(), t.data_ptr(), s)
+                                float(tau), int(seed), x.data_ptr(), y.data_ptr(), t.data_ptr(),
+                                p.data_ptr() if polarity else None, s)
     if rc != 0:
         raise RuntimeError("synth_window_gpu failed (%d)" % rc)
-    return GpuWindow(spec, x, y, t)
+    return GpuWindow(spec, x, y, t, p)
 
 
 def make_stream_gpu(stream, k0, k1, n_scale=1.0):

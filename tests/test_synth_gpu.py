@@ -14,9 +14,12 @@ if not torch.cuda.is_available():
 from synth.gpu import make_window_gpu  # noqa: E402
 
 
-def as_sorted(x, y, t):
-    a = np.stack([np.asarray(t, np.float64), np.asarray(x, np.float64), np.asarray(y, np.float64)], axis=1)
-    return a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+def as_sorted(x, y, t, p=None):
+    cols = [np.asarray(t, np.float64), np.asarray(x, np.float64), np.asarray(y, np.float64)]
+    if p is not None:
+        cols.append(np.asarray(p, np.float64))
+    a = np.stack(cols, axis=1)
+    return a[np.lexsort(tuple(a[:, k] for k in range(a.shape[1] - 1, -1, -1)))]
 
 
 @pytest.mark.parametrize("spec", [
@@ -42,3 +45,16 @@ def test_gpu_generator_batch_windows():
         g = make_window_gpu(spec)
         assert np.array_equal(as_sorted(w.x, w.y, w.t),
                               as_sorted(g.x.cpu().numpy(), g.y.cpu().numpy(), g.t.cpu().numpy()))
+
+
+@pytest.mark.parametrize("spec", [
+    (346, 260, 173.0, 130.0, 3000, 150, 1000, 0.2, 0.5, 1000),
+    (97, 61, 48.5, 30.0, 900, 45, 300, -0.45, 0.35, 9),
+])
+def test_gpu_generator_polarities(spec):
+    # (t, x, y, p) as a multiset: the polarity of every event as numpy draws it
+    w = make_window(*spec)
+    g = make_window_gpu(spec, polarity=True)
+    assert np.array_equal(as_sorted(w.x, w.y, w.t, w.p),
+                          as_sorted(g.x.cpu().numpy(), g.y.cpu().numpy(), g.t.cpu().numpy(), g.p.cpu().numpy()))
+    assert set(np.unique(w.p)) == {-1, 1}
