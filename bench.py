@@ -234,9 +234,9 @@ def run_extras(dd, torch):
                         "exact": fast_mode.evaluate(ws, 160, 90, reps=2),
                         "gamma_0.025": fast_mode.evaluate(ws, 160, 90, reps=2, gamma=0.025)}
     del ws
-    # the warp to the window's start (t_ref = 0) against the paper's (t_ref = tau)
-    from paper_2209_13168_gb300 import reference_time
-    out["reference_time"] = reference_time.evaluate(reps=2)
+    # objective variants (warp to the window's start, polarity planes) against the paper's
+    from paper_2209_13168_gb300 import objective_variants
+    out["objective_variants"] = objective_variants.evaluate(reps=2)
     # the stream-wise estimation: one descent, window by window, in one launch
     from paper_2209_13168_gb300 import stream as stream_mode
     out["stream"] = stream_mode.evaluate(0)

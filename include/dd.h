@@ -33,7 +33,17 @@
  *   demand), its CUDA stream and its BnB queue.
  * - Threads.  A context is not thread-safe: use one context per host thread.
  * - Events.  0 <= x < W, 0 <= y < H, t finite with 0 <= (t - t0) <= tau (the
- *   difference taken in binary32).  Polarity is not read (Sec. 4.2).
+ *   difference taken in binary32).  Polarity is not read (Sec. 4.2: the
+ *   paper's objective leaves it out), unless the context was created with
+ *   dd_config.polarity = 1.
+ * - Polarity planes (dd_config.polarity = 1; the paper notes that polarity
+ *   could be used and does not say how).  Each polarity gets its own image:
+ *   plane 0 holds the events with p > 0, plane 1 those with p <= 0, each of
+ *   M = W*H pixels, and the objective is the sum of the two planes' contrasts:
+ *       K = M (S_0 + S_1) - N_0^2 - N_1^2,
+ *   bounded plane by plane by Eqs. 14-19 (Kbar = M (Sbar_0 + Sbar_1) -
+ *   N_full,0^2 - N_full,1^2).  S, N_in, N_full outputs are the planes' totals;
+ *   images hold both planes, plane 0 first (2 M cells per hypothesis).
  */
 #ifndef DD_H
 #define DD_H
@@ -77,6 +87,9 @@ typedef struct {
     int32_t warp_to_start;  /* 0: events warped to the window's end (Eq. 11, the paper's  */
                             /*    reference time tau); 1: to its start (reference time 0: */
                             /*    x' = FOE + (x - FOE)(1 - D t), linear in D)             */
+    int32_t polarity;       /* 0: polarity unused (the paper's objective); 1: one image   */
+                            /*    per polarity, contrasts added (H <= 2048; every        */
+                            /*    dd_events must then carry p)                            */
 } dd_config;
 
 /* One window of events in structure-of-arrays form. */
@@ -88,6 +101,9 @@ typedef struct {
     float t0;               /* window start                                        */
     float tau;              /* window length, > 0                                  */
     int32_t device_ptrs;    /* 0: host arrays (copied in); 1: device arrays        */
+    const int8_t* p;        /* [n] polarity (same memory as x/y/t): read only by a */
+                            /* context with polarity = 1, which requires it;       */
+                            /* NULL otherwise                                      */
 } dd_events;
 
 /* Result of one exact solve (Algorithm 1). */
@@ -161,7 +177,8 @@ int dd_set_stream(dd_ctx* ctx, void* stream);
 
 /* Eqs. 11-13: the contrast key at each of nD hypotheses D[j] (host array).
  * Writes K[j] (required) and, where non-NULL, S[j], N_in[j], and the IWE of
- * every hypothesis to iwe[j*M + y*W + x] (host, nD*M uint32).
+ * every hypothesis to iwe[j*M + y*W + x] (host, nD*M uint32; with polarity
+ * planes iwe[(2 j + plane) M + y W + x], 2 nD M uint32).
  * Errors: DD_ERR_ARG (bad events, D outside the domain, nD < 0), DD_ERR_OOM,
  * DD_ERR_CUDA. */
 int dd_contrast(dd_ctx* ctx, const dd_events* ev, const float* D, int32_t nD, dd_i128* K,
@@ -431,7 +448,7 @@ double dd_serve_clock(void);
  * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
  * DD_ERR_CUDA. */
 #define DD_NOALLOC_MAX_EVENTS (1 << 20)
-#define DD_NOALLOC_SCRATCH_BYTES 25223680
+#define DD_NOALLOC_SCRATCH_BYTES 25224704
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,
                         int32_t nD, dd_i128* K, void* stream);
 

@@ -50,12 +50,13 @@ class dd_i128(ctypes.Structure):
 class dd_config(ctypes.Structure):
     _fields_ = [("pop_k", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("band_rows", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("max_splits", ctypes.c_int32), ("warp_to_start", ctypes.c_int32)]
+                ("max_splits", ctypes.c_int32), ("warp_to_start", ctypes.c_int32), ("polarity", ctypes.c_int32)]
 
 
 class dd_events(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t", ctypes.c_void_p), ("n", ctypes.c_int64),
-                ("t0", ctypes.c_float), ("tau", ctypes.c_float), ("device_ptrs", ctypes.c_int32)]
+                ("t0", ctypes.c_float), ("tau", ctypes.c_float), ("device_ptrs", ctypes.c_int32),
+                ("p", ctypes.c_void_p)]
 
 
 class dd_result(ctypes.Structure):
@@ -232,32 +233,41 @@ class Events:
 
     Holds references to the arrays so they outlive the call."""
 
-    def __init__(self, x, y, t, t0, tau):
+    def __init__(self, x, y, t, t0, tau, p=None):
+        """p: int8 polarities (same kind of memory as x/y/t), read by a
+        context with polarity=1; None otherwise."""
         dev = hasattr(x, "is_cuda") and x.is_cuda
         if dev:
             import torch
             assert x.dtype == torch.int16 and y.dtype == torch.int16 and t.dtype == torch.float32
             assert x.is_contiguous() and y.is_contiguous() and t.is_contiguous()
+            assert p is None or (p.is_cuda and p.dtype == torch.int8 and p.is_contiguous())
         else:
             x = np.ascontiguousarray(x, dtype=np.int16)
             y = np.ascontiguousarray(y, dtype=np.int16)
             t = np.ascontiguousarray(t, dtype=np.float32)
-        self.x, self.y, self.t = x, y, t
+            p = None if p is None else np.ascontiguousarray(p, dtype=np.int8)
+        self.x, self.y, self.t, self.p = x, y, t, p
         n = int(x.shape[0])
         self.c = dd_events(_ptr(x) if n else None, _ptr(y) if n else None, _ptr(t) if n else None, n,
-                           float(t0), float(tau), 1 if dev else 0)
+                           float(t0), float(tau), 1 if dev else 0, _ptr(p) if (n and p is not None) else None)
 
     @classmethod
-    def of(cls, w, device=None):
+    def of(cls, w, device=None, polarity=False):
         """From a synth.Window (numpy arrays, or torch CUDA tensors already on the
-        device); device='cuda' uploads numpy arrays as torch tensors."""
+        device); device='cuda' uploads numpy arrays as torch tensors;
+        polarity=True passes the window's polarities."""
+        p = w.p if polarity else None
+        if polarity and p is None:
+            raise ValueError("the window has no polarities")
         if hasattr(w.x, "is_cuda") and w.x.is_cuda:
-            return cls(w.x, w.y, w.t, w.t0, w.tau)
+            return cls(w.x, w.y, w.t, w.t0, w.tau, p)
         if device is None:
-            return cls(w.x, w.y, w.t, w.t0, w.tau)
+            return cls(w.x, w.y, w.t, w.t0, w.tau, p)
         import torch
         return cls(torch.from_numpy(w.x).to(device), torch.from_numpy(w.y).to(device),
-                   torch.from_numpy(w.t).to(device), w.t0, w.tau)
+                   torch.from_numpy(w.t).to(device), w.t0, w.tau,
+                   None if p is None else torch.from_numpy(p).to(device))
 
 
 def dd_contrast(h, ev, D, want=("S", "N"), want_iwe=False, M=None):
@@ -528,15 +538,21 @@ class Context:
     """A dd_ctx for one frame geometry (W x H, FOE)."""
 
     def __init__(self, W, H, foe_x, foe_y, pop_k=0, queue_capacity=0, band_rows=0, threads=0, max_rounds=0,
-                 host_loop=0, max_splits=0, warp_to_start=0):
+                 host_loop=0, max_splits=0, warp_to_start=0, polarity=0):
         self.W, self.H = int(W), int(H)
+        self.planes = 2 if polarity else 1
         self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds, host_loop, max_splits,
-                             warp_to_start)
+                             warp_to_start, polarity)
         self.h = dd_create(self.W, self.H, float(foe_x), float(foe_y), self.cfg)
 
     @property
     def M(self):
-        return self.W * self.H
+        """Image cells of one hypothesis (both planes with polarity)."""
+        return self.planes * self.W * self.H
+
+    def _image(self, img):
+        shape = (-1, self.H, self.W) if self.planes == 1 else (-1, 2, self.H, self.W)
+        return img.reshape(shape)
 
     @classmethod
     def tuned(cls, W, H, foe_x, foe_y, n_events, mode="single", **kw):
@@ -572,11 +588,11 @@ class Context:
 
     def contrast(self, ev, D, want_iwe=False):
         K, S, N, img = dd_contrast(self.h, ev, D, want_iwe=want_iwe, M=self.M)
-        return K, S, N, (img.reshape(-1, self.H, self.W) if want_iwe else None)
+        return K, S, N, (self._image(img) if want_iwe else None)
 
     def bound(self, ev, D_lo, D_hi, want_iwe=False):
         K, S, N, img = dd_bound(self.h, ev, D_lo, D_hi, want_iwe=want_iwe, M=self.M)
-        return K, S, N, (img.reshape(-1, self.H, self.W) if want_iwe else None)
+        return K, S, N, (self._image(img) if want_iwe else None)
 
     def solve_batch(self, evs, params=None):
         """Solve several windows at once; params defaults to [-1, 1], 1e-4, 0."""

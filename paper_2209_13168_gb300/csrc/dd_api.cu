@@ -26,6 +26,7 @@ struct dd_ctx {
     int64_t ev_cap = 0;
     int16_t *in_x = nullptr, *in_y = nullptr;   // staging of host-array inputs
     float* in_t = nullptr;
+    int8_t* in_p = nullptr;
     int64_t in_cap = 0;
 
     // per-window buffers, sized for win_cap windows
@@ -111,10 +112,12 @@ bool d_ok(float D, float tau) {
 // Host checks of a window descriptor.  Event contents (coordinates in the
 // frame, times in the window) are checked by the ingest kernels, which flag
 // the window; the call then fails with DD_ERR_ARG.
-int check_events(const dd_events* ev) {
+// With two polarity planes the events must carry their polarities.
+int check_events(const dd_events* ev, int32_t planes) {
     if (!ev || ev->n < 0 || ev->n > INT32_MAX / 2) return DD_ERR_ARG;
     if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
     if (ev->n > 0 && (!ev->x || !ev->y || !ev->t)) return DD_ERR_ARG;
+    if (planes > 1 && ev->n > 0 && !ev->p) return DD_ERR_ARG;
     return DD_OK;
 }
 
@@ -204,7 +207,7 @@ int ensure_windows(dd_ctx* c, int nw) {
     if (nw <= c->win_cap) return DD_OK;
     drop_graph(c);
     const int cap = nw < 8 ? 8 : nw + nw / 2;
-    const int bins = c->g.n_tb * c->g.H;
+    const int bins = dd::bins_of(c->g);
     release(c->row_count);
     release(c->row_off);
     release(c->cursor);
@@ -251,6 +254,24 @@ int ensure_windows(dd_ctx* c, int nw) {
     return DD_OK;
 }
 
+// Staging buffers for n host-array events (with polarities when the context
+// has two planes).
+int ensure_staging(dd_ctx* c, int64_t n) {
+    if (n <= c->in_cap) return DD_OK;
+    release(c->in_x);
+    release(c->in_y);
+    release(c->in_t);
+    release(c->in_p);
+    c->in_cap = 0;
+    const int64_t nc = n + n / 4;
+    DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
+    DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
+    DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
+    if (c->g.planes > 1) DD_TRY(cudaMalloc((void**)&c->in_p, sizeof(int8_t) * nc));
+    c->in_cap = nc;
+    return DD_OK;
+}
+
 // Upload (host arrays) or alias (device arrays) the events of nw windows,
 // then sort each window's events by (time bucket, row).  Sets err[w] on
 // malformed events of window w.
@@ -273,17 +294,8 @@ int ingest(dd_ctx* c, const dd_events* evs, int nw) {
         DD_TRY(cudaMalloc((void**)&c->rcp, sizeof(float2) * nc));
         c->ev_cap = nc;
     }
-    if (host_total > c->in_cap) {
-        release(c->in_x);
-        release(c->in_y);
-        release(c->in_t);
-        c->in_cap = 0;
-        const int64_t nc = host_total + host_total / 4;
-        DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
-        DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
-        DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
-        c->in_cap = nc;
-    }
+    rc = ensure_staging(c, host_total);
+    if (rc) return rc;
     if (chunks > c->chunk_cap) {
         release(c->chunk_win);
         release_host(c->h_chunks);
@@ -301,6 +313,7 @@ int ingest(dd_ctx* c, const dd_events* evs, int nw) {
         wi.x = e.x;
         wi.y = e.y;
         wi.t = e.t;
+        wi.p = c->g.planes > 1 ? e.p : nullptr;
         if (!e.device_ptrs && e.n > 0) {
             DD_TRY(copy(c, c->in_x + hoff, e.x, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice));
             DD_TRY(copy(c, c->in_y + hoff, e.y, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice));
@@ -308,6 +321,10 @@ int ingest(dd_ctx* c, const dd_events* evs, int nw) {
             wi.x = c->in_x + hoff;
             wi.y = c->in_y + hoff;
             wi.t = c->in_t + hoff;
+            if (c->g.planes > 1) {
+                DD_TRY(copy(c, c->in_p + hoff, e.p, sizeof(int8_t) * e.n, cudaMemcpyHostToDevice));
+                wi.p = c->in_p + hoff;
+            }
             hoff += e.n;
         }
         wi.n = e.n;
@@ -341,7 +358,7 @@ dd_i128 from_i128(i128 v) {
 // images to the host.
 int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float* A, const float* B, dd_i128* K,
                uint64_t* S, int64_t* N, uint32_t* iwe) {
-    const int64_t M = (int64_t)c->g.W * c->g.H;
+    const int64_t M = (int64_t)c->g.planes * c->g.W * c->g.H;     // image cells of one task
     for (int32_t j0 = 0; j0 < n; j0 += c->max_tasks) {
         const int32_t m = n - j0 < c->max_tasks ? n - j0 : c->max_tasks;
         int32_t nj = 0;
@@ -496,7 +513,7 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
                dd_node_rec* trace, int64_t trace_cap, int64_t* trace_len) {
     if (!c || !out || !evs || !prm || nw < 1) return DD_ERR_ARG;
     for (int w = 0; w < nw; w++) {
-        int rc = check_events(&evs[w]);
+        int rc = check_events(&evs[w], c->g.planes);
         if (rc) return rc;
         rc = check_params(c, prm[w], evs[w].tau);
         if (rc) return rc;
@@ -632,6 +649,7 @@ void dd_destroy(dd_ctx* c) {
     release(c->in_x);
     release(c->in_y);
     release(c->in_t);
+    release(c->in_p);
     release(c->row_count);
     release(c->row_off);
     release(c->cursor);
@@ -681,6 +699,8 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     if (k.threads && (k.threads % 32 || k.threads > 512)) return DD_ERR_ARG;
     if (k.max_splits < 0 || k.max_splits > 64 || k.host_loop < 0) return DD_ERR_ARG;
     if (k.warp_to_start != 0 && k.warp_to_start != 1) return DD_ERR_ARG;
+    if (k.polarity != 0 && k.polarity != 1) return DD_ERR_ARG;
+    if (k.polarity && H > 2048) return DD_ERR_ARG;          // the event sort has 4096 bins
     if (!k.pop_k) k.pop_k = 1;
     if (!k.queue_capacity) k.queue_capacity = 8192;
     if (!k.max_rounds) k.max_rounds = 1 << 20;
@@ -710,8 +730,10 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
         return DD_ERR_ARG;
     }
     c->g.band_rows = rows;
-    c->g.n_tiles = (H + rows - 1) / rows;
-    c->g.n_tb = dd::time_buckets(H);
+    c->g.planes = k.polarity ? 2 : 1;
+    c->g.plane_tiles = (H + rows - 1) / rows;
+    c->g.n_tiles = c->g.planes * c->g.plane_tiles;
+    c->g.n_tb = dd::time_buckets(c->g.planes * H);
     c->g.max_splits = k.max_splits ? k.max_splits : 16;
     c->g.ref0 = k.warp_to_start ? 1 : 0;
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
@@ -723,7 +745,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     auto A = [&](void** p, size_t bytes) {
         if (rc == DD_OK && cudaMalloc(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
     };
-    const size_t M = (size_t)W * H;
+    const size_t M = (size_t)c->g.planes * W * H;      // image cells of one task
     A((void**)&c->sch, sizeof(dd::Sched));
     A((void**)&c->macc, sizeof(uint32_t) * (size_t)c->max_tasks * M);
     A((void**)&c->mdone, sizeof(int32_t) * (size_t)c->max_tasks * c->g.n_tiles);
@@ -784,7 +806,7 @@ int dd_set_timing(dd_ctx* c, int32_t enable) {
 int dd_contrast(dd_ctx* c, const dd_events* ev, const float* D, int32_t nD, dd_i128* K, uint64_t* S,
                 int64_t* N_in, uint32_t* iwe) {
     if (!c || nD < 0 || (nD > 0 && (!D || !K))) return DD_ERR_ARG;
-    int rc = check_events(ev);
+    int rc = check_events(ev, c->g.planes);
     if (rc) return rc;
     for (int32_t j = 0; j < nD; j++)
         if (!d_ok(D[j], ev->tau)) return DD_ERR_ARG;
@@ -801,7 +823,7 @@ int dd_contrast(dd_ctx* c, const dd_events* ev, const float* D, int32_t nD, dd_i
 int dd_bound(dd_ctx* c, const dd_events* ev, const float* D_lo, const float* D_hi, int32_t n, dd_i128* Kbar,
              uint64_t* Sbar, int64_t* N_full, uint32_t* iwe) {
     if (!c || n < 0 || (n > 0 && (!D_lo || !D_hi || !Kbar))) return DD_ERR_ARG;
-    int rc = check_events(ev);
+    int rc = check_events(ev, c->g.planes);
     if (rc) return rc;
     for (int32_t j = 0; j < n; j++)
         if (!d_ok(D_lo[j], ev->tau) || !d_ok(D_hi[j], ev->tau) || !(D_lo[j] <= D_hi[j])) return DD_ERR_ARG;
@@ -839,7 +861,7 @@ int dd_solve_window(dd_ctx* c, const dd_events* ev, const dd_window_params* p, d
 int dd_features(dd_ctx* c, const dd_events* windows, int32_t n_windows, float* feat) {
     if (!c || !windows || n_windows < 1 || !feat) return DD_ERR_ARG;
     for (int w = 0; w < n_windows; w++) {
-        const int rc = check_events(&windows[w]);
+        const int rc = check_events(&windows[w], c->g.planes);
         if (rc) return rc;
     }
     int rc = ingest(c, windows, n_windows);
@@ -860,24 +882,15 @@ int dd_resample(dd_ctx* c, const dd_events* in, int32_t W, int32_t H, int32_t W2
     if (!c || !n_out || W < 1 || H < 1 || W > 4096 || H > 4096 || W2 < 1 || H2 < 1 || W2 > 4096 || H2 > 4096)
         return DD_ERR_ARG;
     if (!std::isfinite(keep) || !(keep >= 0.0f) || !(keep <= 1.0f)) return DD_ERR_ARG;
-    int rc = check_events(in);
+    int rc = check_events(in, 1);                  // polarities are not carried over
     if (rc) return rc;
     if (in->n > 0 && (!x_out || !y_out || !t_out)) return DD_ERR_ARG;
     const int16_t* x = in->x;
     const int16_t* y = in->y;
     const float* t = in->t;
     if (!in->device_ptrs && in->n > 0) {          // host arrays: through the context's staging buffers
-        if (in->n > c->in_cap) {
-            release(c->in_x);
-            release(c->in_y);
-            release(c->in_t);
-            c->in_cap = 0;
-            const int64_t nc = in->n + in->n / 4;
-            DD_TRY(cudaMalloc((void**)&c->in_x, sizeof(int16_t) * nc));
-            DD_TRY(cudaMalloc((void**)&c->in_y, sizeof(int16_t) * nc));
-            DD_TRY(cudaMalloc((void**)&c->in_t, sizeof(float) * nc));
-            c->in_cap = nc;
-        }
+        rc = ensure_staging(c, in->n);
+        if (rc) return rc;
         DD_TRY(copy(c, c->in_x, in->x, sizeof(int16_t) * in->n, cudaMemcpyHostToDevice));
         DD_TRY(copy(c, c->in_y, in->y, sizeof(int16_t) * in->n, cudaMemcpyHostToDevice));
         DD_TRY(copy(c, c->in_t, in->t, sizeof(float) * in->n, cudaMemcpyHostToDevice));
@@ -960,6 +973,7 @@ int dd_stream_solve(dd_ctx* c, const dd_events* stream, double t_start, float ta
         e.x = stream->x + f[k];
         e.y = stream->y + f[k];
         e.t = stream->t + f[k];
+        e.p = stream->p ? stream->p + f[k] : nullptr;
         e.n = cnt[k];
         e.t0 = t0[k];
         e.tau = tau;

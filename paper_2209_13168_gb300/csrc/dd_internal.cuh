@@ -36,12 +36,20 @@ struct Job {
     int32_t win, task, split, splits;
 };
 
-// Sums of one task's IWE: per task, over all its row bands.
+// Sums of one task's IWE: per task, over all its row bands; counts per
+// polarity plane (plane 1 stays zero without polarity).
 struct Partial {
-    unsigned long long S;      // sum of squared counts
-    unsigned long long cells;  // sum of counts (N_in for a point, increments for a bound)
-    unsigned long long full;   // events whose bound segment lies in the frame
+    unsigned long long S;         // sum of squared counts, both planes
+    unsigned long long cells[2];  // sum of counts (N_in for a point, increments for a bound)
+    unsigned long long full[2];   // events whose bound segment lies in the frame
 };
+
+// Eq. (13) / Eq. (14) in integer form, summed over the polarity planes:
+// K = M S - sum_p N_p^2 with N = N_in for a point and N = N_full for a bound.
+__host__ __device__ inline i128 partial_key(int64_t M, const Partial& q, bool point) {
+    const unsigned long long a = point ? q.cells[0] : q.full[0], b = point ? q.cells[1] : q.full[1];
+    return (i128)M * (i128)q.S - (i128)a * (i128)a - (i128)b * (i128)b;
+}
 
 struct __align__(16) Node {
     float lo, hi;
@@ -111,6 +119,7 @@ struct WinIn {
     const int16_t* x;
     const int16_t* y;
     const float* t;
+    const int8_t* p;       // polarities (read only with two polarity planes)
     int64_t n, ev_off;     // event count; offset in the sorted event buffers
     float t0, tau;
     int32_t chunk0, pad;   // first ingest chunk of the window
@@ -128,15 +137,22 @@ struct Sched {
     int32_t ticket, active, running;
 };
 
-// Geometry of a context.  Events are sorted by (time bucket, row): n_tb
-// buckets of equal length over [0, tau], n_tb * H <= 4096 bins, n_tb <= 8.
+// Geometry of a context.  Events are sorted by (polarity plane, time
+// bucket, row): n_tb buckets of equal length over [0, tau], planes * n_tb *
+// H <= 4096 bins, n_tb <= 8.  A job's units are its row bands, plane 0's
+// first: n_tiles = planes * plane_tiles.
 struct Geom {
     int32_t W, H;
     float fx, fy;
     int32_t band_rows, n_tiles, n_tb, max_splits;
     int32_t split_target;   // units a round needs before its bounds stop splitting (0: no cap)
     int32_t ref0;           // 1: the warp maps events to the window's start (t_ref = 0), not its end
+    int32_t planes;         // 1: polarity unused; 2: one image per polarity (p > 0, p <= 0)
+    int32_t plane_tiles;    // row bands of one plane
 };
+
+// Bins of one window's event sort.
+__host__ __device__ inline int32_t bins_of(const Geom& g) { return g.planes * g.n_tb * g.H; }
 
 // The warp's reference time for a window of length tau.
 __host__ __device__ inline float warp_tref(const Geom& g, float tau) { return g.ref0 ? 0.0f : tau; }
@@ -167,7 +183,8 @@ __host__ __device__ inline int32_t bound_splits(const Geom& g, float D_lo, float
     return s < 1 ? 1 : (s > g.max_splits ? g.max_splits : s);
 }
 
-// Time buckets for a frame of H rows: as many as fit 4096 bins, at most 8.
+// Time buckets for a sort over H rows (rows of every plane): as many as fit
+// 4096 bins, at most 8.
 inline int32_t time_buckets(int32_t H) {
     int32_t b = 4096 / H;
     return b < 1 ? 1 : (b > 8 ? 8 : b);
@@ -175,7 +192,7 @@ inline int32_t time_buckets(int32_t H) {
 
 // Merge buffers of split jobs (single-window searches only).
 struct Merge {
-    uint32_t* acc;                 // [task][M] counts, zero between uses
+    uint32_t* acc;                 // [task][planes * M] counts, zero between uses
     int32_t* done;                 // [task][tile] finished splits, zero between uses
     Partial* sums;                 // [task][tile] sums of the splits, zero between uses
 };
@@ -184,7 +201,7 @@ struct Merge {
 struct EvalArgs {
     const Ev* ev;
     const float2* rcp;
-    const int32_t* row_off;        // per window: n_tb * H + 1 entries
+    const int32_t* row_off;        // per window: bins_of(g) + 1 entries
     const WinIn* wins;
     const Task* tasks;             // per window: task_stride entries
     int32_t task_stride;
@@ -194,7 +211,7 @@ struct EvalArgs {
     Partial* part;                 // [win * task_stride + task]: the task's sums over its row
                                    // bands, accumulated by atomics; zero before the evaluation,
                                    // cleared by their reader
-    uint32_t* iwe_out;             // nullable: [task][M] (single window)
+    uint32_t* iwe_out;             // nullable: [task][planes * M] (single window)
     Merge mg;
 };
 

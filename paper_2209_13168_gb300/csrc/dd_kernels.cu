@@ -68,12 +68,17 @@ __device__ __forceinline__ bool event_ok(int xi, int yi, float ti, float tr, flo
     return isfinite(ti) && tr >= 0.0f && tr <= tau && xi >= 0 && xi < W && yi >= 0 && yi < H;
 }
 
-// Sort key of an event: (time bucket, row).  Bucket b holds the events with
-// t*scale in [b, b+1) (binary32 product), scale = n_tb/tau.
-__device__ __forceinline__ int event_key(const Geom& g, int yi, float tr, float bscale) {
+// Sort key of an event: (polarity plane, time bucket, row).  Bucket b holds
+// the events with t*scale in [b, b+1) (binary32 product), scale = n_tb/tau.
+__device__ __forceinline__ int event_key(const Geom& g, int yi, float tr, float bscale, int plane) {
     int b = __float2int_rd(__fmul_rn(tr, bscale));
     b = min(max(b, 0), g.n_tb - 1);
-    return b * g.H + yi;
+    return (plane * g.n_tb + b) * g.H + yi;
+}
+
+// Plane of event i: 1 for polarity p <= 0 when the planes are split.
+__device__ __forceinline__ int plane_of(const Geom& g, const WinIn& win, int64_t i) {
+    return g.planes > 1 && win.p[i] <= 0 ? 1 : 0;
 }
 
 // Block c counts chunk c of its window into a shared histogram of the
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const WinIn
     __shared__ int32_t h[MAX_BINS];
     const int w = chunk_win[blockIdx.x];
     const WinIn win = wins[w];
-    const int bins = g.n_tb * g.H;
+    const int bins = bins_of(g);
     const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
     for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const WinIn
         const float ti = win.t[i];
         const float tr = __fsub_rn(ti, win.t0);
         if (!event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) { bad = 1; continue; }
-        atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
+        atomicAdd(&h[event_key(g, yi, tr, bscale, plane_of(g, win, i))], 1);
     }
     if (bad) atomicOr(&err[w], 1);
     __syncthreads();
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
     __shared__ int32_t base[MAX_BINS];
     const int w = chunk_win[blockIdx.x];
     const WinIn win = wins[w];
-    const int bins = g.n_tb * g.H;
+    const int bins = bins_of(g);
     const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
     const int64_t i0 = (int64_t)(blockIdx.x - win.chunk0) * CHUNK, i1 = min(win.n, i0 + CHUNK);
     int32_t* cur = cursor + (size_t)w * bins;
@@ -171,7 +176,8 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
         const int xi = win.x[i], yi = win.y[i];
         const float ti = win.t[i];
         const float tr = __fsub_rn(ti, win.t0);
-        if (event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) atomicAdd(&h[event_key(g, yi, tr, bscale)], 1);
+        if (event_ok(xi, yi, ti, tr, win.tau, g.W, g.H))
+            atomicAdd(&h[event_key(g, yi, tr, bscale, plane_of(g, win, i))], 1);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < bins; r += blockDim.x) {
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
         const float ti = win.t[i];
         const float tr = __fsub_rn(ti, win.t0);
         if (!event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) continue;
-        const int key = event_key(g, yi, tr, bscale);
+        const int key = event_key(g, yi, tr, bscale, plane_of(g, win, i));
         const int pos = base[key] + atomicAdd(&h[key], 1);
         Ev e;
         e.dx = __fsub_rn((float)xi, g.fx);
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
 cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_windows, const int32_t* chunk_win_dev,
                           int32_t n_chunks, Ev* out, float2* rcp, int32_t* row_count, int32_t* row_off,
                           int32_t* cursor, int32_t* err, cudaStream_t s) {
-    const int bins = g.n_tb * g.H;
+    const int bins = bins_of(g);
     if (n_windows <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(row_count, 0, sizeof(int32_t) * bins * (size_t)n_windows, s);
     if (e != cudaSuccess) return e;
@@ -568,7 +574,12 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
                                           int* erange, int* s_last, SegQueue& queue) {
-    const int y0 = ti * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
+    // Unit ti is row band `band` of polarity plane `plane`: the plane's own
+    // run of sorted events, its own image and its own counts.
+    const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
+    const int y0 = band * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
+    const int32_t* row_off = p.row_off + (size_t)plane * g.n_tb * g.H;
+    const size_t plane_off = (size_t)plane * g.W * g.H;
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
@@ -577,7 +588,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     if (threadIdx.x < 32) {
         int e0 = 0, e1 = 0;
         if (lane < g.n_tb)
-            bucket_event_range(g, p.row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
+            bucket_event_range(g, row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
                                e1);
         const int len = e1 - e0, incl = warp_incl_scan(len);
         if (lane < g.n_tb) {
@@ -620,7 +631,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     }
     __syncthreads();
 
-    uint32_t* out = p.out ? p.out + (size_t)y0 * W : nullptr;
+    uint32_t* out = p.out ? p.out + plane_off + (size_t)y0 * W : nullptr;
     unsigned long long Cl = C;
     // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
     // take columns.
@@ -663,7 +674,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             }
         }
     } else {
-        uint32_t* acc = p.acc + (size_t)y0 * W;
+        uint32_t* acc = p.acc + plane_off + (size_t)y0 * W;
         // Splits of one band finish together: each starts its pass at its own
         // row so that they add into different words at a time.
         const int rot = (int)((long long)rows * split / splits);
@@ -698,8 +709,8 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 f += red[2][w];
             }
             atomicAdd(&p.sums[ti].S, a);
-            atomicAdd(&p.sums[ti].cells, b);
-            if (f) atomicAdd(&p.sums[ti].full, f);
+            atomicAdd(&p.sums[ti].cells[0], b);
+            if (f) atomicAdd(&p.sums[ti].full[0], f);
             __threadfence();
             *s_last = atomicAdd(&p.done[ti], 1) == splits - 1;
         }
@@ -712,12 +723,12 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         }
         if (threadIdx.x == 0) {
             const unsigned long long qS = atomicExch(&p.sums[ti].S, 0ull);
-            const unsigned long long qC = atomicExch(&p.sums[ti].cells, 0ull);
-            const unsigned long long qF = atomicExch(&p.sums[ti].full, 0ull);
+            const unsigned long long qC = atomicExch(&p.sums[ti].cells[0], 0ull);
+            const unsigned long long qF = atomicExch(&p.sums[ti].full[0], 0ull);
             p.done[ti] = 0;
             if (qS) atomicAdd(&p.part->S, qS);
-            if (qC) atomicAdd(&p.part->cells, qC);
-            if (qF) atomicAdd(&p.part->full, qF);
+            if (qC) atomicAdd(&p.part->cells[plane], qC);
+            if (qF) atomicAdd(&p.part->full[plane], qF);
         }
         return;
     }
@@ -727,8 +738,8 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     full = warp_sum(full);
     if (lane == 0) {
         if (S) atomicAdd(&p.part->S, S);
-        if (C64) atomicAdd(&p.part->cells, C64);
-        if (full) atomicAdd(&p.part->full, full);
+        if (C64) atomicAdd(&p.part->cells[plane], C64);
+        if (full) atomicAdd(&p.part->full[plane], full);
     }
 }
 
@@ -752,7 +763,8 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     int32_t* work = &sch->work[par];
     const Job* jobs = a.jobs + (size_t)par * a.job_stride;
     const int tile_words = g.band_rows * tile_pitch(g);
-    const int bins1 = g.n_tb * g.H + 1;
+    const int bins1 = bins_of(g) + 1;
+    const size_t task_cells = (size_t)g.planes * g.W * g.H;
     // Block b starts with unit b; later units come from the counter, which
     // numbers them from gridDim.x on.
     if (threadIdx.x == 0) s_unit = blockIdx.x;
@@ -773,8 +785,8 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         p.rcp = a.rcp + ev_off;
         p.row_off = a.row_off + (size_t)jb.win * bins1;
         p.part = a.part + ((size_t)jb.win * a.task_stride + jb.task);
-        p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * g.W * g.H : nullptr;
-        p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * g.W * g.H : nullptr;
+        p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * task_cells : nullptr;
+        p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * task_cells : nullptr;
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
         p.sums = a.mg.sums ? a.mg.sums + (size_t)jb.task * g.n_tiles : nullptr;
         eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last, queue);
@@ -800,23 +812,17 @@ cudaError_t launch_eval(const Geom& g, const EvalArgs& a, int threads, int grid_
 
 // ------------------------------------------------------------------- keys
 
-// Eq. (13) / Eq. (14) in integer form: K = M*S - N^2 with N = N_in for a
-// point and N = N_full for a bound.
-__device__ __forceinline__ i128 key_of(int64_t M, unsigned long long S, unsigned long long N) {
-    return (i128)M * (i128)S - (i128)N * (i128)N;
-}
-
 __global__ void k_keys(Geom g, const Task* tasks, int32_t n_tasks, Partial* part, i128* key,
                        unsigned long long* S_out, unsigned long long* C_out, unsigned long long* F_out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tasks) return;
     const Partial p = part[t];
-    part[t] = Partial{0, 0, 0};                   // cleared for the next evaluation
+    part[t] = Partial{};                          // cleared for the next evaluation
     const int64_t M = (int64_t)g.W * g.H;
-    key[t] = key_of(M, p.S, tasks[t].kind == TASK_POINT ? p.cells : p.full);
+    key[t] = partial_key(M, p, tasks[t].kind == TASK_POINT);
     S_out[t] = p.S;
-    C_out[t] = p.cells;
-    F_out[t] = p.full;
+    C_out[t] = p.cells[0] + p.cells[1];
+    F_out[t] = p.full[0] + p.full[1];
 }
 
 cudaError_t launch_keys(const Geom& g, const Task* tasks, int32_t n_tasks, Partial* part, i128* key,
@@ -841,7 +847,7 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
                        int64_t max_rounds, int32_t trace_cap) {
     const int w = w0 + blockIdx.x;
     for (int i = threadIdx.x; i < task_stride; i += blockDim.x)   // the window's task sums start at zero
-        part_all[(size_t)w * task_stride + i] = Partial{0, 0, 0};
+        part_all[(size_t)w * task_stride + i] = Partial{};
     if (threadIdx.x != 0) return;
     const int par = sch->round & 1;
     Job* jobs = jobs_all + (size_t)par * job_stride;
@@ -1021,9 +1027,9 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     // read and cleared for the next round.
     for (int t = tid; t < n_tasks; t += blockDim.x) {
         const Partial q = part[t];
-        part[t] = Partial{0, 0, 0};
-        key[t] = key_of(M, q.S, tasks[t].kind == TASK_POINT ? q.cells : q.full);
-        cells[t] = q.cells;
+        part[t] = Partial{};
+        key[t] = partial_key(M, q, tasks[t].kind == TASK_POINT);
+        cells[t] = q.cells[0] + q.cells[1];
     }
     __syncthreads();
 

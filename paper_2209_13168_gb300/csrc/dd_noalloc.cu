@@ -37,7 +37,7 @@ constexpr size_t OFF_C = align256(OFF_S + sizeof(unsigned long long) * NA_MAX_TA
 constexpr size_t OFF_F = align256(OFF_C + sizeof(unsigned long long) * NA_MAX_TASKS);
 constexpr size_t SCRATCH_BYTES = align256(OFF_F + sizeof(unsigned long long) * NA_MAX_TASKS);
 static_assert(SCRATCH_BYTES == DD_NOALLOC_SCRATCH_BYTES, "dd.h states the static scratch size");
-static_assert(sizeof(dd::Partial) == 24 && sizeof(dd::Task) == 16 && sizeof(dd::Ev) == 16, "layout");
+static_assert(sizeof(dd::Partial) == 40 && sizeof(dd::Task) == 16 && sizeof(dd::Ev) == 16, "layout");
 
 // The scratch itself.  In host code `g_scratch` is only a stand-in symbol:
 // its device address comes from cudaGetSymbolAddress, once per device.
@@ -106,6 +106,8 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     g.max_splits = 1;
     g.split_target = 0;
     g.ref0 = 0;
+    g.planes = 1;                                 // polarity unused (Eq. 12 as the paper writes it)
+    g.plane_tiles = g.n_tiles;
     if (g.n_tiles > NA_MAX_TILES) return DD_ERR_CAPACITY;
     if (dd::eval_smem_setup(g) != cudaSuccess) return DD_ERR_CUDA;
 
@@ -134,6 +136,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     h_win.x = ev->x;
     h_win.y = ev->y;
     h_win.t = ev->t;
+    h_win.p = nullptr;
     h_win.n = ev->n;
     h_win.ev_off = 0;
     h_win.t0 = ev->t0;

@@ -61,6 +61,7 @@ struct dd_server {
     float2* rcp = nullptr;
     int16_t *in_x = nullptr, *in_y = nullptr;
     float* in_t = nullptr;
+    int8_t* in_p = nullptr;       // polarities (two planes only)
     int32_t *row_count = nullptr, *row_off = nullptr, *cursor = nullptr, *err = nullptr, *phase = nullptr;
     int32_t* chunk_zero = nullptr;
     dd::WinIn* wins = nullptr;
@@ -116,6 +117,7 @@ void free_server(dd_server* s) {
     release(s->in_x);
     release(s->in_y);
     release(s->in_t);
+    release(s->in_p);
     release(s->row_count);
     release(s->row_off);
     release(s->cursor);
@@ -140,7 +142,8 @@ void free_server(dd_server* s) {
 }
 
 size_t slot_bytes(const dd_server* s) {
-    return (size_t)s->E * (sizeof(dd::Ev) + sizeof(float2) + 2 * sizeof(int16_t) + sizeof(float)) +
+    return (size_t)s->E * (sizeof(dd::Ev) + sizeof(float2) + 2 * sizeof(int16_t) + sizeof(float) +
+                           (s->g.planes > 1 ? sizeof(int8_t) : 0)) +
            sizeof(int32_t) * (3 * (size_t)s->bins + 1) + sizeof(dd::SolveState) +
            sizeof(dd::Node) * 2 * (size_t)s->qcap + sizeof(dd::Task) * (size_t)s->max_tasks +
            sizeof(dd::Partial) * (size_t)s->max_tasks + sizeof(dd::Job) * 2 * (size_t)s->max_tasks;
@@ -160,6 +163,7 @@ int alloc_server(dd_server* s) {
     A((void**)&s->in_x, sizeof(int16_t) * S * E);
     A((void**)&s->in_y, sizeof(int16_t) * S * E);
     A((void**)&s->in_t, sizeof(float) * S * E);
+    if (s->g.planes > 1) A((void**)&s->in_p, sizeof(int8_t) * S * E);
     A((void**)&s->row_count, sizeof(int32_t) * S * s->bins);
     A((void**)&s->row_off, sizeof(int32_t) * S * (s->bins + 1));
     A((void**)&s->cursor, sizeof(int32_t) * S * s->bins);
@@ -202,6 +206,7 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
     wi.x = e.x;
     wi.y = e.y;
     wi.t = e.t;
+    wi.p = s->g.planes > 1 ? e.p : nullptr;
     const size_t off = (size_t)k * s->E;
     if (!e.device_ptrs && e.n > 0) {
         cudaError_t c1 = cudaMemcpyAsync(s->in_x + off, e.x, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice, s->stream);
@@ -210,6 +215,12 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
         if (c1 != cudaSuccess) return c1;
         if (c2 != cudaSuccess) return c2;
         if (c3 != cudaSuccess) return c3;
+        if (s->g.planes > 1) {
+            cudaError_t c4 = cudaMemcpyAsync(s->in_p + off, e.p, sizeof(int8_t) * e.n, cudaMemcpyHostToDevice,
+                                             s->stream);
+            if (c4 != cudaSuccess) return c4;
+            wi.p = s->in_p + off;
+        }
         wi.x = s->in_x + off;
         wi.y = s->in_y + off;
         wi.t = s->in_t + off;
@@ -419,7 +430,7 @@ int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server
         s->has_model = dd::mlp_device_view(m, &s->model, &dev);
     }
     s->E = max_events;
-    s->bins = s->g.n_tb * s->g.H;
+    s->bins = dd::bins_of(s->g);
     s->max_chunks = (int)((max_events + dd::CHUNK - 1) / dd::CHUNK);
     if (max_slots == 0) {
         // Slots from free device memory: at most half of it, at most 64.
@@ -466,6 +477,7 @@ int dd_serve_submit(dd_server* s, const dd_events* ev, const dd_window_params* p
                     uint64_t* ticket) {
     if (!s || !ev || !p || !ticket) return DD_ERR_ARG;
     if (ev->n < 0 || (ev->n > 0 && (!ev->x || !ev->y || !ev->t))) return DD_ERR_ARG;
+    if (s->g.planes > 1 && ev->n > 0 && !ev->p) return DD_ERR_ARG;
     if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
     auto d_ok = [&](float D) {
         if (!std::isfinite(D)) return false;

@@ -218,18 +218,20 @@ def stream_slot_spec5(stream, k, n_scale=1.0):
     return (1280, 720, 640.0, 360.0, n_sig, max(1, n_sig // 35), n_noise, D, 0.1, 7_000_000 + 1000 * stream + k), tk
 
 
-def stream_events5(stream, k0, k1, n_scale=1.0):
-    """numpy (x, y, t) of slots k0..k1-1 of descent `stream`, sorted by time."""
-    xs, ys, ts = [], [], []
+def stream_events5(stream, k0, k1, n_scale=1.0, with_polarity=False):
+    """numpy (x, y, t) of slots k0..k1-1 of descent `stream`, sorted by time
+    (and their polarities p as a fourth array with with_polarity=True)."""
+    xs, ys, ts, ps = [], [], [], []
     for k in range(k0, k1):
         spec, tk = stream_slot_spec5(stream, k, n_scale)
         w = make_window(*spec, t0=tk)
         xs.append(w.x)
         ys.append(w.y)
         ts.append(w.t)
-    x, y, t = np.concatenate(xs), np.concatenate(ys), np.concatenate(ts)
+        ps.append(w.p)
+    x, y, t, p = np.concatenate(xs), np.concatenate(ys), np.concatenate(ts), np.concatenate(ps)
     o = np.argsort(t, kind="stable")
-    return x[o], y[o], t[o]
+    return (x[o], y[o], t[o], p[o]) if with_polarity else (x[o], y[o], t[o])
 
 
 def serve_config5(stream, w, n_scale=1.0):
