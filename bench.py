@@ -22,6 +22,7 @@ four concurrent 1280x720 descents ("serving").
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -165,6 +166,50 @@ def oracle_rate(w, budget_s, max_solves):
             return n, el
 
 
+def cpu_model():
+    """The host CPU's name from /proc/cpuinfo (model name, else implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for line in info:
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    return "%s implementer %s part %s" % (platform.machine(), fields.get("CPU implementer", "?"),
+                                          fields.get("CPU part", "?"))
+
+
+def oracle_pool_rate(budget_s):
+    """Oracle solves (Algorithm 1, pop 1) of the uneven 256-window batch on
+    every host core, one window per thread (the oracle's C calls release the
+    GIL), in waves of one window per core until about budget_s has passed."""
+    import concurrent.futures as cf
+    import oracle as O
+    from synth.descent import batch_params3, batch_window3
+    O.build()
+    p = batch_params3()
+    cores = os.cpu_count() or 1
+
+    def one(i):
+        r = O.solve(O.Window.of(batch_window3(i, p)), -1.0, 1.0, 1e-4, 0.0, 1)
+        return r["nodes_expanded"]
+    done, t0 = 0, time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        while done < 256 and time.perf_counter() - t0 < budget_s:
+            wave = list(range(done, min(256, done + cores)))
+            list(ex.map(one, wave))
+            done += len(wave)
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": "windows 0-%d of the 256-window batch (config 3, generated in the worker), Algorithm 1 "
+                      "pop 1, %d threads, %.1f s" % (done - 1, cores, el)}
+
+
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
@@ -218,6 +263,19 @@ def run_extras(dd, torch):
                     "nodes_expanded": sum(r["nodes_expanded"] for r in res),
                     "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}}
     ctx.close()
+    # the same windows through the single-window solver, one call each
+    ctx = dd.Context.tuned(640, 480, 320.0, 240.0, n_mean, mode="single")
+    for e in evs[:8]:
+        ctx.solve(e)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for e in evs:
+        ctx.solve(e)
+    dt_loop = time.perf_counter() - t0
+    out["batch"]["loop_solves_per_s"] = len(ws) / dt_loop
+    out["batch"]["batch_over_loop"] = dt_loop / dt
+    out["batch"]["loop_knobs"] = {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}
+    ctx.close()
     del ws, evs
     # learned warm start vs plain on held-out windows
     from paper_2209_13168_gb300 import warm_start
@@ -242,11 +300,37 @@ def run_extras(dd, torch):
     out["stream"] = stream_mode.evaluate(0)
     out["stream"]["workload"] = ("one continuous 1280x720 descent stream (19 s, D = 1/(20 - t)), windows of 0.2 s "
                                  "every 0.1 s solved in one batched launch; time to contact 1/D_end vs 20 - t_end")
-    # four concurrent descents through the server
+    # four concurrent descents through the server, at 4x real time, then the offered rate swept
     from paper_2209_13168_gb300 import serve_bench
-    out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8)
+    sw = serve_bench.make_windows(4, serve_bench.WINDOWS_PER_STREAM)
+    out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8, windows=sw)
     out["serving"]["workload"] = ("4 descents at 1280x720, 189 windows each (0.2 s every 0.1 s of flight, 50k-833k "
                                   "events), Poisson arrivals at 40 windows/s per stream (4x real time)")
+    out["serving_sweep"] = []
+    for rate in (10.0, 20.0, 80.0, 160.0):
+        r = serve_bench.run(rate_hz=rate, n_streams=4, check=0, windows=sw)
+        out["serving_sweep"].append({k: r[k] for k in ("offered_hz_per_stream", "offered_windows_per_s", "p50_ms",
+                                                       "p99_ms", "max_ms", "throughput_windows_per_s",
+                                                       "events_per_s")})
+    del sw
+    # the 346x260 single-window workload: Algorithm 1 (pop 1) and the tuned pop width
+    from synth import window_config1
+    w1 = window_config1()
+    e1 = dd.Events.of(w1, device="cuda")
+    out["config1"] = {"workload": "346x260, FOE (173, 130), 4,000 events (150 points x 20 + 1,000 noise), "
+                                  "D 0.2, tau 0.5; exact solve, inputs device-resident (64 KB, L2-resident)"}
+    for name, kw in (("pop1", {"pop_k": 1}), ("tuned", {})):
+        ctx = dd.Context.tuned(w1.W, w1.H, w1.foe_x, w1.foe_y, w1.n, **kw)
+        r = ctx.solve(e1)
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = ctx.solve(e1)
+        dt = (time.perf_counter() - t0) / reps
+        out["config1"][name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": dt * 1e3,
+                                "event_warps_per_s": r["event_warps"] / dt, "D_star": r["D_star"],
+                                "nodes_expanded": r["nodes_expanded"], "rounds": r["rounds"], "pop_k": ctx.cfg.pop_k}
+        ctx.close()
     torch.cuda.synchronize()
     return out
 
@@ -381,11 +465,14 @@ def run_ours(args):
         extras = run_extras(dd, torch)
 
     cpu = None
+    cpu_batch = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, el = oracle_rate(w, args.cpu_seconds, 5)
         cpu = {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d full oracle solves of the same window (Algorithm 1, pop 1), one host thread, %.1f s"
                          % (n, el)}
+        if not args.no_extras:
+            cpu_batch = oracle_pool_rate(args.cpu_seconds)
 
     ms = sorted(step_ms)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -404,6 +491,8 @@ def run_ours(args):
            "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
            "clocks": clk, "plain_pop1": plain, "roofline_shared_atomics": roofline_atomics,
            "roofline_l2": roofline_l2}
+    if cpu_batch:
+        out["cpu_baseline_batch"] = cpu_batch
     out.update(extras)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -300,3 +300,22 @@ def test_trained_model_gains_over_the_plain_search():
     assert inside >= 0.8 * len(ws)
     ctx.close()
     m.close()
+
+
+def test_training_labels_match_the_oracle():
+    # The training targets are the exact batch solver's D* (u* = D* tau): a
+    # sample of training windows (the three smallest of the first 64) is
+    # re-solved by the oracle with the same pop width.
+    from paper_2209_13168_gb300 import warm_start
+    from synth.descent import WARM_TRAIN_SEED
+    specs = warm_start.window_specs(64, WARM_TRAIN_SEED)
+    pick = sorted(range(64), key=lambda i: specs[i][4] + specs[i][6])[:3]
+    ctx = warm_start.context()
+    _, u, D, _ = warm_start.label(ctx, [specs[i] for i in pick], log=None)
+    u = u.cpu().numpy()
+    for j, i in enumerate(pick):
+        w = make_window(*specs[i])
+        want = O.solve(O.Window.of(w), *warm_start.PARAMS, ctx.cfg.pop_k)
+        assert float(D[j]) == want["D_star"]
+        assert u[j] == np.float32(np.float64(want["D_star"]) * np.float64(np.float32(w.tau)))
+    ctx.close()
