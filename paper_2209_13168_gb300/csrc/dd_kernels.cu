@@ -766,15 +766,18 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     const int bins1 = bins_of(g) + 1;
     const size_t task_cells = (size_t)g.planes * g.W * g.H;
     // Block b starts with unit b; later units come from the counter, which
-    // numbers them from gridDim.x on.
+    // numbers them from gridDim.x on.  The counter is asked when a unit
+    // starts and its answer stored only when the unit ends, so no warp waits
+    // for it; the unit's own barriers order every thread's read of s_unit
+    // before that store.
     if (threadIdx.x == 0) s_unit = blockIdx.x;
     for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0u;
     __syncthreads();
     for (;;) {
         const int u = s_unit;
         if (u >= n_units) break;
-        __syncthreads();                          // every thread has read s_unit
-        if (threadIdx.x == 0) s_unit = gridDim.x + atomicAdd(work, 1);   // the next unit, fetched early
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(work, 1);
         const int j = u / g.n_tiles, ti = u - j * g.n_tiles;
         const Job jb = jobs[j];
         const int64_t ev_off = a.wins[jb.win].ev_off;
@@ -790,7 +793,8 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
         p.sums = a.mg.sums ? a.mg.sums + (size_t)jb.task * g.n_tiles : nullptr;
         eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last, queue);
-        __syncthreads();                          // the unit's readers are done; s_unit is set
+        if (threadIdx.x == 0) s_unit = gridDim.x + next;
+        __syncthreads();                          // the unit is done; s_unit is set
     }
 }
 
