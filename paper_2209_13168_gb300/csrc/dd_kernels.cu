@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     __shared__ Node kids[2 * MAX_POP + 1];
     __shared__ Node sorted_kids[2 * MAX_POP + 1];
     __shared__ int s_nk, s_stop;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int w = blockIdx.x;
     const int par = sch->round & 1;
     SolveState* st = st_all + w;
