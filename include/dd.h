@@ -262,6 +262,14 @@ int dd_resample(dd_ctx* ctx, const dd_events* in, int32_t W, int32_t H, int32_t 
 int dd_stream_solve(dd_ctx* ctx, const dd_events* stream, double t_start, float tau, double hop, int32_t n_windows,
                     const dd_window_params* params, dd_result* out, float* ttc, int64_t* first);
 
+/* The time span of a batch (Sec. 3.3 measures a batch's times from its
+ * earliest event, so the batch covers [0, tau]): t0 = the least finite
+ * timestamp, tau = (greatest - least) in binary32, so every event passes
+ * the solver's window test 0 <= t - t0 <= tau.  ev's t0/tau are ignored;
+ * device arrays are reduced on the context's stream.  Errors: DD_ERR_ARG
+ * (n < 1, no finite timestamp, or all timestamps equal: no span). */
+int dd_time_span(dd_ctx* ctx, const dd_events* ev, float* t0, float* tau);
+
 /* The FOE of the coarse frame: foe (W2/W), foe (H2/H) in binary32. */
 int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
                     float* foe_y2);

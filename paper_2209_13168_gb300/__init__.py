@@ -8,8 +8,8 @@ missing or fails to load, every entry point raises.
 The functions keep the C names (dd_create, dd_contrast, dd_bound, dd_solve,
 dd_solve_trace, dd_solve_window, dd_solve_batch, dd_features, dd_set_warm_model,
 dd_set_stream, dd_get_stats, dd_reset_stats, dd_set_timing, dd_destroy,
-dd_strerror, dd_resample, dd_resample_foe, dd_stream_solve, dd_probe_peaks, the dd_serve_* and
-dd_mlp_* families); ``Context``, ``Server``
+dd_strerror, dd_resample, dd_resample_foe, dd_time_span, dd_stream_solve,
+dd_probe_peaks, the dd_serve_* and dd_mlp_* families); ``Context``, ``Server``
 and ``Mlp`` wrap them for numpy arrays (host events) and torch CUDA tensors
 (device events, features, training batches).
 
@@ -156,6 +156,8 @@ SIGNATURES = {
                                    _P(ctypes.c_int64)]),
     "dd_stream_solve": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_double, ctypes.c_float, ctypes.c_double,
                                        ctypes.c_int32, _P(dd_window_params), _P(dd_result), _VP, _VP]),
+    "dd_time_span": (ctypes.c_int, [_VP, ctypes.POINTER(dd_events), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_float)]),
     "dd_resample_foe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "dd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -251,6 +253,10 @@ class Events:
         n = int(x.shape[0])
         self.c = dd_events(_ptr(x) if n else None, _ptr(y) if n else None, _ptr(t) if n else None, n,
                            float(t0), float(tau), 1 if dev else 0, _ptr(p) if (n and p is not None) else None)
+
+    def with_time(self, t0, tau):
+        """The same arrays as a window [t0, t0 + tau] (e.g. from Context.time_span)."""
+        return Events(self.x, self.y, self.t, t0, tau, self.p)
 
     @classmethod
     def of(cls, w, device=None, polarity=False):
@@ -447,6 +453,13 @@ def dd_stream_solve(h, stream, t_start, tau, hop, n_windows, params=(-1.0, 1.0, 
     return rc, res, ttc, first
 
 
+def dd_time_span(h, ev):
+    """(t0, tau) of a batch measured from its earliest event (Sec. 3.3)."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(load().dd_time_span(h, ctypes.byref(ev.c), ctypes.byref(a), ctypes.byref(b)), "dd_time_span")
+    return a.value, b.value
+
+
 def dd_resample_foe(W, H, foe_x, foe_y, W2, H2):
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(load().dd_resample_foe(W, H, foe_x, foe_y, W2, H2, ctypes.byref(a), ctypes.byref(b)), "dd_resample_foe")
@@ -616,6 +629,10 @@ class Context:
         the fast mode's pre-pass (dd_resample); returns Events on the device."""
         x, y, t = dd_resample(self.h, ev, W, H, self.W, self.H, keep, seed)
         return Events(x.contiguous(), y.contiguous(), t.contiguous(), ev.c.t0, ev.c.tau)
+
+    def time_span(self, ev):
+        """(t0, tau) of a batch measured from its earliest event (Sec. 3.3)."""
+        return dd_time_span(self.h, ev)
 
     def stream_solve(self, stream, t_start, tau, hop, n_windows, params=(-1.0, 1.0, 1e-4, 0.0)):
         """The stream-wise estimation (dd_stream_solve): windows of `stream`."""

@@ -987,6 +987,38 @@ int dd_stream_solve(dd_ctx* c, const dd_events* stream, double t_start, float ta
     return rc;
 }
 
+int dd_time_span(dd_ctx* c, const dd_events* ev, float* t0, float* tau) {
+    if (!c || !ev || !t0 || !tau || ev->n < 1 || !ev->t) return DD_ERR_ARG;
+    float lo = INFINITY, hi = -INFINITY;
+    if (ev->device_ptrs) {
+        const int32_t nb = dd::span_blocks(ev->n);
+        float2* d = nullptr;
+        DD_TRY(cudaMallocAsync((void**)&d, sizeof(float2) * (nb + 1), c->stream));
+        float2 h;
+        cudaError_t e = dd::launch_time_span(ev->t, ev->n, d, d + nb, c->stream);
+        c->stats.kernel_launches += 2;
+        if (e == cudaSuccess) e = copy(c, &h, d + nb, sizeof(float2), cudaMemcpyDeviceToHost);
+        cudaError_t e2 = cudaFreeAsync(d, c->stream);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = sync(c);
+        DD_TRY(e);
+        lo = h.x;
+        hi = h.y;
+    } else {
+        for (int64_t i = 0; i < ev->n; i++)
+            if (std::isfinite(ev->t[i])) {
+                lo = std::fmin(lo, ev->t[i]);
+                hi = std::fmax(hi, ev->t[i]);
+            }
+    }
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return DD_ERR_ARG;
+    const float span = hi - lo;                    // binary32, as the window test takes t - t0
+    if (!(span > 0.0f) || !std::isfinite(span)) return DD_ERR_ARG;
+    *t0 = lo;
+    *tau = span;
+    return DD_OK;
+}
+
 int dd_resample_foe(int32_t W, int32_t H, float foe_x, float foe_y, int32_t W2, int32_t H2, float* foe_x2,
                     float* foe_y2) {
     if (W < 1 || H < 1 || W2 < 1 || H2 < 1 || !foe_x2 || !foe_y2) return DD_ERR_ARG;

@@ -1,8 +1,9 @@
 // Pre-passes over event streams: the paper's fast mode (Sec. 6, the resized
 // and resampled sequences: the events of a window with their coordinates
 // scaled to a coarser frame and a random share of them kept, compacted in
-// their order), and the windows of a time-sorted stream (Sec. 4.4: the
-// stream taken batch by batch).
+// their order), the windows of a time-sorted stream (Sec. 4.4: the stream
+// taken batch by batch), and the time span of a batch (Sec. 3.3 measures a
+// batch's times from its earliest event).
 //
 // Event i goes to the nearest coarse pixel centre, floor(x k + 1/2) with
 // k = W2/W in binary32, clamped to the frame, and is kept when the top 24
@@ -153,7 +154,65 @@ __global__ void k_stream_bounds(const float* t, int64_t n, double t_start, doubl
     t0_out[k] = t0;
 }
 
+// The time span of n timestamps: per block the least and greatest finite t
+// (grid-stride), then one block over the blocks' results.  Non-finite
+// timestamps are skipped here (the solver's own validation rejects them).
+constexpr int SPAN_THREADS = 256;
+
+__device__ __forceinline__ void span_reduce(float& lo, float& hi) {
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    __shared__ float s_lo[SPAN_THREADS / 32], s_hi[SPAN_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < SPAN_THREADS / 32; w++) {
+            lo = fminf(lo, s_lo[w]);
+            hi = fmaxf(hi, s_hi[w]);
+        }
+}
+
+__global__ void __launch_bounds__(SPAN_THREADS) k_span_part(const float* t, int64_t n, float2* part) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * SPAN_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SPAN_THREADS) {
+        const float v = t[i];
+        if (isfinite(v)) {
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    }
+    span_reduce(lo, hi);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_float2(lo, hi);
+}
+
+__global__ void __launch_bounds__(SPAN_THREADS) k_span_final(const float2* part, int nb, float2* out) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += SPAN_THREADS) {
+        lo = fminf(lo, part[i].x);
+        hi = fmaxf(hi, part[i].y);
+    }
+    span_reduce(lo, hi);
+    if (threadIdx.x == 0) *out = make_float2(lo, hi);
+}
+
 }  // namespace
+
+int32_t span_blocks(int64_t n) {
+    const int64_t b = (n + SPAN_THREADS - 1) / SPAN_THREADS;
+    return (int32_t)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+cudaError_t launch_time_span(const float* t, int64_t n, float2* part, float2* out, cudaStream_t s) {
+    const int32_t nb = span_blocks(n);
+    k_span_part<<<nb, SPAN_THREADS, 0, s>>>(t, n, part);
+    k_span_final<<<1, SPAN_THREADS, 0, s>>>(part, nb, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stream_bounds(const float* t, int64_t n, double t_start, double hop, float tau, int32_t n_windows,
                                  int64_t* first, int64_t* count, float* t0, cudaStream_t s) {

@@ -259,6 +259,11 @@ cudaError_t launch_resample(const int16_t* x, const int16_t* y, const float* t, 
                             int32_t W2, int32_t H2, float keep, uint64_t seed, int16_t* x2, int16_t* y2, float* t2,
                             int32_t* counts, int64_t* offsets, int32_t* err, cudaStream_t s);
 
+// Time span of n timestamps (dd_fast.cu): out = (least, greatest) finite t;
+// part holds span_blocks(n) entries.
+int32_t span_blocks(int64_t n);
+cudaError_t launch_time_span(const float* t, int64_t n, float2* part, float2* out, cudaStream_t s);
+
 // Windows of a time-sorted stream (dd_fast.cu): for k < n_windows, the
 // events with (t - t0_k) in [0, tau], t0_k = (float)(t_start + k hop): the
 // first index and the count of them, and t0_k.

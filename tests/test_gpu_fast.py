@@ -70,3 +70,34 @@ def test_fast_solve_matches_oracle(pop_k):
     assert got["trace"] == want["trace"]
     assert abs(got["D_star"] - 0.35) <= 0.05
     ctx.close()
+
+
+def test_time_span_of_a_batch():
+    # Sec. 3.3 measures a batch's times from its earliest event: t0 = the
+    # least timestamp, tau = greatest - least in binary32; the window so
+    # described solves as the oracle's window [t0, t0 + tau].
+    w = make_window(120, 90, 60.0, 45.0, 2000, 80, 500, 0.25, 0.4, 11, t0=3.25)
+    ctx = dd.Context(w.W, w.H, w.foe_x, w.foe_y, pop_k=4)
+    want = (float(w.t.min()), float(np.float32(w.t.max() - w.t.min())))
+    for dev in (None, "cuda"):
+        assert ctx.time_span(dd.Events.of(w, device=dev)) == want
+    t0, tau = want
+    got = ctx.solve(dd.Events.of(w, device="cuda").with_time(t0, tau))
+    ref = O.solve(O.Window(w.W, w.H, w.foe_x, w.foe_y, w.x, w.y, w.t, t0, tau), -1.0, 1.0, 1e-4, 0.0, 4)
+    for k in ("D_star", "K_hat", "gap_K", "nodes_expanded", "rounds"):
+        assert got[k] == ref[k], k
+    # several blocks of the device reduction; a non-finite timestamp is skipped
+    g = torch.Generator(device="cuda").manual_seed(5)
+    t = torch.rand(3_000_001, device="cuda", generator=g) * 7.0 + 1.0
+    t[123] = float("nan")
+    x = torch.zeros(t.shape[0], dtype=torch.int16, device="cuda")
+    tn = t.cpu().numpy()
+    fin = tn[np.isfinite(tn)]
+    assert ctx.time_span(dd.Events(x, x, t, 0.0, 1.0)) == (float(fin.min()), float(np.float32(fin.max() - fin.min())))
+    # no span, no events
+    flat = torch.full((5,), 2.0, device="cuda")
+    with pytest.raises(dd.DDError):
+        ctx.time_span(dd.Events(x[:5], x[:5], flat, 0.0, 1.0))
+    with pytest.raises(dd.DDError):
+        ctx.time_span(dd.Events(x[:0], x[:0], flat[:0], 0.0, 1.0))
+    ctx.close()
