@@ -64,6 +64,7 @@ enum {
     DD_ERR_NO_DEVICE = -6,      /* no usable sm_103 device                       */
     DD_ERR_CAPACITY = -7,       /* input exceeds a fixed capacity (no-alloc scratch, */
                                 /* serving slot)                                     */
+    DD_ERR_CANCELLED = -8,      /* dd_serve_cancel stopped the request              */
     DD_PENDING = 1              /* dd_serve_poll: the request has not finished yet   */
 };
 
@@ -262,6 +263,16 @@ int dd_resample(dd_ctx* ctx, const dd_events* in, int32_t W, int32_t H, int32_t 
 int dd_stream_solve(dd_ctx* ctx, const dd_events* stream, double t_start, float tau, double hop, int32_t n_windows,
                     const dd_window_params* params, dd_result* out, float* ttc, int64_t* first);
 
+/* Checked builds (compiled with -DDD_CHECKED): the evaluation kernels test
+ * every index into a shared tile, a window's events, a split accumulator and
+ * the sorted-event output before using it; an index out of range sets a bit
+ * of an error word and the access is skipped (bits: 1 point and one-pixel
+ * tile cells, 2 segment tile cells, 4 event indices, 8 ingest positions, 16
+ * accumulator and image cells).  *flags = that word of the current device
+ * (0 in other builds), *checked = 1 in a checked build; reset != 0 clears
+ * it.  Errors: DD_ERR_ARG (null outputs), DD_ERR_CUDA. */
+int dd_check_flags(uint32_t* flags, int32_t* checked, int32_t reset);
+
 /* The time span of a batch (Sec. 3.3 measures a batch's times from its
  * earliest event, so the batch covers [0, tau]): t0 = the least finite
  * timestamp, tau = (greatest - least) in binary32, so every event passes
@@ -402,6 +413,14 @@ int dd_serve_slots(dd_server* s, int32_t* slots, int64_t* max_events);
  * DD_ERR_CUDA of the server. */
 int dd_serve_submit(dd_server* s, const dd_events* ev, const dd_window_params* p, double arrival_s,
                     uint64_t* ticket);
+
+/* Cancel a request.  Not yet admitted: it is dropped.  Running: its search
+ * stops at the end of the current round (its slot's evaluations of that
+ * round complete; nothing of it reaches other windows).  Finished: nothing
+ * changes.  dd_serve_poll / dd_serve_wait then return the request's status,
+ * DD_ERR_CANCELLED for a cancelled one.  Errors: DD_ERR_ARG (unknown or
+ * already collected ticket). */
+int dd_serve_cancel(dd_server* s, uint64_t ticket);
 
 /* DD_PENDING while the request runs or waits; otherwise its status (results
  * and latency = finish time - arrival time, in seconds, written when not

@@ -18,7 +18,9 @@ None (Algorithm 1 from the centre), "model" (the context's warm-start model)
 or (D_warm, w_warm) (a given guess and half-width).
 """
 import ctypes
+import json
 import os
+import time
 
 import numpy as np
 
@@ -28,6 +30,7 @@ LIB_PATH = os.path.join(_PKG, "libdd.so")
 DD_OK, DD_ERR_ARG, DD_ERR_OOM, DD_ERR_QUEUE_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_NO_DEVICE = \
     0, -1, -2, -3, -4, -5, -6
 DD_ERR_CAPACITY = -7
+DD_ERR_CANCELLED = -8
 DD_PENDING = 1
 DD_NOALLOC_MAX_EVENTS = 1 << 20
 DD_WARM_NONE, DD_WARM_GIVEN, DD_WARM_MODEL = 0, 1, 2
@@ -141,6 +144,7 @@ SIGNATURES = {
     "dd_serve_submit": (ctypes.c_int, [_VP, _P(dd_events), _P(dd_window_params), ctypes.c_double,
                                        _P(ctypes.c_uint64)]),
     "dd_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(dd_result), _P(ctypes.c_double)]),
+    "dd_serve_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "dd_serve_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(dd_result), _P(ctypes.c_double)]),
     "dd_serve_stats": (ctypes.c_int, [_VP, _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "dd_serve_stop": (ctypes.c_int, [_VP]),
@@ -156,6 +160,7 @@ SIGNATURES = {
                                    _P(ctypes.c_int64)]),
     "dd_stream_solve": (ctypes.c_int, [_VP, _P(dd_events), ctypes.c_double, ctypes.c_float, ctypes.c_double,
                                        ctypes.c_int32, _P(dd_window_params), _P(dd_result), _VP, _VP]),
+    "dd_check_flags": (ctypes.c_int, [_P(ctypes.c_uint32), _P(ctypes.c_int32), ctypes.c_int32]),
     "dd_time_span": (ctypes.c_int, [_VP, ctypes.POINTER(dd_events), ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(ctypes.c_float)]),
     "dd_resample_foe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -167,11 +172,13 @@ _lib = None
 
 
 def load(path=None):
-    """Load libdd.so (built by __graft_entry__.build()); raises if it is absent."""
+    """Load libdd.so (built by __graft_entry__.build(); the environment
+    variable DD_LIBRARY names another build, e.g. the checked one); raises if
+    it is absent."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("DD_LIBRARY") or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError("libdd.so not found at %s: build it with __graft_entry__.build() "
                            "(the estimator has no CPU fallback)" % p)
@@ -453,11 +460,48 @@ def dd_stream_solve(h, stream, t_start, tau, hop, n_windows, params=(-1.0, 1.0, 
     return rc, res, ttc, first
 
 
+def dd_check_flags(reset=False):
+    """(error word, checked build?) of the evaluation kernels' index tests."""
+    f, c = ctypes.c_uint32(), ctypes.c_int32()
+    _check(load().dd_check_flags(ctypes.byref(f), ctypes.byref(c), 1 if reset else 0), "dd_check_flags")
+    return f.value, bool(c.value)
+
+
 def dd_time_span(h, ev):
     """(t0, tau) of a batch measured from its earliest event (Sec. 3.3)."""
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(load().dd_time_span(h, ctypes.byref(ev.c), ctypes.byref(a), ctypes.byref(b)), "dd_time_span")
     return a.value, b.value
+
+
+LOG_KEYS = ("status", "D_star", "D_end", "contrast", "bound_gap", "K_hat", "gap_K", "nodes_expanded", "point_evals",
+            "bound_evals", "event_warps", "cell_increments", "bound_increments", "rounds", "max_queue", "D_warm",
+            "w_warm")
+
+
+def write_pgm(path, img):
+    """An image of counts as a binary PGM (16-bit, big-endian samples; counts
+    above 65535 saturate), written from a host array; no graphics library."""
+    a = np.asarray(img)
+    if a.ndim != 2:
+        raise ValueError("write_pgm takes one [H][W] image")
+    a = np.minimum(a.astype(np.int64), 65535).astype(">u2")
+    with open(path, "wb") as f:
+        f.write(b"P5\n%d %d\n65535\n" % (a.shape[1], a.shape[0]))
+        f.write(a.tobytes())
+
+
+def read_pgm(path):
+    """The counts of a PGM written by write_pgm."""
+    with open(path, "rb") as f:
+        data = f.read()
+    parts = data.split(b"\n", 3)
+    if parts[0] != b"P5":
+        raise ValueError("not a binary PGM")
+    W, H = (int(v) for v in parts[1].split())
+    maxval = int(parts[2])
+    dt = ">u2" if maxval > 255 else "u1"
+    return np.frombuffer(parts[3], dtype=dt, count=W * H).reshape(H, W).astype(np.uint32)
 
 
 def dd_resample_foe(W, H, foe_x, foe_y, W2, H2):
@@ -528,6 +572,11 @@ class Server:
         d["latency_s"] = lat.value
         return d
 
+    def cancel(self, ticket):
+        """Drop a waiting request or stop a running one after its current round;
+        poll/wait then raise DDError with DD_ERR_CANCELLED."""
+        _check(load().dd_serve_cancel(self.h, ticket), "dd_serve_cancel")
+
     def poll(self, ticket):
         return self._take(load().dd_serve_poll, ticket)
 
@@ -557,11 +606,27 @@ class Context:
         self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds, host_loop, max_splits,
                              warp_to_start, polarity)
         self.h = dd_create(self.W, self.H, float(foe_x), float(foe_y), self.cfg)
+        self._log = None
 
     @property
     def M(self):
         """Image cells of one hypothesis (both planes with polarity)."""
         return self.planes * self.W * self.H
+
+    def set_log(self, path):
+        """Append one JSON line per solved window to `path` (None: stop)."""
+        if self._log:
+            self._log.close()
+        self._log = open(path, "a") if path else None
+
+    def _logged(self, results, seconds, kind):
+        if self._log:
+            for r in results:
+                rec = {k: r[k] for k in LOG_KEYS if k in r}
+                rec.update(kind=kind, windows_in_call=len(results), call_us=seconds * 1e6)
+                self._log.write(json.dumps(rec) + "\n")
+            self._log.flush()
+        return results
 
     def _image(self, img):
         shape = (-1, self.H, self.W) if self.planes == 1 else (-1, 2, self.H, self.W)
@@ -580,6 +645,9 @@ class Context:
         if self.h:
             dd_destroy(self.h)
             self.h = None
+        if getattr(self, "_log", None):
+            self._log.close()
+            self._log = None
 
     def __del__(self):
         try:
@@ -611,15 +679,27 @@ class Context:
         """Solve several windows at once; params defaults to [-1, 1], 1e-4, 0."""
         if params is None:
             params = [(-1.0, 1.0, 1e-4, 0.0)] * len(evs)
-        return dd_solve_batch(self.h, evs, params)
+        t0 = time.perf_counter()
+        rc, res = dd_solve_batch(self.h, evs, params)
+        self._logged(res, time.perf_counter() - t0, "batch")
+        return rc, res
 
     def solve(self, ev, D_lo=-1.0, D_hi=1.0, tol_D=1e-4, gamma=0.0, trace_cap=0, warm=None):
         """One exact solve; warm = None, "model" or (D_warm, w_warm)."""
+        t0 = time.perf_counter()
         if warm is not None:
-            return dd_solve_window(self.h, ev, (D_lo, D_hi, tol_D, gamma, warm), trace_cap)
-        if trace_cap:
-            return dd_solve_trace(self.h, ev, D_lo, D_hi, tol_D, gamma, trace_cap)
-        return dd_solve(self.h, ev, D_lo, D_hi, tol_D, gamma)
+            r = dd_solve_window(self.h, ev, (D_lo, D_hi, tol_D, gamma, warm), trace_cap)
+        elif trace_cap:
+            r = dd_solve_trace(self.h, ev, D_lo, D_hi, tol_D, gamma, trace_cap)
+        else:
+            r = dd_solve(self.h, ev, D_lo, D_hi, tol_D, gamma)
+        self._logged([r], time.perf_counter() - t0, "single")
+        return r
+
+    def image(self, ev, D):
+        """The image of warped events at D (Eq. 12): uint32 [H][W], or
+        [2][H][W] with polarity planes."""
+        return self.contrast(ev, np.array([D], np.float32), want_iwe=True)[3][0]
 
     def features(self, evs):
         return dd_features(self.h, evs)

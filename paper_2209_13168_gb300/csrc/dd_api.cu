@@ -276,6 +276,7 @@ int ensure_staging(dd_ctx* c, int64_t n) {
 // then sort each window's events by (time bucket, row).  Sets err[w] on
 // malformed events of window w.
 int ingest(dd_ctx* c, const dd_events* evs, int nw) {
+    dd::NvtxRange range("dd ingest");
     int rc = ensure_windows(c, nw);
     if (rc) return rc;
     int64_t total = 0, host_total = 0, chunks = 0;
@@ -359,6 +360,7 @@ dd_i128 from_i128(i128 v) {
 int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float* A, const float* B, dd_i128* K,
                uint64_t* S, int64_t* N, uint32_t* iwe) {
     const int64_t M = (int64_t)c->g.planes * c->g.W * c->g.H;     // image cells of one task
+    dd::NvtxRange range(kind == dd::TASK_POINT ? "dd contrast" : "dd bound");
     for (int32_t j0 = 0; j0 < n; j0 += c->max_tasks) {
         const int32_t m = n - j0 < c->max_tasks ? n - j0 : c->max_tasks;
         int32_t nj = 0;
@@ -519,6 +521,7 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
         if (rc) return rc;
     }
     if (trace_cap < 0 || (trace_cap > 0 && (!trace || nw != 1))) return DD_ERR_ARG;
+    dd::NvtxRange range(nw == 1 ? "dd solve" : "dd solve batch");
     if (trace_cap > c->trace_cap) {
         release(c->trace);
         c->trace_cap = 0;
@@ -558,6 +561,7 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
     c->stats.kernel_launches++;
     dd::TraceRec* tr_dev = trace_cap > 0 ? c->trace : nullptr;
     const bool graph = !c->cfg.host_loop && !c->timing;
+    dd::NvtxRange rounds("dd rounds");
     if (graph) {
         // One graph launch runs every round on the device.
         if (!c->gexec || c->g_nw != nw || c->g_key[0] != (const void*)c->ev || c->g_key[1] != (const void*)tr_dev ||
@@ -636,7 +640,8 @@ const char* dd_strerror(int status) {
         case DD_ERR_TIMEOUT: return "branch-and-bound round limit reached";
         case DD_ERR_CUDA: return "CUDA runtime error";
         case DD_ERR_NO_DEVICE: return "no sm_103 CUDA device";
-        case DD_ERR_CAPACITY: return "input exceeds the fixed scratch of the allocation-free entry point";
+        case DD_ERR_CAPACITY: return "input exceeds a fixed capacity (allocation-free scratch or serving slot)";
+        case DD_ERR_CANCELLED: return "request cancelled";
         default: return "unknown status";
     }
 }
@@ -985,6 +990,12 @@ int dd_stream_solve(dd_ctx* c, const dd_events* stream, double t_start, float ta
         for (int32_t k = 0; k < n_windows; k++)   // time to contact at the window's end: 1/D_end
             ttc[k] = out[k].status == DD_OK && out[k].D_end > 0.0f ? 1.0f / out[k].D_end : INFINITY;
     return rc;
+}
+
+int dd_check_flags(uint32_t* flags, int32_t* checked, int32_t reset) {
+    if (!flags || !checked) return DD_ERR_ARG;
+    DD_TRY(dd::check_flags(flags, checked, reset != 0));
+    return DD_OK;
 }
 
 int dd_time_span(dd_ctx* c, const dd_events* ev, float* t0, float* tau) {

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 struct dd_ctx;
 struct dd_mlp;
@@ -11,6 +12,15 @@ struct dd_mlp;
 namespace dd {
 
 typedef __int128 i128;
+
+// A named range over a host-side phase (ingest, rounds, read-back) for
+// profilers that record NVTX; free when none is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // One event after ingest: its offsets from the FOE as the warp uses them
 // (binary32 x - FOE_x and y - FOE_y) and its time since t0 (binary32
@@ -88,6 +98,7 @@ struct __align__(16) SolveState {
     float D_hat;
     int32_t phase, status, n_tasks, n_pop, q_n, q_start, q_cur, have_leaf, have_stop;
     float D_warm, w_warm;                 // the warm start the search began from
+    int32_t cancel, pad_c0, pad_c1, pad_c2;   // set between rounds: stop at the next control step
     int64_t nodes_expanded, point_evals, bound_evals, cells, bcells, rounds, max_queue, trace_len;
     Popped pop[MAX_POP];
 };
@@ -269,6 +280,9 @@ cudaError_t launch_time_span(const float* t, int64_t n, float2* part, float2* ou
 // first index and the count of them, and t0_k.
 cudaError_t launch_stream_bounds(const float* t, int64_t n, double t_start, double hop, float tau, int32_t n_windows,
                                  int64_t* first, int64_t* count, float* t0, cudaStream_t s);
+
+// The checked-build error word of the evaluation kernels (dd_kernels.cu).
+cudaError_t check_flags(uint32_t* flags, int32_t* checked, bool reset);
 
 // Context accessors for the serving engine (dd_serve.cu).
 void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks,

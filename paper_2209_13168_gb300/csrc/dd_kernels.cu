@@ -44,6 +44,25 @@ __device__ constexpr float WIDEN_UP = 1.0f + 0x1p-19f;
 // Half a pixel plus a 2^-8 px margin (above the cell rounding error).
 __device__ constexpr float HALF_PLUS = 0.50390625f;
 
+// Checked builds (-DDD_CHECKED, the stand-in for a memory checker): every
+// index into a shared tile, a window's events, a split accumulator or the
+// sorted-event output is tested first; an index out of range sets a bit of
+// g_dd_check and the access is skipped (nothing traps).  Bits: 1 point and
+// one-pixel tile cells, 2 segment tile cells, 4 event indices, 8 ingest
+// positions, 16 accumulator and image cells.  Other builds compile the tests
+// away.
+#ifdef DD_CHECKED
+__device__ unsigned int g_dd_check;
+__device__ __forceinline__ bool dd_in(long long i, long long n, unsigned bit) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_dd_check, bit);
+    return false;
+}
+#define DD_IN(i, n, bit) dd_in((long long)(i), (long long)(n), (bit))
+#else
+#define DD_IN(i, n, bit) true
+#endif
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
@@ -192,6 +211,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const Wi
         if (!event_ok(xi, yi, ti, tr, win.tau, g.W, g.H)) continue;
         const int key = event_key(g, yi, tr, bscale, plane_of(g, win, i));
         const int pos = base[key] + atomicAdd(&h[key], 1);
+        if (!DD_IN(pos, win.n, 8u)) continue;
         Ev e;
         e.dx = __fsub_rn((float)xi, g.fx);
         e.dy = __fsub_rn((float)yi, g.fy);
@@ -346,7 +366,7 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
                                          int addr, int y0, int y1, uint32_t* tile, unsigned long long& S,
                                          uint32_t& C) {
     if (mode == SEG_ONE) {
-        bump<DENSE>(&tile[addr], S, C);
+        if (DD_IN(addr, (y1 - y0) * tile_pitch(g), 2u)) bump<DENSE>(&tile[addr], S, C);
         return;
     }
     const bool major_x = mode == SEG_X;
@@ -360,11 +380,14 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
     const int j1 = cell_of(fn, dn, lo), j2 = cell_of(fn, dn, hi);
     if (major_x) {
         const int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), g.H - 1), y1 - 1);
-        for (int j = j0; j <= jn; j++) bump<DENSE>(&tile[(j - y0) * tile_pitch(g) + k], S, C);
+        for (int j = j0; j <= jn; j++)
+            if (DD_IN((j - y0) * tile_pitch(g) + k, (y1 - y0) * tile_pitch(g), 2u))
+                bump<DENSE>(&tile[(j - y0) * tile_pitch(g) + k], S, C);
     } else {
         const int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), g.W - 1);
         uint32_t* row = tile + (k - y0) * tile_pitch(g);
-        for (int j = j0; j <= jn; j++) bump<DENSE>(&row[j], S, C);
+        for (int j = j0; j <= jn; j++)
+            if (DD_IN((k - y0) * tile_pitch(g) + j, (y1 - y0) * tile_pitch(g), 2u)) bump<DENSE>(&row[j], S, C);
     }
 }
 
@@ -409,6 +432,9 @@ struct UnitPtrs {
     uint32_t* acc;                // split jobs: the task's accumulator [H][W]
     int32_t* done;                // split jobs: finished splits per tile
     Partial* sums;                // split jobs: sums of the splits per tile
+#ifdef DD_CHECKED
+    int64_t n_ev;                 // the window's event count
+#endif
 };
 
 // Bound images with at least this many covered cells per event (estimated
@@ -501,6 +527,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
         float sa = 0.0f, sb = 0.0f;
         if (f < total) {
             e = cur.at(f);
+            if (!DD_IN(e, p.n_ev, 4u)) e = 0;
             const Ev v = p.ev[e];
             const float dy = v.dy;
             const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
@@ -524,7 +551,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
                     // in s, so the segment covers that pixel only.
                     if ((unsigned)xa < (unsigned)W && ya_here) {
                         uint32_t Ci = 0;
-                        bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
+                        if (DD_IN((ya - y0) * P + xa, rows * P, 1u)) bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
                         C += Ci;
                     }
                 } else {
@@ -611,12 +638,15 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         uint32_t Ct = 0;                          // at most one increment per event
 #pragma unroll 4
         for (int f = f_begin + threadIdx.x; f < total; f += blockDim.x) {
-            const Ev v = p.ev[cur.at(f)];
+            const int e = cur.at(f);
+            if (!DD_IN(e, p.n_ev, 4u)) continue;
+            const Ev v = p.ev[e];
             const float s = warp_s(D, v.t, gg);
             const int uy = cell_of(g.fy, v.dy, s);
             if ((unsigned)(uy - y0) >= (unsigned)rows) continue;
             const int ux = cell_of(g.fx, v.dx, s);
-            if ((unsigned)ux < (unsigned)W) bump<false>(&tile[(uy - y0) * P + ux], S, Ct);
+            if ((unsigned)ux < (unsigned)W && DD_IN((uy - y0) * P + ux, rows * P, 1u))
+                bump<false>(&tile[(uy - y0) * P + ux], S, Ct);
         }
         C = Ct;
     } else {
@@ -641,7 +671,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             for (int r = wid; r < rows; r += nw)
                 for (int c = lane; c < W; c += 32) {
                     const uint32_t v = tile[r * P + c];
-                    out[r * W + c] = v;
+                    if (DD_IN(r * W + c, rows * W, 16u)) out[r * W + c] = v;
                     tile[r * P + c] = 0u;
                     if (dense) {
                         S += (unsigned long long)v * v;
@@ -685,6 +715,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
                 const uint32_t v = tile[r * P + c];
                 if (v) {
                     tile[r * P + c] = 0u;
+                    if (!DD_IN(r * W + c, rows * W, 16u)) continue;
                     const unsigned long long w = atomicAdd(&acc[r * W + c], v);
                     S += (2ull * w + v) * v;
                     Cl += v;
@@ -786,6 +817,9 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         UnitPtrs p;
         p.ev = a.ev + ev_off;
         p.rcp = a.rcp + ev_off;
+#ifdef DD_CHECKED
+        p.n_ev = a.wins[jb.win].n;
+#endif
         p.row_off = a.row_off + (size_t)jb.win * bins1;
         p.part = a.part + ((size_t)jb.win * a.task_stride + jb.task);
         p.out = a.iwe_out ? a.iwe_out + (size_t)jb.task * task_cells : nullptr;
@@ -796,6 +830,24 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         if (threadIdx.x == 0) s_unit = gridDim.x + next;
         __syncthreads();                          // the unit is done; s_unit is set
     }
+}
+
+// The checked-build error word (always 0 in other builds); reset clears it.
+cudaError_t check_flags(uint32_t* flags, int32_t* checked, bool reset) {
+#ifdef DD_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_dd_check, sizeof(uint32_t));
+    if (e == cudaSuccess && reset) {
+        const uint32_t zero = 0;
+        e = cudaMemcpyToSymbol(g_dd_check, &zero, sizeof(uint32_t));
+    }
+    *checked = 1;
+    return e;
+#else
+    (void)reset;
+    *flags = 0;
+    *checked = 0;
+    return cudaSuccess;
+#endif
 }
 
 int eval_resident_blocks(const Geom& g, int threads) {
@@ -897,6 +949,7 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
     }
     st->phase = PH_INIT;
     st->status = DD_OK;
+    st->cancel = 0;
     st->n_pop = 0;
     st->q_n = 0;
     st->q_start = 0;
@@ -1041,6 +1094,9 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         int stop = 0, nk = 0;
         if (*err) {
             if (lane == 0) s.status = DD_ERR_ARG;
+            stop = 1;
+        } else if (s.cancel) {                    // the host cancelled the search between rounds
+            if (lane == 0) s.status = DD_ERR_CANCELLED;
             stop = 1;
         } else if (s.phase == PH_INIT) {
             if (lane == 0) {

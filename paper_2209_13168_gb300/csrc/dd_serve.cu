@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -42,6 +43,8 @@ struct Request {
     int slot = -1;
     int state = 0;            // 0 waiting, 1 running, 2 finished
     int status = DD_OK;
+    bool cancel = false;      // running: stop it at the next round
+    bool cancel_sent = false; // its slot's device flag is set
     dd_result res{};
 };
 
@@ -54,6 +57,7 @@ struct dd_server {
     int S = 0;
     int64_t E = 0;
     int bins = 0, max_chunks = 0;
+    bool cancel_pending = false;  // a running request was cancelled (under mu)
     cudaStream_t stream = nullptr;
 
     // device, per slot
@@ -368,6 +372,32 @@ void loop(dd_server* s) {
             s->admitted++;
         }
         if (busy > s->peak_busy) s->peak_busy = busy;
+        // Cancelled running requests: their slots' searches stop at this
+        // round's control step (the flag is written before the round, in
+        // stream order).
+        std::vector<int> cancels;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->cancel_pending) {
+                for (int k = 0; k < s->S; k++) {
+                    if (!s->slot_req[k]) continue;
+                    Request& r = s->reqs[s->slot_req[k]];
+                    if (r.cancel && !r.cancel_sent) {
+                        r.cancel_sent = true;
+                        cancels.push_back(k);
+                    }
+                }
+                s->cancel_pending = false;
+            }
+        }
+        for (int k : cancels) {
+            static const int32_t one = 1;
+            if (cudaMemcpyAsync(reinterpret_cast<char*>(s->st + k) + offsetof(dd::SolveState, cancel), &one,
+                                sizeof(int32_t), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+                fail_all(s, DD_ERR_CUDA);
+                return;
+            }
+        }
         // One round over every busy slot.
         if (dd::launch_eval(s->g, a, s->threads, s->eval_blocks, s->stream) != cudaSuccess ||
             dd::launch_control(s->g, s->S, s->st, s->queues, s->tasks, s->max_tasks, s->part, s->err, nullptr,
@@ -521,6 +551,32 @@ static int take(dd_server* s, uint64_t ticket, dd_result* out, double* latency_s
     if (latency_s) *latency_s = it->second.done_t - it->second.arrival;
     s->reqs.erase(it);
     return st;
+}
+
+int dd_serve_cancel(dd_server* s, uint64_t ticket) {
+    if (!s) return DD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return DD_ERR_ARG;
+    Request& r = it->second;
+    if (r.state == 0) {                           // not admitted: dropped
+        for (auto q = s->waiting.begin(); q != s->waiting.end(); ++q)
+            if (*q == ticket) {
+                s->waiting.erase(q);
+                break;
+            }
+        std::memset(&r.res, 0, sizeof(r.res));
+        r.res.status = DD_ERR_CANCELLED;
+        r.status = DD_ERR_CANCELLED;
+        r.state = 2;
+        r.done_t = now_s();
+        s->cv.notify_all();
+    } else if (r.state == 1 && !r.cancel) {       // running: the serving thread stops it
+        r.cancel = true;
+        s->cancel_pending = true;
+        s->cv.notify_all();
+    }
+    return DD_OK;
 }
 
 int dd_serve_poll(dd_server* s, uint64_t ticket, dd_result* out, double* latency_s) {

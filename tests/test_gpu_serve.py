@@ -86,3 +86,43 @@ def test_capacity_and_malformed_windows():
     for w, r in ((ws[0], r0), (ws[2], r2)):
         assert r["K_hat"] == ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS)["K_hat"]
     ctx.close()
+
+
+def test_cancel_waiting_running_and_finished_requests():
+    import time
+    heavy = serve_config5(0, 188)                      # 833k events: hundreds of rounds at pop 1
+    light = [serve_config5(1, 20 + 30 * i, n_scale=0.02) for i in range(3)]
+    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=1)
+    solo = [ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS) for w in light]
+    srv = dd.Server(ctx, max_slots=2, max_events=1 << 20)
+    # waiting: arrives in an hour, dropped
+    far = srv.submit(dd.Events.of(light[0], device="cuda"), PARAMS, dd.Server.clock() + 3600.0)
+    srv.cancel(far)
+    with pytest.raises(dd.DDError) as e:
+        srv.wait(far)
+    assert e.value.status == dd.DD_ERR_CANCELLED
+    # running: cancelled once admitted, stopped at the end of a round
+    t_heavy = srv.submit(dd.Events.of(heavy, device="cuda"), PARAMS)
+    t0 = time.perf_counter()
+    while srv.stats()["admitted"] < 1 and time.perf_counter() - t0 < 10.0:
+        time.sleep(1e-4)
+    t_light = [srv.submit(dd.Events.of(w, device="cuda"), PARAMS) for w in light]
+    srv.cancel(t_heavy)
+    with pytest.raises(dd.DDError) as e:
+        srv.wait(t_heavy)
+    assert e.value.status == dd.DD_ERR_CANCELLED
+    # the others, served beside it, are unaffected
+    for t, want in zip(t_light, solo):
+        got = srv.wait(t)
+        for k in KEYS:
+            assert got[k] == want[k], k
+    # finished, not yet collected: nothing changes; unknown tickets are errors
+    t_done = srv.submit(dd.Events.of(light[1], device="cuda"), PARAMS)
+    time.sleep(0.5)
+    srv.cancel(t_done)
+    got = srv.wait(t_done)
+    assert got["K_hat"] == solo[1]["K_hat"]
+    with pytest.raises(dd.DDError):
+        srv.cancel(t_done)                             # already collected
+    srv.stop()
+    ctx.close()
