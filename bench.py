@@ -68,21 +68,29 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu, self.p, self.lines = gpu, None, []
 
-    def start(self):
+    def start(self, ready_s=3.0):
+        """Start sampling every 50 ms; returns once the first sample has
+        arrived (or after ready_s), so the timed region is covered."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                       "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.p = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < ready_s:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Median SM clock and throttle reasons of the samples taken between
+        t_begin and t_end (host perf_counter; all samples if none fall there)."""
         if not self.p:
             return None
         self.p.terminate()
@@ -90,9 +98,13 @@ class Clocks:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
+        lines = self.lines
+        if t_begin is not None:
+            inside = [x for x in lines if t_begin <= x[0] <= t_end + 0.06]
+            lines = inside or lines
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -368,12 +380,13 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local)
+    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     ctx.reset_stats()
     results = []
+    t_begin = time.perf_counter()
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
@@ -381,8 +394,9 @@ def run_ours(args):
             results.append(ctx.solve(ev))
             ends[k].record(stream)
     torch.cuda.synchronize()
+    t_end = time.perf_counter()
     st = ctx.stats()
-    clk = clocks.stop()
+    clk = clocks.stop(t_begin, t_end)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     r = results[-1]
@@ -506,7 +520,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pop-k", type=int, default=0, help="0: the autotuned value")
