@@ -554,6 +554,18 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
                         if (DD_IN((ya - y0) * P + xa, rows * P, 1u)) bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
                         C += Ci;
                     }
+                } else if ((xa == xb && abs(ya - yb) == 1) || (ya == yb && abs(xa - xb) == 1)) {
+                    // End cells side by side: one coordinate is constant and
+                    // the other takes two adjacent values, so the segment
+                    // covers exactly those two pixels (each counted where it
+                    // lies in the frame and in this band).
+                    uint32_t Ci = 0;
+                    if ((unsigned)xa < (unsigned)W && ya_here && DD_IN((ya - y0) * P + xa, rows * P, 1u))
+                        bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
+                    if ((unsigned)xb < (unsigned)W && (unsigned)(yb - y0) < (unsigned)rows &&
+                        DD_IN((yb - y0) * P + xb, rows * P, 1u))
+                        bump<DENSE>(&tile[(yb - y0) * P + xb], S, Ci);
+                    C += Ci;
                 } else {
                     pend = true;
                 }
