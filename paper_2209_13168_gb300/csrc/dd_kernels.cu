@@ -721,16 +721,32 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         // row so that they add into different words at a time.
         const int rot = (int)((long long)rows * split / splits);
         S = Cl = 0;
+        // Four columns per lane at a time: their additions are issued
+        // before any returned count is used, so the L2 round trips overlap.
+        constexpr int MERGE_COLS = 4;
         for (int q = wid; q < rows; q += nw) {
             const int r = q + rot < rows ? q + rot : q + rot - rows;
-            for (int c = lane; c < W; c += 32) {
-                const uint32_t v = tile[r * P + c];
-                if (v) {
-                    tile[r * P + c] = 0u;
-                    if (!DD_IN(r * W + c, rows * W, 16u)) continue;
-                    const unsigned long long w = atomicAdd(&acc[r * W + c], v);
-                    S += (2ull * w + v) * v;
-                    Cl += v;
+            for (int c0 = lane; c0 < W; c0 += 32 * MERGE_COLS) {
+                uint32_t v[MERGE_COLS], w[MERGE_COLS];
+#pragma unroll
+                for (int k = 0; k < MERGE_COLS; k++) {
+                    const int c = c0 + 32 * k;
+                    v[k] = c < W ? tile[r * P + c] : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < MERGE_COLS; k++) {
+                    const int c = c0 + 32 * k;
+                    w[k] = 0u;
+                    if (v[k]) {
+                        tile[r * P + c] = 0u;
+                        if (DD_IN(r * W + c, rows * W, 16u)) w[k] = atomicAdd(&acc[r * W + c], v[k]);
+                        else v[k] = 0u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < MERGE_COLS; k++) {
+                    S += (2ull * w[k] + v[k]) * v[k];
+                    Cl += v[k];
                 }
             }
         }
