@@ -115,6 +115,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--quick", action="store_true", help="fewer candidates")
+    ap.add_argument("--reps", type=int, default=3, help="timed repetitions per candidate (single windows)")
     args = ap.parse_args()
     import torch
     from synth import window_config1, window_config2
@@ -131,7 +132,7 @@ def main():
     for mode, ws in jobs:
         n = int(sum(w.n for w in ws) / len(ws))
         print("tuning %s %dx%d, %d windows of ~%d events" % (mode, ws[0].W, ws[0].H, len(ws), n), flush=True)
-        best = tune(ws, mode, cand)
+        best = tune(ws, mode, cand, reps=args.reps if mode == "single" else 3)
         best["windows"] = len(ws)
         best["events_per_window"] = n
         table[key(ws[0].W, ws[0].H, n, mode, name)] = best
