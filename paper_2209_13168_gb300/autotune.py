@@ -116,6 +116,7 @@ def main():
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--quick", action="store_true", help="fewer candidates")
     ap.add_argument("--reps", type=int, default=3, help="timed repetitions per candidate (single windows)")
+    ap.add_argument("--only", default=None, help="tune only the jobs whose name contains this (e.g. 1280x720)")
     args = ap.parse_args()
     import torch
     from synth import window_config1, window_config2
@@ -126,10 +127,17 @@ def main():
     cand = None
     if args.quick:
         cand = {"band_rows": [16, 38], "threads": [256, 512], "pop_k": [16, 32], "max_splits": [8, 16]}
+    from synth.descent import serve_config5
     jobs = [("single", [window_config1()]), ("single", [window_config2()])]
     params = batch_params3()
     jobs.append(("batch", [batch_window3(i, params) for i in range(256)]))
+    # 1280x720 descent windows (serving, stream and fast-mode studies): five
+    # windows of 100k-800k events one at a time, and a stream's 0.2 s windows
+    jobs.append(("single", [serve_config5(0, k) for k in (20, 60, 100, 140, 180)]))
+    jobs.append(("batch", [serve_config5(0, k, n_scale=0.5) for k in range(0, 189, 3)]))
     for mode, ws in jobs:
+        if args.only and args.only not in "%s %dx%d" % (mode, ws[0].W, ws[0].H):
+            continue
         n = int(sum(w.n for w in ws) / len(ws))
         print("tuning %s %dx%d, %d windows of ~%d events" % (mode, ws[0].W, ws[0].H, len(ws), n), flush=True)
         best = tune(ws, mode, cand, reps=args.reps if mode == "single" else 3)

@@ -19,7 +19,8 @@ def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=16, reps=3, gamma=0.0, lo
     PARAMS = (-1.0, 2.0, 1e-4, gamma)
     import torch
     w0 = windows[0]
-    full = dd.Context(w0.W, w0.H, w0.foe_x, w0.foe_y, pop_k=pop_k)
+    n_mean = sum(w.n for w in windows) // len(windows)
+    full = dd.Context.tuned(w0.W, w0.H, w0.foe_x, w0.foe_y, n_mean, mode="single", pop_k=pop_k)
     fx, fy = dd.dd_resample_foe(w0.W, w0.H, w0.foe_x, w0.foe_y, W2, H2)
     fast = dd.Context(W2, H2, fx, fy, pop_k=pop_k)
     evs = [dd.Events.of(w) for w in windows]

@@ -32,7 +32,9 @@ def compare(windows, params=(-1.0, 1.0, 1e-4, 0.0), pop_k=16, reps=3, batch=Fals
     nodes = {}
     for name, kw in variants:
         evs = [dd.Events.of(w, polarity=bool(kw.get("polarity"))) for w in windows]
-        ctx = dd.Context(w0.W, w0.H, w0.foe_x, w0.foe_y, pop_k=pop_k, **kw)
+        n_mean = sum(w.n for w in windows) // len(windows)
+        ctx = dd.Context.tuned(w0.W, w0.H, w0.foe_x, w0.foe_y, n_mean, mode="batch" if batch else "single",
+                               pop_k=pop_k, **kw)
         if batch:
             def run():
                 rc, res = ctx.solve_batch(evs, [params] * len(evs))

@@ -56,7 +56,7 @@ def run(rate_hz=40.0, n_streams=4, per_stream=WINDOWS_PER_STREAM, slots=16, pop_
     import torch
     own_ctx = ctx is None
     if own_ctx:
-        ctx = dd.Context(W, H, FX, FY, pop_k=pop_k)
+        ctx = dd.Context.tuned(W, H, FX, FY, 100_000, mode="batch", pop_k=pop_k)
     if windows is None:
         windows = make_windows(n_streams, per_stream)
     E = max(w.n for _, _, w in windows)
@@ -116,7 +116,7 @@ def main():
     import torch
     torch.cuda.set_device(0)
     ws = make_windows(a.streams, a.per_stream)
-    ctx = dd.Context(W, H, FX, FY, pop_k=a.pop_k)
+    ctx = dd.Context.tuned(W, H, FX, FY, 100_000, mode="batch", pop_k=a.pop_k)
     for r in a.rate:
         run(r, a.streams, a.per_stream, a.slots, host=a.host, windows=ws, ctx=ctx, log=print)
     ctx.close()

@@ -45,7 +45,8 @@ def evaluate(stream=0, n_windows=188, pop_k=16, reps=2, n_scale=1.0, log=None):
     from synth.gpu import make_stream_gpu
     x, y, t = make_stream_gpu(stream, 0, n_windows + 1, n_scale)
     ev = dd.Events(x, y, t, 0.0, 1.0)
-    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=pop_k)
+    ctx = dd.Context.tuned(1280, 720, 640.0, 360.0, int(x.shape[0]) * 2 // max(1, n_windows), mode="batch",
+                           pop_k=pop_k)
     rc, res, ttc, first = ctx.stream_solve(ev, 0.0, TAU, HOP, n_windows, PARAMS)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
