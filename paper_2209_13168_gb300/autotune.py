@@ -111,6 +111,29 @@ def lookup(W, H, n_events, mode="single", path=DEFAULT_TABLE):
     return {k: entry[k] for k in ("band_rows", "threads", "pop_k", "max_splits")}
 
 
+class _Resampled:
+    """A window given by device arrays (the fast mode's coarse window)."""
+
+    def __init__(self, ev, W, H, foe_x, foe_y):
+        self.x, self.y, self.t, self.t0, self.tau = ev.x, ev.y, ev.t, ev.c.t0, ev.c.tau
+        self.W, self.H, self.foe_x, self.foe_y = W, H, foe_x, foe_y
+        self.n = int(ev.c.n)
+
+
+def fast_mode_windows(W2=160, H2=90, keep=0.25, step=20):
+    """The fast mode's coarse windows of one 1280x720 descent (resampled on the GPU)."""
+    from synth.descent import serve_spec5
+    from synth.gpu import make_window_gpu
+    fx, fy = dd.dd_resample_foe(1280, 720, 640.0, 360.0, W2, H2)
+    rctx = dd.Context(W2, H2, fx, fy)
+    out = []
+    for k in range(0, 189, step):
+        ev = rctx.resample(dd.Events.of(make_window_gpu(serve_spec5(0, k))), 1280, 720, keep=keep, seed=0)
+        out.append(_Resampled(ev, W2, H2, fx, fy))
+    rctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_TABLE)
@@ -135,6 +158,7 @@ def main():
     # windows of 100k-800k events one at a time, and a stream's 0.2 s windows
     jobs.append(("single", [serve_config5(0, k) for k in (20, 60, 100, 140, 180)]))
     jobs.append(("batch", [serve_config5(0, k, n_scale=0.5) for k in range(0, 189, 3)]))
+    jobs.append(("single", fast_mode_windows()))
     for mode, ws in jobs:
         if args.only and args.only not in "%s %dx%d" % (mode, ws[0].W, ws[0].H):
             continue

@@ -11,7 +11,7 @@ import numpy as np
 
 import paper_2209_13168_gb300 as dd
 
-def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=16, reps=3, gamma=0.0, log=None):
+def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=None, reps=3, gamma=0.0, log=None):
     """Full-resolution vs fast-mode solves of `windows` (device-resident, one
     geometry): mean time per window (the fast mode includes its pre-pass)
     and mean |D* - D_true|.  gamma: Algorithm 1's stopping gap (contrast
@@ -20,9 +20,10 @@ def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=16, reps=3, gamma=0.0, lo
     import torch
     w0 = windows[0]
     n_mean = sum(w.n for w in windows) // len(windows)
-    full = dd.Context.tuned(w0.W, w0.H, w0.foe_x, w0.foe_y, n_mean, mode="single", pop_k=pop_k)
+    kw = {"pop_k": pop_k} if pop_k else {}       # None: each frame's tuned knobs
+    full = dd.Context.tuned(w0.W, w0.H, w0.foe_x, w0.foe_y, n_mean, mode="single", **kw)
     fx, fy = dd.dd_resample_foe(w0.W, w0.H, w0.foe_x, w0.foe_y, W2, H2)
-    fast = dd.Context(W2, H2, fx, fy, pop_k=pop_k)
+    fast = dd.Context.tuned(W2, H2, fx, fy, int(n_mean * keep), mode="single", **kw)
     evs = [dd.Events.of(w) for w in windows]
 
     def run_full():
@@ -43,6 +44,8 @@ def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=16, reps=3, gamma=0.0, lo
         out[name] = {"ms_per_window": dt * 1e3, "mean_abs_err_D": float(np.mean(err)),
                      "max_abs_err_D": float(np.max(err)), "mean_nodes": float(np.mean([r["nodes_expanded"] for r in res]))}
     out["speedup"] = out["full"]["ms_per_window"] / out["fast"]["ms_per_window"]
+    out["knobs"] = {name: {k: getattr(c.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}
+                    for name, c in (("full", full), ("fast", fast))}
     out["frame"] = "%dx%d -> %dx%d, keep %.2f" % (w0.W, w0.H, W2, H2, keep)
     out["gamma"] = gamma
     out["windows"] = len(windows)
