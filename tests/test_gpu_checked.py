@@ -90,3 +90,16 @@ def test_checked_build_parity_and_no_index_out_of_range():
 def test_normal_build_reports_no_checks():
     import paper_2209_13168_gb300 as dd
     assert dd.dd_check_flags() == (0, False)
+
+
+def test_checked_build_on_random_configurations():
+    # the randomised parity cases (every knob, FOE on the frame's edges,
+    # polarity, start-of-window warp) on the checked build: each compares
+    # with the oracle and asserts that no index was out of range
+    sys.path.insert(0, os.path.join(ROOT, "paper_2209_13168_gb300"))
+    import _build
+    env = dict(os.environ, DD_LIBRARY=_build.build(checked=True))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_gpu_fuzz.py"), "-q", "-x",
+                        "-p", "no:cacheprovider"], env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+    assert "40 passed" in r.stdout
