@@ -1,9 +1,10 @@
 // GB300 (sm_103a) kernels of the exact divergence estimator:
-//   ingest   validate + counting-sort events by (time bucket, row), per window
+//   ingest   validate + counting-sort events by (polarity plane, time bucket,
+//            row), per window
 //   eval     point contrast (Eqs. 11-13) and interval bound (Eqs. 14-19) on
 //            shared-memory IWE tiles: a resident grid takes (job, row band)
 //            units, a job being one task (or one split of it) of one window
-//   keys     per-task integer keys from the per-tile partial sums
+//   keys     per-task integer keys from the per-task sums
 //   control  Algorithm 1 on the device, one block per window: incumbent,
 //            priority queue, pruning, the next round's jobs
 //
