@@ -157,10 +157,18 @@ def profile_traffic(kernel_hash):
 
 
 def kernel_hash():
+    """sha256 of the evaluation kernel's sources without // comments and blank
+    lines: an edit to a comment does not make the profiled counters stale."""
     import hashlib
     h = hashlib.sha256()
     for f in ("dd_kernels.cu", "dd_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2209_13168_gb300", "csrc", f), "rb").read())
+        lines = []
+        for line in open(os.path.join(ROOT, "paper_2209_13168_gb300", "csrc", f)).read().splitlines():
+            i = line.find("//")
+            line = (line[:i] if i >= 0 else line).rstrip()
+            if line:
+                lines.append(line)
+        h.update("\n".join(lines).encode())
     return h.hexdigest()
 
 
