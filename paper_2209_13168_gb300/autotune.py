@@ -21,7 +21,7 @@ import paper_2209_13168_gb300 as dd
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
 
 CANDIDATES = {
-    "band_rows": [8, 12, 16, 24, 38],
+    "band_rows": [8, 10, 12, 16, 18, 20, 24, 38],
     "threads": [128, 256, 512],
     "pop_k": [16, 32, 64],
     "max_splits": [4, 8, 16],
