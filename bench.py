@@ -204,30 +204,47 @@ def cpu_model():
                                           fields.get("CPU part", "?"))
 
 
-def oracle_pool_rate(budget_s):
-    """Oracle solves (Algorithm 1, pop 1) of the uneven 256-window batch on
+def oracle_pool_rate(budget_s, make, n_total, params, what):
+    """Oracle solves (Algorithm 1, pop 1) of windows make(0), make(1), ... on
     every host core, one window per thread (the oracle's C calls release the
     GIL), in waves of one window per core until about budget_s has passed."""
     import concurrent.futures as cf
     import oracle as O
-    from synth.descent import batch_params3, batch_window3
     O.build()
-    p = batch_params3()
     cores = os.cpu_count() or 1
 
     def one(i):
-        r = O.solve(O.Window.of(batch_window3(i, p)), -1.0, 1.0, 1e-4, 0.0, 1)
-        return r["nodes_expanded"]
+        return O.solve(O.Window.of(make(i)), *params, 1)["nodes_expanded"]
     done, t0 = 0, time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
-        while done < 256 and time.perf_counter() - t0 < budget_s:
-            wave = list(range(done, min(256, done + cores)))
+        while done < n_total and time.perf_counter() - t0 < budget_s:
+            wave = list(range(done, min(n_total, done + cores)))
             list(ex.map(one, wave))
             done += len(wave)
     el = time.perf_counter() - t0
     return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
-            "sample": "windows 0-%d of the 256-window batch (config 3, generated in the worker), Algorithm 1 "
-                      "pop 1, %d threads, %.1f s" % (done - 1, cores, el)}
+            "sample": "%d %s (generated in the worker), Algorithm 1 pop 1, %d threads, %.1f s"
+                      % (done, what, cores, el)}
+
+
+def oracle_baselines(budget_s):
+    """The oracle beside the batch, serving and 346x260 workloads."""
+    import numpy as np
+    from synth import window_config1
+    from synth.descent import batch_params3, batch_window3, serve_config5
+    p = batch_params3()
+    out = {"cpu_baseline_batch": oracle_pool_rate(budget_s, lambda i: batch_window3(i, p), 256,
+                                                  (-1.0, 1.0, 1e-4, 0.0),
+                                                  "windows of the 256-window batch (config 3), in order")}
+    order = np.random.default_rng(5).permutation(4 * 189)
+    out["cpu_baseline_serving"] = oracle_pool_rate(
+        budget_s, lambda i: serve_config5(int(order[i]) % 4, int(order[i]) // 4), 4 * 189, (-1.0, 2.0, 1e-4, 0.0),
+        "windows of the four 1280x720 descents (config 5), a seeded random sample")
+    n, el = oracle_rate(window_config1(), budget_s, 200)
+    out["cpu_baseline_config1"] = {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": "%d full oracle solves of the 346x260 window (config 1), one host "
+                                             "thread, %.1f s" % (n, el)}
+    return out
 
 
 def run_reference(args):
@@ -494,7 +511,7 @@ def run_ours(args):
                "sample": "%d full oracle solves of the same window (Algorithm 1, pop 1), one host thread, %.1f s"
                          % (n, el)}
         if not args.no_extras:
-            cpu_batch = oracle_pool_rate(args.cpu_seconds)
+            cpu_batch = oracle_baselines(args.cpu_seconds)
 
     ms = sorted(step_ms)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -514,7 +531,7 @@ def run_ours(args):
            "clocks": clk, "plain_pop1": plain, "roofline_shared_atomics": roofline_atomics,
            "roofline_l2": roofline_l2}
     if cpu_batch:
-        out["cpu_baseline_batch"] = cpu_batch
+        out.update(cpu_batch)
     out.update(extras)
     if rank == 0:
         print(json.dumps(out), flush=True)
