@@ -364,14 +364,16 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
     for (int32_t j0 = 0; j0 < n; j0 += c->max_tasks) {
         const int32_t m = n - j0 < c->max_tasks ? n - j0 : c->max_tasks;
         int32_t nj = 0;
-        const int32_t cap = dd::split_cap(c->g, m * c->g.n_tiles);
+        int32_t n_dense = 0, rank = 0;
+        for (int32_t j = 0; j < m; j++)
+            n_dense += kind == dd::TASK_BOUND && dd::bound_cells(c->g, A[j0 + j], B[j0 + j], ev->tau) >= dd::DENSE_CELLS;
         for (int32_t j = 0; j < m; j++) {
             dd::Task& t = c->h_tasks[j];
             t.D_lo = A[j0 + j];
             t.D_hi = B[j0 + j];
             t.kind = kind;
-            const int32_t sp = dd::bound_splits(c->g, t.D_lo, t.D_hi, ev->tau);
-            t.splits = kind == dd::TASK_BOUND ? (sp < cap ? sp : cap) : 1;
+            const bool dense = kind == dd::TASK_BOUND && dd::bound_cells(c->g, t.D_lo, t.D_hi, ev->tau) >= dd::DENSE_CELLS;
+            t.splits = dense ? dd::fill_splits(c->g, m * c->g.n_tiles, n_dense, rank++) : 1;
         }
         for (int32_t j = m - 1; j >= 0; j--)              // heavier tasks first
             for (int32_t s = 0; s < c->h_tasks[j].splits; s++) {
@@ -773,7 +775,7 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     if (rc == DD_OK && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && dd::eval_smem_setup(c->g) != cudaSuccess) rc = DD_ERR_CUDA;
     if (rc == DD_OK && (c->eval_blocks = dd::eval_resident_blocks(c->g, c->threads)) <= 0) rc = DD_ERR_CUDA;
-    c->g.split_target = 2 * c->eval_blocks;
+    c->g.split_target = c->eval_blocks;
     if (rc == DD_OK) rc = ensure_windows(c, 1);
     if (rc != DD_OK) {
         dd_destroy(c);

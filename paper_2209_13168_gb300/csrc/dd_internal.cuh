@@ -156,7 +156,7 @@ struct Geom {
     int32_t W, H;
     float fx, fy;
     int32_t band_rows, n_tiles, n_tb, max_splits;
-    int32_t split_target;   // units a round needs before its bounds stop splitting (0: no cap)
+    int32_t split_target;   // resident evaluation blocks: a round's bounds split to fill one wave (0: never)
     int32_t ref0;           // 1: the warp maps events to the window's start (t_ref = 0), not its end
     int32_t planes;         // 1: polarity unused; 2: one image per polarity (p > 0, p <= 0)
     int32_t plane_tiles;    // row bands of one plane
@@ -168,31 +168,35 @@ __host__ __device__ inline int32_t bins_of(const Geom& g) { return g.planes * g.
 // The warp's reference time for a window of length tau.
 __host__ __device__ inline float warp_tref(const Geom& g, float tau) { return g.ref0 ? 0.0f : tau; }
 
-// Splits a bound task may take in a round of `units` (task, row band) units:
-// none once the round alone fills the evaluation grid, else enough to reach
-// split_target.  A schedule choice only.
-__host__ __device__ inline int32_t split_cap(const Geom& g, int32_t units) {
-    if (g.split_target <= 0) return g.max_splits;
-    if (units >= g.split_target) return 1;
-    const int32_t c = (g.split_target + units - 1) / (units > 0 ? units : 1);
-    return c < 1 ? 1 : (c > g.max_splits ? g.max_splits : c);
+// Covered cells per event of a bound over [D_lo, D_hi], estimated from the
+// scale change at t = 0, |g(D_hi) - g(D_lo)| with g = 1/(1 - D tau), times a
+// typical offset from the FOE, (W + H)/4.  Bounds of at least DENSE_CELLS are
+// dense (their tiles are summed in one pass) and are the ones worth
+// splitting over several blocks.  A schedule estimate only.
+constexpr float DENSE_CELLS = 4.0f;
+__host__ __device__ inline float bound_cells(const Geom& g, float D_lo, float D_hi, float tau) {
+    const float gl = 1.0f / (1.0f - D_lo * tau), gh = 1.0f / (1.0f - D_hi * tau);
+    return 1.0f + (gh > gl ? gh - gl : gl - gh) * 0.25f * (float)(g.W + g.H);
+}
+
+// Splits of dense bound task `rank` (0-based among the round's nb dense
+// bound tasks) in a round of `units` unsplit (task, row band) units: when the
+// round alone does not fill one wave of the resident evaluation grid
+// (split_target blocks), the spare blocks go to the dense bound tasks as extra
+// splits, spread evenly (an extra split of a task adds n_tiles units), so the
+// round runs as one wave of shorter units; none once the round fills the grid
+// (other tasks never split: their units are short already).  A schedule
+// choice only.
+__host__ __device__ inline int32_t fill_splits(const Geom& g, int32_t units, int32_t nb, int32_t rank) {
+    if (g.split_target <= 0 || nb <= 0 || units >= g.split_target) return 1;
+    const int32_t extra = (g.split_target - units) / g.n_tiles;
+    const int32_t s = 1 + extra / nb + (rank < extra % nb ? 1 : 0);
+    return s > g.max_splits ? g.max_splits : s;
 }
 
 // Row pitch of a shared-memory IWE tile: odd, so that the cells of one
 // column in consecutive rows fall in different shared-memory banks.
 __host__ __device__ inline int32_t tile_pitch(const Geom& g) { return g.W | 1; }
-
-// Blocks per row band for a bound task: about one per four estimated cells
-// per event.  An event's segment spans about |s(D_hi) - s(D_lo)| * |offset|
-// pixels; at t = 0 the scale change is |g(D_hi) - g(D_lo)|, g = 1/(1 - D tau),
-// and a typical offset is (W + H)/4.  A schedule heuristic only.
-__host__ __device__ inline int32_t bound_splits(const Geom& g, float D_lo, float D_hi, float tau) {
-    const float gl = 1.0f / (1.0f - D_lo * tau), gh = 1.0f / (1.0f - D_hi * tau);
-    const float ds = gh > gl ? gh - gl : gl - gh;
-    const float cells = 1.0f + ds * 0.25f * (float)(g.W + g.H);
-    const int32_t s = (int32_t)(cells * 0.25f);
-    return s < 1 ? 1 : (s > g.max_splits ? g.max_splits : s);
-}
 
 // Time buckets for a sort over H rows (rows of every plane): as many as fit
 // 4096 bins, at most 8.

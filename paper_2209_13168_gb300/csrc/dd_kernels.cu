@@ -438,10 +438,8 @@ struct UnitPtrs {
 #endif
 };
 
-// Bound images with at least this many covered cells per event (estimated
-// as in bound_splits) are dense: their increments skip the returned count
-// and the tile's sums are taken in one pass afterwards.
-constexpr float DENSE_CELLS = 4.0f;
+// Dense bound images (bound_cells >= DENSE_CELLS): their increments skip the
+// returned count and the tile's sums are taken in one pass afterwards.
 
 // Eqs. (16) and (19) for the unit's share of events, positions [f_begin,
 // total): Hbar into the tile, N_full into `full`, and (sparse) S and C.
@@ -663,10 +661,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
         }
         C = Ct;
     } else {
-        // The scale change at t = 0 times a typical offset, (W + H)/4 (the
-        // estimate bound_splits uses): covered cells per event.
-        const float gl = 1.0f / (1.0f - tk.D_lo * tau), gh = 1.0f / (1.0f - tk.D_hi * tau);
-        dense = 1.0f + fabsf(gh - gl) * 0.25f * (float)(g.W + g.H) >= DENSE_CELLS;
+        dense = bound_cells(g, tk.D_lo, tk.D_hi, tau) >= DENSE_CELLS;
         if (dense)
             bound_pass<true>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
         else
@@ -993,16 +988,20 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
     a.splits = 1;
     tasks[0] = a;
     int nt = 1, n_jobs = 1;
-    int n_pieces = 0;
-    for (int i = 0; i + 1 < n_cut; i++) n_pieces += cut[i] < cut[i + 1];
-    const int cap = split_ok ? split_cap(g, (1 + n_pieces) * g.n_tiles) : 1;
+    int n_pieces = 0, n_dense = 0, rank = 0;
+    for (int i = 0; i + 1 < n_cut; i++)
+        if (cut[i] < cut[i + 1]) {
+            n_pieces++;
+            n_dense += bound_cells(g, cut[i], cut[i + 1], tau) >= DENSE_CELLS;
+        }
     for (int i = 0; i + 1 < n_cut; i++) {
         if (!(cut[i] < cut[i + 1])) continue;
         Task b;                                   // bound of one piece
         b.D_lo = cut[i];
         b.D_hi = cut[i + 1];
         b.kind = TASK_BOUND;
-        b.splits = split_ok ? min(cap, bound_splits(g, b.D_lo, b.D_hi, tau)) : 1;
+        const bool dense = bound_cells(g, b.D_lo, b.D_hi, tau) >= DENSE_CELLS;
+        b.splits = split_ok && dense ? fill_splits(g, (1 + n_pieces) * g.n_tiles, n_dense, rank++) : 1;
         tasks[nt++] = b;
         n_jobs += b.splits;
     }
@@ -1360,11 +1359,11 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                         l.D_lo = p.lo;
                         l.D_hi = p.c;
                         l.kind = TASK_BOUND;
-                        l.splits = split_ok ? bound_splits(g, p.lo, p.c, s.tau) : 1;
+                        l.splits = 1;                 // the job builder decides (fill_splits)
                         r.D_lo = p.c;
                         r.D_hi = p.hi;
                         r.kind = TASK_BOUND;
-                        r.splits = split_ok ? bound_splits(g, p.c, p.hi, s.tau) : 1;
+                        r.splits = 1;
                         tasks[t] = l;
                         tasks[t + 1] = r;
                     } else {
@@ -1386,24 +1385,37 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             }
         }
         __syncwarp();
-        // Jobs of the next round, bound tasks first: a task of `splits`
-        // splits contributes that many jobs.
+        // Jobs of the next round, bound tasks first: a task of `splits` splits
+        // contributes that many jobs (fill_splits for the dense bounds, ranked
+        // in this loop's order; every other task has one split).
         if (s.phase != PH_DONE) {
-            const int nt = s.n_tasks;
-            const int cap = split_ok ? split_cap(g, nt * g.n_tiles) : 1;
+            const int nt = s.n_tasks, np = s.n_pop;
+            auto dense_at = [&](int q) {
+                const int t = nt - 1 - q;
+                return split_ok && q < nt && t >= np && bound_cells(g, tasks[t].D_lo, tasks[t].D_hi, s.tau) >= DENSE_CELLS;
+            };
+            int nd = 0;
+            for (int c0 = 0; c0 < nt; c0 += 32) nd += __popc(__ballot_sync(0xffffffffu, dense_at(c0 + lane)));
+            auto splits_at = [&](int q, int& seen) {
+                const bool d = dense_at(q);
+                const unsigned db = __ballot_sync(0xffffffffu, d);
+                const int rank = seen + __popc(db & ((1u << lane) - 1u));
+                seen += __popc(db);
+                return q < nt ? (d ? fill_splits(g, nt * g.n_tiles, nd, rank) : 1) : 0;
+            };
             int run = 0, base = 0;
-            int total = 0;
+            int total = 0, seen = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {
-                const int q = c0 + lane;
-                const int c = q < nt ? max(1, min(cap, tasks[nt - 1 - q].splits)) : 0;
+                const int c = splits_at(c0 + lane, seen);
                 total += __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
             }
             if (lane == 0) base = atomicAdd(&sch->n_jobs[par ^ 1], total);
             base = __shfl_sync(0xffffffffu, base, 0);
+            seen = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {
                 const int q = c0 + lane;
                 const int t = nt - 1 - q;
-                const int c = q < nt ? max(1, min(cap, tasks[t].splits)) : 0;
+                const int c = splits_at(q, seen);
                 const int incl = warp_incl_scan(c);
                 for (int k = 0; k < c; k++) {
                     Job j;
