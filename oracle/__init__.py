@@ -25,6 +25,8 @@ What each function follows (paper: McLeod et al., arXiv 2209.13168):
 
 Every function is pinned by tests/test_oracle_*.py against closed forms,
 invariants and brute force; none is marked "parity unpinned".
+tests/test_oracle_mutants.py plants plausible mistakes in copies of
+oracle.c and checks that the pins catch each one.
 """
 import ctypes
 import os

@@ -87,6 +87,27 @@ def test_identity_warp_at_D0(oracle_lib):
         assert np.array_equal(img, hist(win, win.x.astype(np.int64), win.y.astype(np.int64)))
 
 
+def test_time_origin_is_the_window_start(oracle_lib):
+    # Sec. 3.3: a batch's times count from its start, so moving every t and
+    # t0 by the same amount changes nothing.  Times on a 2^-12 grid and
+    # t0 = 2 keep every t - t0 exact in binary32.
+    rng = np.random.default_rng(12)
+    W, H, n, tau = 33, 27, 250, 0.5
+    x = rng.integers(0, W, n).astype(np.int16)
+    y = rng.integers(0, H, n).astype(np.int16)
+    t = (rng.integers(0, 2048, n) / 4096.0).astype(np.float32)
+    a = O.Window(W, H, 16.0, 13.0, x, y, t, 0.0, tau)
+    b = O.Window(W, H, 16.0, 13.0, x, y, (t + np.float32(2.0)).astype(np.float32), 2.0, tau)
+    assert np.array_equal((b.t - np.float32(2.0)).astype(np.float32), t)
+    for D in (-0.8, 0.3, 1.2):
+        assert O.contrast(a, D)[:3] == O.contrast(b, D)[:3]
+        assert np.array_equal(O.warp_cells(a, D)[0], O.warp_cells(b, D)[0])
+    for lo, hi in ((-1.0, 1.0), (0.2, 0.3)):
+        assert O.bound(a, lo, hi)[:3] == O.bound(b, lo, hi)[:3]
+    ra, rb = O.solve(a, -1.0, 1.0, 1e-4, 0.0, 2), O.solve(b, -1.0, 1.0, 1e-4, 0.0, 2)
+    assert (ra["D_star"], ra["K_hat"], ra["nodes_expanded"]) == (rb["D_star"], rb["K_hat"], rb["nodes_expanded"])
+
+
 @pytest.mark.parametrize("D,g", [(1.0, 2), (1.5, 4)])
 def test_zoom_when_all_t_zero(oracle_lib, D, g):
     # t_i = 0 makes the warp a pure zoom about the FOE by g = 1/(1 - D tau);
@@ -225,10 +246,23 @@ def test_bound_rasterisation_matches_real_segment(oracle_lib):
         if not a < b:
             continue
         win = O.Window(W, H, fx, fy, [x], [y], [t], 0.0, tau)
-        Hb = O.bound(win, a, b, want_iwe=True)[3]
+        Kb, Sb, Nf, Hb = O.bound(win, a, b, want_iwe=True)
         s = lambda D: (1 - D * t) / (1 - D * tau)
         p0 = (fx + (x - fx) * s(a), fy + (y - fy) * s(a))
         p1 = (fx + (x - fx) * s(b), fy + (y - fy) * s(b))
+        # Eqs. (18)-(19) for one event: each covered pixel holds 1, so
+        # Sbar = L (the covered count), and N_full is 1 exactly when the
+        # whole segment lies in the frame (decided here in binary64, away
+        # from the frame's edges).
+        L = int(Hb.sum())
+        inside = [-0.5 + 1e-3 <= p[0] <= W - 0.5 - 1e-3 and -0.5 + 1e-3 <= p[1] <= H - 0.5 - 1e-3 for p in (p0, p1)]
+        outside = [not (-0.5 - 1e-3 <= p[0] <= W - 0.5 + 1e-3 and -0.5 - 1e-3 <= p[1] <= H - 0.5 + 1e-3)
+                   for p in (p0, p1)]
+        if all(inside):
+            assert Nf == 1, trial
+        if any(outside):
+            assert Nf == 0, trial
+        assert Sb == L and Kb == win.M * L - Nf, trial
         ts = np.linspace(0.0, 1.0, 20001)
         cx = np.floor(p0[0] + (p1[0] - p0[0]) * ts + 0.5).astype(int)
         cy = np.floor(p0[1] + (p1[1] - p0[1]) * ts + 0.5).astype(int)
@@ -273,6 +307,35 @@ def test_sweep_is_exhaustive_on_a_narrow_interval(oracle_lib):
     assert O.sweep_max(win2, float(lo), float(D[-1]))[0] == best
 
 
+def test_sweep_finds_a_sliver_next_to_a_breakpoint(oracle_lib):
+    # Two events in one pixel column whose warps share a pixel on only 4
+    # binary32 values of D, next to a real breakpoint: the binary32 warp
+    # changes pixel a few ulps away from the real crossing, so a sweep that
+    # only looked at breakpoints and the midpoints between them would miss
+    # the maximum.  Every binary32 D of the interval enumerated one by one.
+    win = O.Window(40, 8, 4.0, 4.0, [35, 35], [4, 4], [0.435791015625, 0.307373046875], 0.0, 0.5)
+    lo, hi = np.float32(-0.2872776687145233), np.float32(-0.287276953458786)
+    D = [lo]
+    while D[-1] < hi:
+        D.append(np.nextafter(D[-1], np.float32(1)))
+    K = [O.contrast(win, float(d))[0] for d in D]
+    best = max(K)
+    assert best == 4 * win.M - 4 and K.count(best) <= 4
+    assert O.sweep_max(win, float(lo), float(hi))[0] == best
+
+
+def test_grid_includes_its_upper_end(oracle_lib):
+    # The dense grid evaluates D_lo + j h and D_hi itself: on an interval
+    # that enters the two-event plateau of golden/two_event_plateau.json by
+    # less than one step, only the upper end finds the plateau's K.
+    g = json.load(open(os.path.join(GOLDEN, "two_event_plateau.json")))
+    win = O.Window(g["W"], g["H"], g["foe"][0], g["foe"][1], g["x"], g["y"], g["t"], 0.0, g["tau"])
+    hi = float(np.float32(g["plateau"][0] + 0.001))
+    lo = float(np.float32(hi - 0.0195))
+    K, D_at, n = O.grid_max(win, lo, hi, 0.01)
+    assert (K, D_at, n) == (4 * win.M - 4, hi, 3)
+
+
 @pytest.mark.parametrize("K_pop", [1, 3, 8])
 def test_bnb_agrees_with_brute_force(oracle_lib, K_pop):
     # Algorithm 1 returns a K it attained, and its certificate covers the
@@ -290,6 +353,31 @@ def test_bnb_agrees_with_brute_force(oracle_lib, K_pop):
         assert r["K_hat"] <= Kmax <= r["K_hat"] + r["gap_K"]
         assert Kgrid <= Kmax
         assert r["gap_K"] >= 0 and r["bound_gap"] >= 0
+        # the reported contrast is Eq. (13) at D*: the variance of its image
+        ux, uy = O.warp_cells(win, r["D_star"])
+        C = np.var(hist(win, ux, uy).astype(np.float64))
+        assert math.isclose(r["contrast"], C, rel_tol=1e-12, abs_tol=1e-15)
+
+
+@pytest.mark.parametrize("K_pop", [1, 4])
+def test_ties_follow_algorithm_1(oracle_lib, K_pop):
+    # One event 2 px right of the FOE at t = tau/2 stays in the frame for
+    # every D in [-1, 1] (its offset scales by 5/6 to 3/2), so C(D) is the
+    # same everywhere (K = M - 1) and every expanded centre ties the
+    # incumbent: with Algorithm 1's ">=" each replaces it, and D* is the
+    # last centre expanded.  Every child bound is at least M - 1 (the event
+    # covers a pixel and the segment stays in the frame), so the ">=" of the
+    # insertion queues every child: expanding the root queues both halves,
+    # [-1, 0] only tying the incumbent (its segment stays in pixel 18).
+    win = O.Window(32, 32, 16.0, 16.0, [18], [16], [0.25], 0.0, 0.5)
+    M = win.M
+    for D in (-1.0, -0.3, 0.0, 0.6, 1.0):
+        assert O.contrast(win, D)[0] == M - 1
+    assert O.bound(win, -1.0, 0.0)[0] == M - 1 and O.bound(win, 0.0, 1.0)[0] == 2 * M - 1
+    r = O.solve(win, -1.0, 1.0, 1e-4, 0.0, K_pop, trace_cap=4096)
+    assert r["nodes_expanded"] > 1 and r["K_hat"] == M - 1
+    assert r["D_star"] == r["trace"][-1][2] != 0.0
+    assert r["max_queue"] >= 2
 
 
 def test_pop_k_keeps_the_optimum(oracle_lib):

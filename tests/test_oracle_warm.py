@@ -196,6 +196,10 @@ def test_warm_map(oracle_lib):
         D, w = O.warm_map(0.12, k * math.log(2.0), tau)
         assert w == np.float32(np.float32(2.0 ** k) / np.float32(tau))
         assert D == np.float32(np.float32(0.12) / np.float32(tau))
+    for k in range(-12, 1):                       # the exponent rounds to nearest
+        assert O.warm_map(0.0, (k + 0.4) * math.log(2.0), tau)[1] == np.float32(np.float32(2.0 ** k) / np.float32(tau))
+        assert O.warm_map(0.0, (k + 0.6) * math.log(2.0), tau)[1] == np.float32(
+            np.float32(2.0 ** (k + 1)) / np.float32(tau))
     assert O.warm_map(0.0, 50.0, tau)[1] == np.float32(np.float32(2.0) / np.float32(tau))
     assert O.warm_map(0.0, -50.0, tau)[1] == np.float32(np.float32(2.0 ** -20) / np.float32(tau))
     assert O.warm_map(0.0, float("nan"), tau)[1] == np.float32(np.float32(2.0 ** -20) / np.float32(tau))
