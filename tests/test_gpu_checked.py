@@ -94,12 +94,14 @@ def test_normal_build_reports_no_checks():
 
 def test_checked_build_on_random_configurations():
     # the randomised parity cases (every knob, FOE on the frame's edges,
-    # polarity, start-of-window warp) on the checked build: each compares
-    # with the oracle and asserts that no index was out of range
+    # polarity, start-of-window warp; single windows and batches) on the
+    # checked build: each compares with the oracle and asserts that no index
+    # was out of range
     sys.path.insert(0, os.path.join(ROOT, "paper_2209_13168_gb300"))
     import _build
     env = dict(os.environ, DD_LIBRARY=_build.build(checked=True))
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_gpu_fuzz.py"), "-q", "-x",
-                        "-p", "no:cacheprovider"], env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_gpu_fuzz.py"),
+                        os.path.join(ROOT, "tests", "test_gpu_batch_fuzz.py"), "-q", "-x", "-p", "no:cacheprovider"],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    assert "40 passed" in r.stdout
+    assert "52 passed" in r.stdout
