@@ -1053,6 +1053,7 @@ __device__ __forceinline__ int rank_in(const Node* q, int n, const Node& e) {
 }
 
 constexpr int CTL_THREADS = 256;
+constexpr int Q_STAGE = 256;   // queued intervals staged in shared memory for the merge
 
 __device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
     unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
@@ -1089,6 +1090,8 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     __shared__ unsigned long long cells[3 * MAX_POP];
     __shared__ Node kids[2 * MAX_POP + 1];
     __shared__ Node sorted_kids[2 * MAX_POP + 1];
+    __shared__ Node q_stage[Q_STAGE];
+    __shared__ float2 bound_iv[3 * MAX_POP];      // the next round's bound tasks' intervals
     __shared__ int s_nk, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int w = blockIdx.x;
@@ -1256,23 +1259,29 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     const int stop = s_stop;
 
     if (!stop) {
-        // sort the new children, then merge them with the queued intervals
+        // sort the new children, then merge them with the queued intervals;
+        // a queue that fits is staged in shared memory first, so that the
+        // children's ranks are searched there instead of in global memory
+        const Node* src = (s.q_cur ? qb : qa) + s.q_start;
+        Node* dst = s.q_cur ? qa : qb;
+        const int a = s.q_n;
+        const bool staged = a <= Q_STAGE;
         for (int i = tid; i < nk; i += blockDim.x) {
             int r = 0;
             for (int j = 0; j < nk; j++) r += better(kids[j], kids[i]);
             sorted_kids[r] = kids[i];
         }
+        if (staged)
+            for (int i = tid; i < a; i += blockDim.x) q_stage[i] = src[i];
         __syncthreads();
-        const Node* src = (s.q_cur ? qb : qa) + s.q_start;
-        Node* dst = s.q_cur ? qa : qb;
-        const int a = s.q_n;
+        const Node* qs = staged ? q_stage : src;
         for (int i = tid; i < a; i += blockDim.x) {
-            const Node e = src[i];
+            const Node e = qs[i];
             dst[i + rank_in(sorted_kids, nk, e)] = e;
         }
         for (int j = tid; j < nk; j += blockDim.x) {
             const Node e = sorted_kids[j];
-            dst[j + rank_in(src, a, e)] = e;
+            dst[j + rank_in(qs, a, e)] = e;
         }
         __syncthreads();
         if (tid == 0) {
@@ -1366,6 +1375,8 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                         r.splits = 1;
                         tasks[t] = l;
                         tasks[t + 1] = r;
+                        bound_iv[t] = make_float2(p.lo, p.c);
+                        bound_iv[t + 1] = make_float2(p.c, p.hi);
                     } else {
                         p.t_left = p.t_right = -1;
                     }
@@ -1392,7 +1403,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             const int nt = s.n_tasks, np = s.n_pop;
             auto dense_at = [&](int q) {
                 const int t = nt - 1 - q;
-                return split_ok && q < nt && t >= np && bound_cells(g, tasks[t].D_lo, tasks[t].D_hi, s.tau) >= DENSE_CELLS;
+                return split_ok && q < nt && t >= np && bound_cells(g, bound_iv[t].x, bound_iv[t].y, s.tau) >= DENSE_CELLS;
             };
             int nd = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) nd += __popc(__ballot_sync(0xffffffffu, dense_at(c0 + lane)));
