@@ -82,6 +82,10 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
 // ------------------------------------------------------------------ ingest
 
 constexpr int INGEST_THREADS = 512;
+// Blocks per ingest chunk: each takes CHUNK / INGEST_SUB consecutive events,
+// so that a window of a few chunks still spreads over many SMs.
+constexpr int INGEST_SUB = 8;
+static_assert(CHUNK % INGEST_SUB == 0, "sub-chunks tile a chunk");
 constexpr int MAX_BINS = 4096;
 
 __device__ __forceinline__ bool event_ok(int xi, int yi, float ti, float tr, float tau, int W, int H) {
@@ -101,19 +105,29 @@ __device__ __forceinline__ int plane_of(const Geom& g, const WinIn& win, int64_t
     return g.planes > 1 && win.p[i] <= 0 ? 1 : 0;
 }
 
-// Block c counts chunk c of its window into a shared histogram of the
+// Events [i0, i1) of the sub-chunk that block b ingests: sub-chunk
+// b % INGEST_SUB of chunk b / INGEST_SUB, within that chunk's window.
+__device__ __forceinline__ void sub_chunk(const WinIn& win, int chunk, int sub, int64_t& i0, int64_t& i1) {
+    constexpr int SUB_EVENTS = CHUNK / INGEST_SUB;
+    i0 = min(win.n, (int64_t)(chunk - win.chunk0) * CHUNK + (int64_t)sub * SUB_EVENTS);
+    i1 = min(win.n, i0 + SUB_EVENTS);
+}
+
+// Block b counts its sub-chunk of its window into a shared histogram of the
 // window's bins, then adds it to the window's global counts.
 __global__ void __launch_bounds__(INGEST_THREADS) k_row_hist(Geom g, const WinIn* __restrict__ wins,
                                                              const int32_t* __restrict__ chunk_win,
                                                              int32_t* row_count, int32_t* err) {
     __shared__ int32_t h[MAX_BINS];
-    const int w = chunk_win[blockIdx.x];
+    const int chunk = blockIdx.x / INGEST_SUB;
+    const int w = chunk_win[chunk];
     const WinIn win = wins[w];
     const int bins = bins_of(g);
     const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
     for (int r = threadIdx.x; r < bins; r += blockDim.x) h[r] = 0;
     __syncthreads();
-    const int64_t i0 = (int64_t)(blockIdx.x - win.chunk0) * CHUNK, i1 = min(win.n, i0 + CHUNK);
+    int64_t i0, i1;
+    sub_chunk(win, chunk, blockIdx.x % INGEST_SUB, i0, i1);
     int bad = 0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int xi = win.x[i], yi = win.y[i];
@@ -172,21 +186,23 @@ __global__ void __launch_bounds__(1024) k_row_scan(int bins, const int32_t* row_
     if (threadIdx.x == 1023) row_off[bins] = excl;
 }
 
-// Scatter each valid event of chunk c to its bin (offsets within the
-// window); a block reserves one range per bin, so the global atomics are per
-// (block, bin).  Also stores the reciprocals of the event's offsets from the
-// FOE (used by the bound's cell walk).
+// Scatter each valid event of the block's sub-chunk to its bin (offsets
+// within the window); a block reserves one range per bin, so the global
+// atomics are per (block, bin).  Also stores the reciprocals of the event's
+// offsets from the FOE (used by the bound's cell walk).
 __global__ void __launch_bounds__(INGEST_THREADS) k_row_scatter(Geom g, const WinIn* __restrict__ wins,
                                                                 const int32_t* __restrict__ chunk_win,
                                                                 int32_t* cursor, Ev* __restrict__ out,
                                                                 float2* __restrict__ rcp) {
     __shared__ int32_t h[MAX_BINS];
     __shared__ int32_t base[MAX_BINS];
-    const int w = chunk_win[blockIdx.x];
+    const int chunk = blockIdx.x / INGEST_SUB;
+    const int w = chunk_win[chunk];
     const WinIn win = wins[w];
     const int bins = bins_of(g);
     const float bscale = __fdiv_rn((float)g.n_tb, win.tau);
-    const int64_t i0 = (int64_t)(blockIdx.x - win.chunk0) * CHUNK, i1 = min(win.n, i0 + CHUNK);
+    int64_t i0, i1;
+    sub_chunk(win, chunk, blockIdx.x % INGEST_SUB, i0, i1);
     int32_t* cur = cursor + (size_t)w * bins;
     Ev* o = out + win.ev_off;
     float2* rc = rcp + win.ev_off;
@@ -232,9 +248,10 @@ cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_window
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(err, 0, sizeof(int32_t) * (size_t)n_windows, s);
     if (e != cudaSuccess) return e;
-    if (n_chunks > 0) k_row_hist<<<n_chunks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, row_count, err);
+    const unsigned blocks = (unsigned)n_chunks * INGEST_SUB;
+    if (n_chunks > 0) k_row_hist<<<blocks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, row_count, err);
     k_row_scan<<<n_windows, 1024, 0, s>>>(bins, row_count, row_off, cursor);
-    if (n_chunks > 0) k_row_scatter<<<n_chunks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, cursor, out, rcp);
+    if (n_chunks > 0) k_row_scatter<<<blocks, INGEST_THREADS, 0, s>>>(g, wins_dev, chunk_win_dev, cursor, out, rcp);
     return cudaGetLastError();
 }
 
