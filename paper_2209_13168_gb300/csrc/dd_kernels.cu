@@ -1108,6 +1108,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     __shared__ Node kids[2 * MAX_POP + 1];
     __shared__ Node sorted_kids[2 * MAX_POP + 1];
     __shared__ Node q_stage[Q_STAGE];
+    __shared__ Node q_head[MAX_POP];               // the merged queue's first entries, for the dequeue
     __shared__ float2 bound_iv[3 * MAX_POP];      // the next round's bound tasks' intervals
     __shared__ int s_nk, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1283,10 +1284,18 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         Node* dst = s.q_cur ? qa : qb;
         const int a = s.q_n;
         const bool staged = a <= Q_STAGE;
-        for (int i = tid; i < nk; i += blockDim.x) {
+        // A child's rank among the children (they are distinct: popped
+        // intervals are disjoint) counted by `per` threads, each over every
+        // per-th child, summed within the thread group.
+        int per = 1;
+        while (per < 32 && 2 * per * nk <= (int)blockDim.x) per *= 2;
+        for (int base = 0; base < nk * per; base += blockDim.x) {
+            const int i = (base + tid) / per, part = (base + tid) % per;
             int r = 0;
-            for (int j = 0; j < nk; j++) r += better(kids[j], kids[i]);
-            sorted_kids[r] = kids[i];
+            if (i < nk)
+                for (int j = part; j < nk; j += per) r += better(kids[j], kids[i]);
+            for (int o = per / 2; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (i < nk && part == 0) sorted_kids[r] = kids[i];
         }
         if (staged)
             for (int i = tid; i < a; i += blockDim.x) q_stage[i] = src[i];
@@ -1294,11 +1303,15 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         const Node* qs = staged ? q_stage : src;
         for (int i = tid; i < a; i += blockDim.x) {
             const Node e = qs[i];
-            dst[i + rank_in(sorted_kids, nk, e)] = e;
+            const int at = i + rank_in(sorted_kids, nk, e);
+            dst[at] = e;
+            if (at < MAX_POP) q_head[at] = e;
         }
         for (int j = tid; j < nk; j += blockDim.x) {
             const Node e = sorted_kids[j];
-            dst[j + rank_in(qs, a, e)] = e;
+            const int at = j + rank_in(qs, a, e);
+            dst[at] = e;
+            if (at < MAX_POP) q_head[at] = e;
         }
         __syncthreads();
         if (tid == 0) {
@@ -1311,7 +1324,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     }
 
     if (wid == 0) {
-        const Node* q = s.q_cur ? qb : qa;
+        const Node* q = q_head;                   // the first entries of the queue just merged
         int np = 0;
         if (!stop) {                              // dequeue up to K_pop intervals
             const i128 K0 = s.K_hat, gK = s.gamma_K;
