@@ -1288,7 +1288,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         // intervals are disjoint) counted by `per` threads, each over every
         // per-th child, summed within the thread group.
         int per = 1;
-        while (per < 32 && 2 * per * nk <= (int)blockDim.x) per *= 2;
+        while (nk > 32 && per < 32 && 2 * per * nk <= (int)blockDim.x) per *= 2;
         for (int base = 0; base < nk * per; base += blockDim.x) {
             const int i = (base + tid) / per, part = (base + tid) % per;
             int r = 0;
@@ -1450,7 +1450,14 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                 const int c = splits_at(c0 + lane, seen);
                 total += __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
             }
-            if (lane == 0) base = atomicAdd(&sch->n_jobs[par ^ 1], total);
+            if (lane == 0) {
+                if (n_windows == 1) {             // the only block: the list is its own
+                    sch->n_jobs[par ^ 1] = total;
+                    base = 0;
+                } else {
+                    base = atomicAdd(&sch->n_jobs[par ^ 1], total);
+                }
+            }
             base = __shfl_sync(0xffffffffu, base, 0);
             seen = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {
@@ -1476,7 +1483,12 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     } // s.phase != PH_DONE at entry
     __syncthreads();
     if (tid == 0 && phase_out) phase_out[w] = s.phase;
-    if (tid == 0) {
+    if (tid == 0 && n_windows == 1) {             // the only block is the last: no ticket
+        const int active = s.phase != PH_DONE ? 1 : 0;
+        sch->running = active;
+        sch->round += 1;
+        if (use_loop) cudaGraphSetConditional(loop, active ? 1u : 0u);
+    } else if (tid == 0) {
         __threadfence();
         if (s.phase != PH_DONE) atomicAdd(&sch->active, 1);
         if (atomicAdd(&sch->ticket, 1) == n_windows - 1) {    // the last block of the round
