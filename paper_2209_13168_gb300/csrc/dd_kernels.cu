@@ -1095,7 +1095,7 @@ __device__ __forceinline__ i128 warp_max_i128(i128 v) {
 // sorted in priority order in one of two buffers: insertion is a parallel
 // merge into the other buffer, a dequeue takes a prefix.  The last block to
 // finish counts the windows still searching, advances the round and sets the
-// graph loop condition.
+// graph loop condition (with one window, its block does so directly).
 __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windows, SolveState* st_all,
                                                         Node* queues, Task* tasks_all, int32_t task_stride,
                                                         Partial* part_all, const int32_t* err_all,
