@@ -150,6 +150,15 @@ MUTANTS = [
      "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;", "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B8ull;"),
     ("resample_clamp", "the far-edge clamp one pixel short",
      "if (cx > W2 - 1) cx = W2 - 1;", "if (cx > W2 - 2) cx = W2 - 2;"),
+    # the binary64 diagnostic
+    ("fp64_counts_nothing", "the binary64 diagnostic never counts",
+     "if (ux != cell(w->foe_x, dx, s) || uy != cell(w->foe_y, dy, s)) bad++;",
+     "if (0) bad++;"),
+    ("fp64_reference_tau", "the binary64 warp ignores the reference time",
+     "double Dd = D, tau = w->t_ref;", "double Dd = D, tau = w->tau;"),
+    ("fp64_no_half", "the binary64 pixel without the half pixel",
+     "int64_t ux = (int64_t)floor((double)w->foe_x + X * sd + 0.5);",
+     "int64_t ux = (int64_t)floor((double)w->foe_x + X * sd);"),
     # argument checks
     ("accepts_late_events", "events after the window's end accepted",
      "if (!isfinite(w->t[i]) || !(ti >= 0.0f) || !(ti <= w->tau)) return OR_ERR_ARG;",

@@ -431,10 +431,34 @@ def test_divergence_retrieval(oracle_lib):
     assert math.isclose(r["D_end"], -paper, rel_tol=1e-6)
 
 
-def test_fp64_disagreement_is_rare(oracle_lib):
-    win = O.Window.of(window_config1())
-    for D in (0.0, 0.2, -0.5, 0.9):
-        assert O.fp64_disagreements(win, D) <= 4
+def _fp64_recount(win, D):
+    # the same warp in binary64 with numpy (times relative to t0 as binary32
+    # differences, the FOE and D as their binary32 values), against the
+    # oracle's binary32 cells
+    c = win.c
+    ux, uy = O.warp_cells(win, D)
+    D64 = float(np.float32(D))
+    ti = (win.t - np.float32(c.t0)).astype(np.float32).astype(np.float64)
+    sd = (1.0 - D64 * ti) / (1.0 - D64 * float(c.t_ref))
+    fx, fy = float(c.foe_x), float(c.foe_y)
+    ux64 = np.floor(fx + (win.x.astype(np.float64) - fx) * sd + 0.5).astype(np.int64)
+    uy64 = np.floor(fy + (win.y.astype(np.float64) - fy) * sd + 0.5).astype(np.int64)
+    return int(((ux64 != ux) | (uy64 != uy)).sum())
+
+
+@pytest.mark.parametrize("t_ref", [None, 0.0])
+def test_fp64_disagreements(oracle_lib, t_ref):
+    # The diagnostic counts the events whose binary64 warp lands in another
+    # pixel than the binary32 warp: a numpy recount agrees at every D of a
+    # sweep, the count is nonzero somewhere (events near pixel borders), and
+    # it stays rare (a few events of 4,000).
+    win = O.Window.of(window_config1(), t_ref=t_ref)
+    counts = []
+    for D in np.linspace(-1.0, 1.0, 201):
+        n = O.fp64_disagreements(win, float(np.float32(D)))
+        assert n == _fp64_recount(win, float(np.float32(D))), float(D)
+        counts.append(n)
+    assert sum(counts) > 0 and max(counts) <= 4
 
 
 # ------------------------------------------------------------- arguments
