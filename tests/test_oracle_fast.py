@@ -42,6 +42,18 @@ def test_half_resolution_is_nearest_coarse_pixel(oracle_lib):
     assert (r.c.foe_x, r.c.foe_y) == (15.75, 11.5)
 
 
+def test_the_foe_maps_like_a_frame_point(oracle_lib):
+    # An anisotropic resize (640x480 -> 160x240: a quarter of the columns,
+    # half the rows): an event on an integer FOE lands in the coarse pixel
+    # nearest the coarse FOE, on each axis separately, so that the radial
+    # geometry of Eq. (11) carries over to the coarse frame.
+    for fx, fy in ((320.0, 240.0), (100.0, 400.0), (600.0, 30.0)):
+        w = window(640, 480, (fx, fy), [int(fx)], [int(fy)], [0.25])
+        r = O.resample(w, 160, 240, 1.0, 0)
+        assert abs(r.c.foe_x - r.x[0]) <= 0.5 and abs(r.c.foe_y - r.y[0]) <= 0.5, (fx, fy)
+        assert (r.c.foe_x, r.c.foe_y) == (fx / 4.0, fy / 2.0)
+
+
 def test_clamp_at_the_far_edge(oracle_lib):
     # W = 5 -> W2 = 2: k = 0.4 (binary32); x = 4 maps to floor(2.1) = 2, clamped to 1.
     w = window(5, 5, (2.0, 2.0), [0, 1, 2, 3, 4], [4, 3, 2, 1, 0], np.zeros(5, np.float32))

@@ -150,6 +150,14 @@ MUTANTS = [
      "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;", "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B8ull;"),
     ("resample_clamp", "the far-edge clamp one pixel short",
      "if (cx > W2 - 1) cx = W2 - 1;", "if (cx > W2 - 2) cx = W2 - 2;"),
+    ("warm_piece_lower_unclamped", "the lower cut not clamped to the domain",
+     "if (!(a >= D_lo)) a = D_lo;", "if (0) a = D_lo;"),
+    ("loss_no_width_term", "the loss without its log half-width term",
+     "loss += 0.5 * q * e * e + o[1];", "loss += 0.5 * q * e * e;"),
+    ("feature_radius_x_only", "the largest radius from the x extent alone",
+     "const float R2 = cx * cx + cy * cy;", "const float R2 = cx * cx;"),
+    ("resample_foe_wrong_axis", "the coarse FOE's row scaled by the column ratio",
+     "*fy2 = w->foe_y * ((float)H2 / (float)w->H);", "*fy2 = w->foe_y * ((float)W2 / (float)w->W);"),
     # the binary64 diagnostic
     ("fp64_counts_nothing", "the binary64 diagnostic never counts",
      "if (ux != cell(w->foe_x, dx, s) || uy != cell(w->foe_y, dy, s)) bad++;",
