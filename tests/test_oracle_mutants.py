@@ -168,6 +168,17 @@ MUTANTS = [
      "int64_t ux = (int64_t)floor((double)w->foe_x + X * sd + 0.5);",
      "int64_t ux = (int64_t)floor((double)w->foe_x + X * sd);"),
     # argument checks
+    ("rejects_far_foe", "an FOE on the frame's far edge rejected",
+     "w->foe_x > (float)w->W", "w->foe_x >= (float)w->W"),
+    ("rejects_domain_edge", "D tau = 3/4 rejected",
+     "return dt <= 0.75 && dt >= -64.0;", "return dt < 0.75 && dt >= -64.0;"),
+    ("accepts_late_t_ref", "a reference time after the window's end accepted",
+     "if (!(w->t_ref >= 0.0f) || !(w->t_ref <= w->tau)) return OR_ERR_ARG;",
+     "if (!(w->t_ref >= 0.0f)) return OR_ERR_ARG;"),
+    ("rejects_last_row", "the frame's last row rejected",
+     "w->y[i] < 0 || w->y[i] >= w->H)", "w->y[i] < 0 || w->y[i] >= w->H - 1)"),
+    ("rejects_window_end", "an event at the window's end rejected",
+     "!(ti >= 0.0f) || !(ti <= w->tau)) return OR_ERR_ARG;", "!(ti >= 0.0f) || !(ti < w->tau)) return OR_ERR_ARG;"),
     ("accepts_late_events", "events after the window's end accepted",
      "if (!isfinite(w->t[i]) || !(ti >= 0.0f) || !(ti <= w->tau)) return OR_ERR_ARG;",
      "if (!isfinite(w->t[i]) || !(ti >= 0.0f)) return OR_ERR_ARG;"),

@@ -476,6 +476,18 @@ def test_rejects_bad_arguments(oracle_lib):
     assert O.validate(O.Window(20, 20, 30.0, 10.0, [1], [2], [0.1], 0.0, 0.5), -1, 1) != 0  # FOE out
     assert O.validate(O.Window(20, 20, 10.0, 10.0, [20], [2], [0.1], 0.0, 0.5), -1, 1) != 0  # x = W
     assert O.validate(O.Window(20, 20, 10.0, 10.0, [3], [-1], [0.1], 0.0, 0.5), -1, 1) != 0  # y < 0
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [3], [20], [0.1], 0.0, 0.5), -1, 1) != 0  # y = H
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [3], [2], [0.1], 0.0, 0.5, 0.6), -1, 1) != 0  # t_ref > tau
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [3], [2], [0.1], 0.0, 0.5, -0.1), -1, 1) != 0  # t_ref < 0
+    assert O.validate(ok, -128.5, 1.0) != 0               # D tau < -64
+    # the boundaries themselves are inside: the FOE on the frame's corners,
+    # the last row and column, events at both ends of the window, D tau at
+    # 3/4 and -64, the warp to either end of the window
+    for fx, fy in ((0.0, 0.0), (20.0, 20.0)):
+        assert O.validate(O.Window(20, 20, fx, fy, [19, 0], [0, 19], [0.0, 0.5], 0.0, 0.5), -1, 1) == 0
+    assert O.validate(O.Window(20, 20, 10.0, 10.0, [1], [2], [2.5], 2.0, 0.5), -128.0, 1.5) == 0
+    for t_ref in (0.0, 0.5):
+        assert O.validate(O.Window(20, 20, 10.0, 10.0, [1], [2], [0.25], 0.0, 0.5, t_ref), -1, 1) == 0
     empty = O.Window(20, 20, 10.0, 10.0, [], [], [], 0.0, 0.5)
     assert O.contrast(empty, 0.3)[:3] == (0, 0, 0)
     r = O.solve(empty, -1.0, 1.0, 1e-4, 0.0, 1)
