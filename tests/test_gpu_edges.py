@@ -69,6 +69,25 @@ def test_largest_frame():
     check(w, [-1.0, 1.0], [-1.0, 0.349], [1.0, 0.351], want_iwe=False, solve_pop=0, max_splits=1)
 
 
+def test_the_ends_of_the_search_domain():
+    # D tau at both ends of the accepted domain, -64 and 3/4 (where the
+    # bound's widening is still proven to hold): keys and images at the ends,
+    # bounds reaching them, and a search whose interval ends at 3/4.
+    w = make_window(64, 48, 32.0, 24.0, 1500, 60, 300, 0.5, 0.5, 61)
+    assert np.float32(w.tau) == np.float32(0.5)
+    check(w, [-128.0, -1.0, 1.5], [-128.0, 1.25, 1.4999], [-127.0, 1.5, 1.5], solve_pop=0)
+    win = O.Window.of(w)
+    ev = dd.Events.of(w, device="cuda")
+    for pop in (1, 8):
+        ctx = dd.Context(w.W, w.H, w.foe_x, w.foe_y, pop_k=pop)
+        got = ctx.solve(ev, -2.0, 1.5, 1e-4, 0.0, trace_cap=4096)
+        want = O.solve(win, -2.0, 1.5, 1e-4, 0.0, pop, trace_cap=4096)
+        for k in KEYS:
+            assert got[k] == want[k], (k, pop)
+        assert got["trace"] == want["trace"]
+        ctx.close()
+
+
 def test_events_on_the_frame_edges_and_at_the_window_ends():
     w = make_window(64, 48, 31.5, 23.5, 2000, 80, 400, 0.3, 0.5, 51, t0=2.0)
     rng = np.random.default_rng(3)
