@@ -116,6 +116,15 @@ MUTANTS = [
      "r.D_end = (float)((double)D_hat / (1.0 + (double)D_hat * (double)w->tau));"),
     ("contrast_over_M", "the reported contrast K / M instead of K / M^2",
      "r.contrast = (double)K_hat / ((double)M * (double)M);", "r.contrast = (double)K_hat / (double)M;"),
+    ("cells_skip_root_centre", "the root centre's image left out of the cell count",
+     "        cells += N;\n        node root = {D_lo, D_hi, 0};", "        node root = {D_lo, D_hi, 0};"),
+    ("bound_cells_one_child", "one child's covered cells left out of the bound count",
+     "            b.kb = eval_bound(w, b.lo, b.hi, img, &S, &nf, &nc);\n            cells += nc;\n            bcells += nc;",
+     "            b.kb = eval_bound(w, b.lo, b.hi, img, &S, &nf, &nc);\n            cells += nc;"),
+    ("bound_evals_one_per_split", "one bound evaluation counted per split",
+     "            r.bound_evals += 2;", "            r.bound_evals += 1;"),
+    ("event_warps_points_only", "event-warps counted for centres only",
+     "        r.event_warps = w->n * (r.point_evals + r.bound_evals);", "        r.event_warps = w->n * r.point_evals;"),
     # brute force
     ("sweep_no_neighbours", "the sweep skips the binary32 neighbours of each breakpoint",
      "for (int u = 0; u < 4; u++) {", "for (int u = 0; u < 0; u++) {"),

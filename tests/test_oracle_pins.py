@@ -360,6 +360,32 @@ def test_bnb_agrees_with_brute_force(oracle_lib, K_pop):
 
 
 @pytest.mark.parametrize("K_pop", [1, 4])
+def test_search_counters_rebuilt_from_the_trace(oracle_lib, K_pop):
+    # The search's work counters, recounted from its trace: the root's centre
+    # and bound, then per expanded interval its centre and, unless it is a
+    # leaf, its two halves' bounds, each re-evaluated on its own; the cells
+    # are the in-frame events of each centre's image (Eq. 12) and the
+    # covered cells of each bound's image (Eq. 16).
+    win = tiny(77, W=31, H=23, n=150)
+    lo, hi = -1.0, 1.0
+    r = O.solve(win, lo, hi, 1e-4, 0.0, K_pop, trace_cap=100000)
+    tr = r["trace"]
+    assert len(tr) == r["trace_len"] == r["nodes_expanded"]
+    c0 = float(np.float32(np.float32(lo) + np.float32(0.5) * (np.float32(hi) - np.float32(lo))))
+    points, bounds = [c0] + [t[2] for t in tr], [(lo, hi)]
+    for D_lo, D_hi, D_c, leaf, _, _ in tr:
+        if not leaf:
+            bounds += [(D_lo, D_c), (D_c, D_hi)]
+    assert (r["point_evals"], r["bound_evals"]) == (len(points), len(bounds))
+    assert r["event_warps"] == win.x.size * (len(points) + len(bounds))
+    pc = sum(int(O.contrast(win, D)[2]) for D in points)
+    bc = sum(int(O.bound(win, a, b, want_iwe=True)[3].sum()) for a, b in bounds)
+    assert (r["cell_increments"], r["bound_increments"]) == (pc + bc, bc)
+    if K_pop == 1:
+        assert r["rounds"] == r["nodes_expanded"]
+
+
+@pytest.mark.parametrize("K_pop", [1, 4])
 def test_ties_follow_algorithm_1(oracle_lib, K_pop):
     # One event 2 px right of the FOE at t = tau/2 stays in the frame for
     # every D in [-1, 1] (its offset scales by 5/6 to 3/2), so C(D) is the
