@@ -69,7 +69,7 @@ static float warp_s(float D, float ti, float g) {
     float a = 1.0f - D * ti;
     return a * g;
 }
-/* Eq. (12): "lies in pixel u".  Pixel u covers [u - 1/2, u + 1/2), so
+/* Eq. (12): the pixel a warped event falls in.  Pixel u covers [u - 1/2, u + 1/2), so
  * integer event coordinates are pixel centres (reading; the paper is silent). */
 static int32_t cell(float foe, float d, float s) {
     float p = foe + d * s;
