@@ -1,5 +1,6 @@
 """bench.py keeps its output contract: one JSON line with the required keys
-(the reference arm here, on CPU; our arm in tests/test_gpu_bench_contract.py)."""
+(the reference arm here, on CPU; our arm in tests/test_gpu_bench_contract.py),
+and a clock record taken from the samples of the timed region."""
 import json
 import os
 import subprocess
@@ -22,3 +23,29 @@ def test_reference_arm_line():
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
     assert "workload" in out["config"]
+
+
+def test_clock_samples_are_filtered_and_parsed():
+    # The clock record of the bench line: only samples inside the timed
+    # region (plus one sampling period), the median SM clock, and the
+    # throttle reasons reported Active in any of them; malformed lines skipped.
+    import bench
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.Clocks(0)
+    c.p = FakeProc()
+    row = lambda sm, hw="Not Active", pc="Not Active": "0, %d, 2070, 900.0, 0x0, %s, Not Active, Not Active, %s" % (
+        sm, hw, pc)
+    c.lines = [(0.5, row(1000, hw="Active")),          # before the timed region: ignored
+               (1.0, row(2070)), (1.1, row(1995, pc="Active")), (1.2, row(2070)), (1.25, "garbage"),
+               (1.3, row(2040)), (2.5, row(900, hw="Active"))]   # after it: ignored
+    out = c.stop(1.0, 1.3)
+    assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    c.lines = [(5.0, row(1900))]                       # nothing inside: every sample is used
+    assert bench.Clocks.stop(c, 1.0, 1.3)["samples"] == 1
