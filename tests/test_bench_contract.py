@@ -49,3 +49,26 @@ def test_clock_samples_are_filtered_and_parsed():
     assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
     c.lines = [(5.0, row(1900))]                       # nothing inside: every sample is used
     assert bench.Clocks.stop(c, 1.0, 1.3)["samples"] == 1
+
+
+def test_profile_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
+    # roofline.traffic comes from the committed ncu summary only while the
+    # evaluation kernel's source (comments and blank lines aside) is the one
+    # that was profiled.
+    import shutil
+    import bench
+    src = tmp_path / "paper_2209_13168_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for f in ("dd_kernels.cu", "dd_internal.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_2209_13168_gb300", "csrc", f), src / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_hash()
+    (tmp_path / "profiles" / "k_eval_config2.json").write_text(
+        json.dumps({"kernel_source_sha256": h, "dram_bytes_per_launch": 123.0}))
+    assert bench.profile_traffic(bench.kernel_hash()) == 123.0
+    k = src / "dd_kernels.cu"
+    k.write_text(k.read_text() + "\n// a comment\n\n")             # comments do not count
+    assert bench.kernel_hash() == h
+    k.write_text(k.read_text() + "static int changed;\n")           # code does
+    assert bench.kernel_hash() != h and bench.profile_traffic(bench.kernel_hash()) is None
