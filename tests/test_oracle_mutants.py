@@ -65,7 +65,7 @@ MUTANTS = [
     ("polarity_one_plane", "every event put in the first polarity plane",
      "return (w->p && w->p[i] <= 0) ? 1 : 0;", "return 0;"),
     ("polarity_planes_swapped", "the polarity planes swapped",
-     "return (w->p && w->p[i] <= 0) ? 1 : 0;", "return (w->p && w->p[i] <= 0) ? 0 : 1;"),
+     "return (w->p && w->p[i] <= 0) ? 1 : 0;", "return w->p ? (w->p[i] <= 0 ? 0 : 1) : 0;"),
     # Eqs. (14)-(19): the bound
     ("no_widen_up", "the scale interval not widened upwards",
      "static const float WIDEN_UP = 1.0f + 0x1p-19f;", "static const float WIDEN_UP = 1.0f;"),
@@ -130,6 +130,9 @@ MUTANTS = [
      "for (int u = 0; u < 4; u++) {", "for (int u = 0; u < 0; u++) {"),
     ("sweep_breakpoint_sign", "the breakpoints' denominator with the wrong sign",
      "double den = d * ti - c * tau;", "double den = d * ti + c * tau;"),
+    ("grid_double_step", "the grid steps twice as far as asked",
+     "float D = j <= steps ? (float)((double)D_lo + (double)j * (double)h) : D_hi;",
+     "float D = j <= steps ? (float)((double)D_lo + 2.0 * (double)j * (double)h) : D_hi;"),
     ("grid_skips_upper_end", "the grid stops short of its last point",
      "for (int64_t j = 0; j <= steps + 1; j++) {", "for (int64_t j = 0; j < steps; j++) {"),
     # the learned warm start

@@ -324,6 +324,26 @@ def test_sweep_finds_a_sliver_next_to_a_breakpoint(oracle_lib):
     assert O.sweep_max(win, float(lo), float(hi))[0] == best
 
 
+def test_grid_is_its_definition(oracle_lib):
+    # The dense grid: the contrast at D_lo + j h (binary64, rounded to
+    # binary32) for j = 0, 1, ... while it stays within [D_lo, D_hi], plus
+    # D_hi itself; the largest key and the smallest D attaining it.
+    # The two-event plateau of golden/two_event_plateau.json, [6/11, 10/13),
+    # is first reached at an odd grid point from 0.45 in steps of 0.1.
+    g = json.load(open(os.path.join(GOLDEN, "two_event_plateau.json")))
+    plateau = O.Window(g["W"], g["H"], g["foe"][0], g["foe"][1], g["x"], g["y"], g["t"], 0.0, g["tau"])
+    for win, lo, hi, h in ((tiny(31, W=27, H=21, n=90), -0.75, 0.5, 0.0625), (plateau, 0.45, 0.9, 0.1)):
+        steps = int(math.floor((np.float64(np.float32(hi)) - np.float64(np.float32(lo))) /
+                               np.float64(np.float32(h))))
+        Ds = [float(np.float32(np.float64(np.float32(lo)) + j * np.float64(np.float32(h)))) for j in range(steps + 1)]
+        Ds.append(float(np.float32(hi)))
+        Ks = [O.contrast(win, D)[0] for D in Ds]
+        best = max(Ks)
+        K, D_at, n = O.grid_max(win, lo, hi, h)
+        assert (K, D_at, n) == (best, min(D for D, k in zip(Ds, Ks) if k == best), len(Ds))
+    assert K == 4 * plateau.M - 4 and abs(D_at - 0.55) < 1e-6
+
+
 def test_grid_includes_its_upper_end(oracle_lib):
     # The dense grid evaluates D_lo + j h and D_hi itself: on an interval
     # that enters the two-event plateau of golden/two_event_plateau.json by
