@@ -237,6 +237,21 @@ def _ptr(a):
     return a.ctypes.data
 
 
+def _host_ints(a, dtype, name):
+    """A host array of integers as a contiguous array of `dtype`; values that
+    are not integers or do not fit are an error, not a silent cast."""
+    a = np.asarray(a)
+    if a.ndim != 1:
+        raise ValueError("%s: a 1-D array is required" % name)
+    if a.dtype != dtype and a.size:
+        info = np.iinfo(dtype)
+        if a.dtype.kind not in "iu" and not np.all(np.equal(np.mod(a, 1), 0)):
+            raise ValueError("%s: integer values are required" % name)
+        if a.min() < info.min or a.max() > info.max:
+            raise ValueError("%s: values outside %s" % (name, np.dtype(dtype).name))
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
 class Events:
     """dd_events over numpy arrays (host) or torch CUDA tensors (device).
 
@@ -244,20 +259,28 @@ class Events:
 
     def __init__(self, x, y, t, t0, tau, p=None):
         """p: int8 polarities (same kind of memory as x/y/t), read by a
-        context with polarity=1; None otherwise."""
+        context with polarity=1; None otherwise.  Host arrays are converted
+        (coordinates must be integers within int16, polarities within int8);
+        CUDA tensors must already have the ABI's types."""
         dev = hasattr(x, "is_cuda") and x.is_cuda
         if dev:
             import torch
-            assert x.dtype == torch.int16 and y.dtype == torch.int16 and t.dtype == torch.float32
-            assert x.is_contiguous() and y.is_contiguous() and t.is_contiguous()
-            assert p is None or (p.is_cuda and p.dtype == torch.int8 and p.is_contiguous())
+            want = ((x, torch.int16, "x"), (y, torch.int16, "y"), (t, torch.float32, "t")) + \
+                (() if p is None else ((p, torch.int8, "p"),))
+            for a, dt, name in want:
+                if not (hasattr(a, "is_cuda") and a.is_cuda and a.dtype == dt and a.dim() == 1 and a.is_contiguous()):
+                    raise TypeError("%s: a contiguous 1-D CUDA tensor of %s is required" % (name, dt))
         else:
-            x = np.ascontiguousarray(x, dtype=np.int16)
-            y = np.ascontiguousarray(y, dtype=np.int16)
+            x = _host_ints(x, np.int16, "x")
+            y = _host_ints(y, np.int16, "y")
             t = np.ascontiguousarray(t, dtype=np.float32)
-            p = None if p is None else np.ascontiguousarray(p, dtype=np.int8)
-        self.x, self.y, self.t, self.p = x, y, t, p
+            if t.ndim != 1:
+                raise ValueError("t: a 1-D array is required")
+            p = None if p is None else _host_ints(p, np.int8, "p")
         n = int(x.shape[0])
+        if any(int(a.shape[0]) != n for a in (y, t) + (() if p is None else (p,))):
+            raise ValueError("x, y, t (and p) must have the same length")
+        self.x, self.y, self.t, self.p = x, y, t, p
         self.c = dd_events(_ptr(x) if n else None, _ptr(y) if n else None, _ptr(t) if n else None, n,
                            float(t0), float(tau), 1 if dev else 0, _ptr(p) if (n and p is not None) else None)
 

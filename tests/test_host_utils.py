@@ -38,3 +38,24 @@ def test_autotune_lookup_picks_the_nearest_bucket(tmp_path, monkeypatch):
     assert at.lookup(1280, 720, 100_000, "single", str(p)) is None                # no such geometry
     monkeypatch.setattr(at, "gpu_name", lambda: "GPU_Z")
     assert at.lookup(640, 480, 100_000, "single", str(p)) is None                 # another GPU
+
+
+def test_events_marshalling_rejects_what_it_cannot_pass():
+    # The C side reads n entries of every array: lengths must agree, and
+    # values the ABI's types cannot hold are an error rather than a cast.
+    import pytest
+    ok = dd.Events([1, 2], [3, 4], [0.1, 0.2], 0.0, 0.5)
+    assert ok.x.dtype == np.int16 and ok.t.dtype == np.float32 and ok.c.n == 2
+    assert dd.Events(np.array([1.0, 2.0]), [3, 4], [0.1, 0.2], 0.0, 0.5).x.tolist() == [1, 2]
+    assert dd.Events([], [], [], 0.0, 0.5).c.n == 0
+    for bad in (([1, 2], [3], [0.1, 0.2]),             # a short array
+                ([1, 2], [3, 4], [0.1]),
+                ([1.5, 2], [3, 4], [0.1, 0.2]),        # not a pixel coordinate
+                ([40000, 2], [3, 4], [0.1, 0.2]),      # beyond int16
+                ([[1, 2]], [[3, 4]], [0.1, 0.2])):     # not 1-D
+        with pytest.raises(ValueError):
+            dd.Events(*bad, 0.0, 0.5)
+    with pytest.raises(ValueError):
+        dd.Events([1], [2], [0.1], 0.0, 0.5, p=[300])   # beyond int8
+    with pytest.raises(ValueError):
+        dd.Events([1, 2], [3, 4], [0.1, 0.2], 0.0, 0.5, p=[1])
