@@ -38,18 +38,21 @@ METRIC = "exact divergence solves/sec"
 UNIT = "solves/s"
 
 # Algorithmic ALU operations per unit of work of the IWE kernel (binary32 or
-# int32 lane operations):
-#   point event-warp  12: D*t, 1-., .*g; per axis d*s, +FOE, +1/2, floor; the
-#                         in-frame test; one increment
-#   bound event       26: two scales (6), two widenings (2), four end cells
-#                         (4 x 4), the full test (2)
-#   bound increment   10: the major cell's two s-boundaries (4), the minor
-#                         cells at its two ends (amortised, 5), one increment
-OPS_POINT_WARP = 12
-OPS_BOUND_EVENT = 26
-OPS_BOUND_INCREMENT = 10
-SM_COUNT = 152
-LANES_PER_SM = 128
+# int32 lane operations), as the measurement plan counts them:
+#   point event-warp   8: D*t, 1-., .*g; per axis d*s, +FOE (the rounding
+#                         to a cell not counted)
+#   bound event       20: two scales (6), two widenings (2), four end cells
+#                         (4 x 3), the full test
+#   bound increment    4: the major cell's two s-boundaries, one increment
+OPS_POINT_WARP = 8
+OPS_BOUND_EVENT = 20
+OPS_BOUND_INCREMENT = 4
+# A finer count of the same work, reported beside it: +1/2 and the floor of
+# every cell, the in-frame test and the increment of a point (12); the full
+# test's comparisons (26); the minor cells at a major cell's two ends,
+# amortised (10).
+OPS_FINE = (12, 26, 10)
+LANES_PER_SM = 128      # binary32 / int32 lanes of one sm_100-family SM (4 x 32)
 
 
 def env_int(k, d):
@@ -57,6 +60,30 @@ def env_int(k, d):
         return int(os.environ.get(k, d))
     except ValueError:
         return d
+
+
+def nvsmi_gpu_id(uuid=None, visible=None, local=0):
+    """The `nvidia-smi -i` argument naming the GPU this process runs on.
+    nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES, so
+    the device is named by its UUID (from the CUDA device properties); else
+    by the CUDA_VISIBLE_DEVICES entry it maps to; else by its index."""
+    if uuid:
+        u = str(uuid)
+        return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    if visible:
+        entries = [x.strip() for x in visible.split(",") if x.strip()]
+        if 0 <= local < len(entries):
+            return entries[local]
+    return str(local)
+
+
+def device_uuid(local):
+    """The UUID torch reports for CUDA device `local` (None if unavailable)."""
+    try:
+        import torch
+        return getattr(torch.cuda.get_device_properties(local), "uuid", None)
+    except Exception:
+        return None
 
 
 class Clocks:
@@ -298,7 +325,7 @@ def run_extras(dd, torch):
                                 "noise 10-40%%, tau 0.1-0.5 s; one batched solve" % n_mean,
                     "solves_per_s": len(ws) / dt, "ms_per_batch": dt * 1e3, "status": rc,
                     "nodes_expanded": sum(r["nodes_expanded"] for r in res),
-                    "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}}
+                    "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits", "fuse_span")}}
     ctx.close()
     # the same windows through the single-window solver, one call each
     ctx = dd.Context.tuned(640, 480, 320.0, 240.0, n_mean, mode="single")
@@ -311,7 +338,7 @@ def run_extras(dd, torch):
     dt_loop = time.perf_counter() - t0
     out["batch"]["loop_solves_per_s"] = len(ws) / dt_loop
     out["batch"]["batch_over_loop"] = dt_loop / dt
-    out["batch"]["loop_knobs"] = {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}
+    out["batch"]["loop_knobs"] = {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits", "fuse_span")}
     ctx.close()
     del ws, evs
     # learned warm start vs plain on held-out windows
@@ -404,7 +431,7 @@ def run_ours(args):
     # ---- timed region: device-resident inputs, L2 flushed before each step
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = Clocks(local)
+    clocks = Clocks(nvsmi_gpu_id(device_uuid(local), os.environ.get("CUDA_VISIBLE_DEVICES"), local))
     clocks.start()
     if dist:
         dist.barrier()
@@ -456,23 +483,36 @@ def run_ours(args):
                "h2d_bytes_per_step": sh["h2d_bytes"] // args.steps,
                "d2h_bytes_per_step": sh["d2h_bytes"] // args.steps}
 
-    # ---- roofline of the dominant kernel (IWE evaluation), separate pass
+    # ---- roofline of the dominant kernel (IWE evaluation), separate pass:
+    # the same solve with its rounds launched from the host one per poll, each
+    # evaluation launch bracketed by CUDA events on the solver's stream, so
+    # every timed launch is a round with work (launch k = round k)
     ctx.set_timing(True)
-    ctx.reset_stats()
     reps = 5
+    per_round = []
     for _ in range(reps):
+        ctx.reset_stats()
         rr = ctx.solve(ev)
-    sr = ctx.stats()
+        per_round.append(ctx.launch_times())
     ctx.set_timing(False)
-    eval_ms_per_solve = sr["eval_ms"] / reps
-    launches_per_solve = sr["timed_launches"] / reps
+    rounds = int(rr["rounds"]) + 1                # the first evaluation (root) and one per round after it
+    assert all(len(x) == rounds for x in per_round), ([len(x) for x in per_round], rounds)
+    round_ms = [float(statistics.median(float(x[k]) for x in per_round)) for k in range(rounds)]
+    eval_ms_per_solve = sum(round_ms)
     N = w.n
     pe, be, bi = rr["point_evals"], rr["bound_evals"], rr["bound_increments"]
     ops = OPS_POINT_WARP * N * pe + OPS_BOUND_EVENT * N * be + OPS_BOUND_INCREMENT * bi
+    ops_fine = OPS_FINE[0] * N * pe + OPS_FINE[1] * N * be + OPS_FINE[2] * bi
     achieved = ops / (eval_ms_per_solve / 1e3) / 1e12
     peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 0.0)
+    peak_src = "max SM clock of the measured peaks"
+    if not sm_max:
+        sm_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
+        peak_src = "max SM clock reported by nvidia-smi"
+    peak = sms * LANES_PER_SM * sm_max * 1e6 / 1e12
     traffic = profile_traffic(kernel_hash())
     # the scatter's other two ceilings, from the library's own probes
     atom_peak, l2_peak = dd.dd_probe_peaks(stream.cuda_stream)
@@ -481,17 +521,27 @@ def run_ours(args):
     roofline_atomics = {"bound": "shared_atomics", "achieved": incr / (eval_ms_per_solve / 1e3) / 1e9,
                         "peak": atom_peak / 1e9, "unit": "G increments/s",
                         "frac": incr / (eval_ms_per_solve / 1e3) / atom_peak,
+                        "increments_per_solve": incr,
                         "peak_source": "measured: dd_probe_peaks (shared atomics with return, random cells)"}
     roofline_l2 = {"bound": "l2", "achieved": ev_bytes / (eval_ms_per_solve / 1e3) / 1e9, "peak": l2_peak / 1e9,
                    "unit": "GB/s", "frac": ev_bytes / (eval_ms_per_solve / 1e3) / l2_peak,
+                   "bytes_per_solve": ev_bytes,
                    "peak_source": "measured: dd_probe_peaks (32 MiB L2-resident stream)"}
     roofline = {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "derived: %d SMs x %d lanes x %.0f MHz (max SM clock of measured peaks)"
-                               % (SM_COUNT, LANES_PER_SM, sm_max),
-                "ops_per_solve": ops, "eval_ms_per_solve": eval_ms_per_solve,
-                "eval_launches_per_solve": launches_per_solve,
-                "eval_share_of_step": eval_ms_per_solve / (sum(step_ms) / len(step_ms))}
+                "peak_source": "derived: %d SMs (device) x %d lanes x %.0f MHz (%s)"
+                               % (sms, LANES_PER_SM, sm_max, peak_src),
+                "ops_per_solve": ops,
+                "ops_formula": "%d N point_evals + %d N bound_evals + %d bound_increments; N=%d, point_evals=%d, "
+                               "bound_evals=%d, bound_increments=%d"
+                               % (OPS_POINT_WARP, OPS_BOUND_EVENT, OPS_BOUND_INCREMENT, N, pe, be, bi),
+                "frac_fine_counts": ops_fine / (eval_ms_per_solve / 1e3) / 1e12 / peak,
+                "eval_ms_per_solve": eval_ms_per_solve, "eval_launches_per_solve": rounds,
+                "eval_ms_per_launch": eval_ms_per_solve / rounds,
+                "eval_ms_per_round": [round(x, 4) for x in round_ms],
+                "eval_share_of_step": eval_ms_per_solve / (sum(step_ms) / len(step_ms)),
+                "timing": "CUDA events around each evaluation launch on the solver's stream, rounds launched "
+                          "from the host one per poll, median over %d solves per round" % reps}
 
     # ---- secondary: Algorithm 1 one interval per round (pop 1)
     plain = None
@@ -526,7 +576,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "events": N,
-                      "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")},
+                      "knobs": {k: getattr(ctx.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits", "fuse_span")},
                       "l2": "flushed before each timed step, device-resident and e2e alike (%d MiB device write)"
                             % args.flush_mb,
                       "inputs": "device-resident SoA", "parallelism": "replicas" if world > 1 else "single GPU"},

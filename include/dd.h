@@ -91,6 +91,11 @@ typedef struct {
     int32_t polarity;       /* 0: polarity unused (the paper's objective); 1: one image   */
                             /*    per polarity, contrasts added (H <= 2048; every        */
                             /*    dd_events must then carry p)                            */
+    int32_t fuse_span;      /* an expanded interval whose events move by at most          */
+                            /*    fuse_span/100 pixel across it (estimated from the scale  */
+                            /*    change, as the split rule does) has its centre and both  */
+                            /*    halves evaluated in one pass; 0: default (25), < 0:      */
+                            /*    never.  A schedule choice: results do not depend on it   */
 } dd_config;
 
 /* One window of events in structure-of-arrays form. */
@@ -303,8 +308,19 @@ int dd_reset_stats(dd_ctx* ctx);
 
 /* enable != 0: bracket every IWE evaluation launch with CUDA events on the
  * context's stream and add its duration to dd_stats.eval_ms (costs a few
- * microseconds per launch; off by default). */
+ * microseconds per launch; off by default).  While timing is on, a solve
+ * launches its rounds from the host one round per poll (dd_config.host_loop
+ * behaviour without the batching), so every timed launch evaluates work:
+ * launch k of a solve is its round k. */
 int dd_set_timing(dd_ctx* ctx, int32_t enable);
+
+/* Telemetry: the device durations (ms) of the timed IWE launches since the
+ * last dd_reset_stats, in launch order, the first DD_MAX_LAUNCH_TIMES of
+ * them.  Copies min(cap, count) entries into ms (host array) and the count
+ * into *n.  No GPU work.  Errors: DD_ERR_ARG (null ctx or n, cap < 0, ms
+ * NULL with cap > 0). */
+#define DD_MAX_LAUNCH_TIMES 65536
+int dd_get_launch_times(dd_ctx* ctx, float* ms, int32_t cap, int32_t* n);
 
 /* ------------------------------------------------------------------------
  * Learned warm start.  An extension of the paper's method: its Algorithm 1
@@ -466,14 +482,19 @@ double dd_serve_clock(void);
  *
  * Set-up: the first call on each device (made with that device current)
  * looks up the device address of the static array and caches it; make that
- * first call before any stream capture on the device.
+ * first call before any stream capture on the device.  The cached address
+ * belongs to the device's primary context: after cudaDeviceReset on that
+ * device it is stale, so this entry point must not be called on that device
+ * again in the same process.  The first call may also load this library's
+ * device code (and with it the static array) if nothing else has yet; later
+ * calls leave the device's free memory unchanged.
  * Sharing: every call on a device uses the same array and leaves the last
  * call's contents in it (everything that must start at zero is cleared by the
  * call itself).  Calls whose GPU work overlaps -- from several host threads
  * or on several streams at once -- race on the array; serialise them.
- * Errors: DD_ERR_CAPACITY if ev->n > DD_NOALLOC_MAX_EVENTS; DD_ERR_ARG as
- * dd_contrast, or if the events are not device pointers; DD_ERR_NO_DEVICE;
- * DD_ERR_CUDA. */
+ * Errors: DD_ERR_CAPACITY if ev->n > DD_NOALLOC_MAX_EVENTS; DD_ERR_ARG in
+ * every case dd_contrast rejects (the same descriptor and domain checks), or
+ * if the events are not device pointers; DD_ERR_NO_DEVICE; DD_ERR_CUDA. */
 #define DD_NOALLOC_MAX_EVENTS (1 << 20)
 #define DD_NOALLOC_SCRATCH_BYTES 25224704
 int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_y, const dd_events* ev, const float* D,

@@ -53,7 +53,8 @@ class dd_i128(ctypes.Structure):
 class dd_config(ctypes.Structure):
     _fields_ = [("pop_k", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("band_rows", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("max_splits", ctypes.c_int32), ("warp_to_start", ctypes.c_int32), ("polarity", ctypes.c_int32)]
+                ("max_splits", ctypes.c_int32), ("warp_to_start", ctypes.c_int32), ("polarity", ctypes.c_int32),
+                ("fuse_span", ctypes.c_int32)]
 
 
 class dd_events(ctypes.Structure):
@@ -152,6 +153,7 @@ SIGNATURES = {
     "dd_get_stats": (ctypes.c_int, [_VP, _P(dd_stats)]),
     "dd_reset_stats": (ctypes.c_int, [_VP]),
     "dd_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "dd_get_launch_times": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "dd_contrast_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                            _P(dd_events), _VP, ctypes.c_int32, _VP, _VP]),
     "dd_probe_peaks": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _VP]),
@@ -227,6 +229,15 @@ def dd_reset_stats(h):
 
 def dd_set_timing(h, enable):
     _check(load().dd_set_timing(h, 1 if enable else 0), "dd_set_timing")
+
+
+def dd_get_launch_times(h):
+    """Device durations (ms) of the timed evaluation launches since the last reset."""
+    n = ctypes.c_int32(0)
+    _check(load().dd_get_launch_times(h, None, 0, ctypes.byref(n)), "dd_get_launch_times")
+    ms = np.zeros(max(n.value, 1), np.float32)
+    _check(load().dd_get_launch_times(h, ms.ctypes.data, n.value, ctypes.byref(n)), "dd_get_launch_times")
+    return ms[:n.value]
 
 
 def _ptr(a):
@@ -623,11 +634,11 @@ class Context:
     """A dd_ctx for one frame geometry (W x H, FOE)."""
 
     def __init__(self, W, H, foe_x, foe_y, pop_k=0, queue_capacity=0, band_rows=0, threads=0, max_rounds=0,
-                 host_loop=0, max_splits=0, warp_to_start=0, polarity=0):
+                 host_loop=0, max_splits=0, warp_to_start=0, polarity=0, fuse_span=0):
         self.W, self.H = int(W), int(H)
         self.planes = 2 if polarity else 1
         self.cfg = dd_config(pop_k, queue_capacity, band_rows, threads, max_rounds, host_loop, max_splits,
-                             warp_to_start, polarity)
+                             warp_to_start, polarity, fuse_span)
         self.h = dd_create(self.W, self.H, float(foe_x), float(foe_y), self.cfg)
         self._log = None
 
@@ -689,6 +700,9 @@ class Context:
 
     def set_timing(self, enable):
         dd_set_timing(self.h, enable)
+
+    def launch_times(self):
+        return dd_get_launch_times(self.h)
 
     def contrast(self, ev, D, want_iwe=False):
         K, S, N, img = dd_contrast(self.h, ev, D, want_iwe=want_iwe, M=self.M)

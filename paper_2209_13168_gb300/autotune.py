@@ -1,9 +1,12 @@
 """Autotuner for the IWE tiling and the BnB schedule.
 
 Times exact solves of sample windows on the current GPU for each candidate
-(band rows, threads per block, intervals per round, split cap) and records
-the fastest in a JSON table keyed by (frame geometry, event-count bucket,
-single-window or batch, GPU name).  The knobs change only the schedule:
+(band rows, threads per block, intervals per round, split cap), then, with
+the fastest of those, for each fusing threshold (how narrow an expanded
+interval must be for its centre and both halves to run as one fused job:
+the tasks evaluated per unit, one or three), and records the fastest in a
+JSON table keyed by (frame geometry, event-count bucket, single-window or
+batch, GPU name).  The knobs change only the schedule:
 results are identical for every candidate (the table stores times, and the
 tuner checks that every candidate returned the same keys).
 
@@ -26,6 +29,9 @@ CANDIDATES = {
     "pop_k": [16, 32, 64],
     "max_splits": [4, 8, 16],
 }
+# second stage: dd_config.fuse_span (-1: never fuse, one task per unit)
+FUSE_CANDIDATES = [-1, 10, 25, 40, 70]
+KNOBS = ("band_rows", "threads", "pop_k", "max_splits", "fuse_span")
 
 
 def size_bucket(n_events):
@@ -63,9 +69,13 @@ def tune(windows, mode="single", candidates=None, reps=3, log=print):
     evs = [dd.Events.of(w, device="cuda") for w in windows]
     best, ref = None, None
     grid = list(itertools.product(cand["band_rows"], cand["threads"], cand["pop_k"],
-                                  cand["max_splits"] if mode == "single" else [1]))
-    for rows, thr, k, ms in grid:
-        ctx = dd.Context(w0.W, w0.H, w0.foe_x, w0.foe_y, pop_k=k, band_rows=rows, threads=thr, max_splits=ms)
+                                  cand["max_splits"] if mode == "single" else [1], [0]))
+    fuse = cand.get("fuse_span", FUSE_CANDIDATES)
+    stage2 = False
+    while grid:
+        rows, thr, k, ms, fz = grid.pop(0)
+        ctx = dd.Context(w0.W, w0.H, w0.foe_x, w0.foe_y, pop_k=k, band_rows=rows, threads=thr, max_splits=ms,
+                         fuse_span=fz)
         if mode == "single":
             dt, out = _time(lambda: [ctx.solve(e) for e in evs], reps)
             keys = [r["K_hat"] for r in out]
@@ -78,9 +88,14 @@ def tune(windows, mode="single", candidates=None, reps=3, log=print):
         if ref is None:
             ref = keys
         assert keys == ref, "a schedule knob changed a result"
-        log("  rows=%3d threads=%4d pop_k=%2d max_splits=%2d: %.3f ms per window" % (rows, thr, k, ms, dt * 1e3))
+        log("  rows=%3d threads=%4d pop_k=%2d max_splits=%2d fuse_span=%d: %.3f ms per window"
+            % (rows, thr, k, ms, fz, dt * 1e3))
         if best is None or dt < best["ms_per_window"] / 1e3:
-            best = {"band_rows": rows, "threads": thr, "pop_k": k, "max_splits": ms, "ms_per_window": dt * 1e3}
+            best = {"band_rows": rows, "threads": thr, "pop_k": k, "max_splits": ms, "fuse_span": fz,
+                    "ms_per_window": dt * 1e3}
+        if not grid and not stage2:              # then the fusing threshold, with the best of the rest
+            stage2 = True
+            grid = [(best["band_rows"], best["threads"], best["pop_k"], best["max_splits"], f) for f in fuse]
     torch.cuda.synchronize()
     return best
 
@@ -108,7 +123,7 @@ def lookup(W, H, n_events, mode="single", path=DEFAULT_TABLE):
         if not near:
             return None
         entry = table[min(near)[1]]
-    return {k: entry[k] for k in ("band_rows", "threads", "pop_k", "max_splits")}
+    return {k: entry[k] for k in KNOBS if k in entry}
 
 
 class _Resampled:
@@ -149,7 +164,8 @@ def main():
     table = load_table(args.out)
     cand = None
     if args.quick:
-        cand = {"band_rows": [16, 38], "threads": [256, 512], "pop_k": [16, 32], "max_splits": [8, 16]}
+        cand = {"band_rows": [16, 38], "threads": [256, 512], "pop_k": [16, 32], "max_splits": [8, 16],
+                "fuse_span": [-1, 25]}
     from synth.descent import serve_config5
     jobs = [("single", [window_config1()]), ("single", [window_config2()])]
     params = batch_params3()

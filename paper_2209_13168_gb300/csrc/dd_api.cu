@@ -10,6 +10,8 @@
 #include <vector>
 
 using dd::i128;
+using dd::check_events;
+using dd::d_ok;
 
 struct dd_ctx {
     int device = 0;
@@ -78,6 +80,7 @@ struct dd_ctx {
     int timing = 0;
     std::vector<cudaEvent_t> t_ev;
     size_t t_used = 0;
+    std::vector<float> t_ms;      // durations of the timed launches since the last reset
 
     // pinned host staging
     dd::SolveState* h_st = nullptr;
@@ -101,24 +104,6 @@ namespace {
 int cuda_status(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return DD_ERR_OOM;
     return DD_ERR_CUDA;
-}
-
-bool d_ok(float D, float tau) {
-    if (!std::isfinite(D)) return false;
-    double dt = (double)D * (double)tau;
-    return dt <= 0.75 && dt >= -64.0;
-}
-
-// Host checks of a window descriptor.  Event contents (coordinates in the
-// frame, times in the window) are checked by the ingest kernels, which flag
-// the window; the call then fails with DD_ERR_ARG.
-// With two polarity planes the events must carry their polarities.
-int check_events(const dd_events* ev, int32_t planes) {
-    if (!ev || ev->n < 0 || ev->n > INT32_MAX / 2) return DD_ERR_ARG;
-    if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
-    if (ev->n > 0 && (!ev->x || !ev->y || !ev->t)) return DD_ERR_ARG;
-    if (planes > 1 && ev->n > 0 && !ev->p) return DD_ERR_ARG;
-    return DD_OK;
 }
 
 template <class T>
@@ -146,6 +131,7 @@ cudaError_t sync(dd_ctx* c) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, c->t_ev[i], c->t_ev[i + 1]) == cudaSuccess) c->stats.eval_ms += ms;
             c->stats.timed_launches++;
+            if (c->t_ms.size() < DD_MAX_LAUNCH_TIMES) c->t_ms.push_back(ms);
         }
         c->t_used = 0;
     }
@@ -573,8 +559,9 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
         }
         DD_TRY(cudaGraphLaunch(c->gexec, c->stream));
     } else {
-        // Host-driven rounds: launch batches, poll for the end.
-        int batch = 2;
+        // Host-driven rounds: launch batches, poll for the end.  With timing
+        // on, one round per poll, so that every timed launch has work.
+        int batch = c->timing ? 1 : 2;
         for (;;) {
             for (int b = 0; b < batch; b++) {
                 DD_TRY(eval(c, nullptr, nw == 1));
@@ -585,7 +572,7 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
             DD_TRY(copy(c, c->h_sch, c->sch, sizeof(dd::Sched), cudaMemcpyDeviceToHost));
             DD_TRY(sync(c));
             if (c->h_sch->running == 0) break;
-            if (batch < 64) batch *= 2;
+            if (batch < 64 && !c->timing) batch *= 2;
         }
     }
     DD_TRY(copy(c, c->h_st, c->st, sizeof(dd::SolveState) * nw, cudaMemcpyDeviceToHost));
@@ -617,6 +604,24 @@ int solve_impl(dd_ctx* c, const dd_events* evs, int nw, const dd_window_params* 
 }  // namespace
 
 namespace dd {
+bool d_ok(float D, float tau) {
+    if (!std::isfinite(D)) return false;
+    double dt = (double)D * (double)tau;
+    return dt <= 0.75 && dt >= -64.0;
+}
+
+// Host checks of a window descriptor.  Event contents (coordinates in the
+// frame, times in the window) are checked by the ingest kernels, which flag
+// the window; the call then fails with DD_ERR_ARG.
+// With two polarity planes the events must carry their polarities.
+int check_events(const ::dd_events* ev, int32_t planes) {
+    if (!ev || ev->n < 0 || ev->n > INT32_MAX / 2) return DD_ERR_ARG;
+    if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
+    if (ev->n > 0 && (!ev->x || !ev->y || !ev->t)) return DD_ERR_ARG;
+    if (planes > 1 && ev->n > 0 && !ev->p) return DD_ERR_ARG;
+    return DD_OK;
+}
+
 void ctx_info(const ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval_blocks, int32_t* max_tasks, int32_t* pop_k,
               int32_t* queue_capacity, int64_t* max_rounds) {
     *g = c->g;
@@ -743,6 +748,9 @@ int dd_create(int32_t W, int32_t H, float foe_x, float foe_y, const dd_config* c
     c->g.n_tb = dd::time_buckets(c->g.planes * H);
     c->g.max_splits = k.max_splits ? k.max_splits : 16;
     c->g.ref0 = k.warp_to_start ? 1 : 0;
+    if (!k.fuse_span) k.fuse_span = 25;
+    c->g.fuse_cells = k.fuse_span > 0 ? 0.01f * (float)k.fuse_span : 0.0f;
+    c->cfg.fuse_span = k.fuse_span;
     c->max_tasks = 3 * k.pop_k > 64 ? 3 * k.pop_k : 64;
     c->cfg.threads = c->threads;
     c->cfg.band_rows = rows;
@@ -801,6 +809,15 @@ int dd_get_stats(dd_ctx* c, dd_stats* out) {
 int dd_reset_stats(dd_ctx* c) {
     if (!c) return DD_ERR_ARG;
     std::memset(&c->stats, 0, sizeof(c->stats));
+    c->t_ms.clear();
+    return DD_OK;
+}
+
+int dd_get_launch_times(dd_ctx* c, float* ms, int32_t cap, int32_t* n) {
+    if (!c || !n || cap < 0 || (cap > 0 && !ms)) return DD_ERR_ARG;
+    const int32_t k = (int32_t)c->t_ms.size();
+    for (int32_t i = 0; i < k && i < cap; i++) ms[i] = c->t_ms[i];
+    *n = k;
     return DD_OK;
 }
 

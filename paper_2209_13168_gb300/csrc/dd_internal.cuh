@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include "../../include/dd.h"
+
 struct dd_ctx;
 struct dd_mlp;
 
@@ -41,7 +43,10 @@ struct Task {
 };
 
 // One schedulable job: split `split` of `splits` of task `task` of window
-// `win`; a job covers every row band of the frame.
+// `win`; a job covers every row band of the frame.  A fused job (splits < 0)
+// evaluates the three tasks of one expanded interval together: the contrast
+// at its centre (task `task`) and the bounds of its two halves (tasks
+// `split` and `split` + 1).
 struct Job {
     int32_t win, task, split, splits;
 };
@@ -160,6 +165,8 @@ struct Geom {
     int32_t ref0;           // 1: the warp maps events to the window's start (t_ref = 0), not its end
     int32_t planes;         // 1: polarity unused; 2: one image per polarity (p > 0, p <= 0)
     int32_t plane_tiles;    // row bands of one plane
+    float fuse_cells;       // an expanded interval whose bound_cells - 1 is at most this runs as one
+                            // fused job (0: never); a schedule choice only
 };
 
 // Bins of one window's event sort.
@@ -294,5 +301,11 @@ void ctx_info(const struct ::dd_ctx* c, Geom* g, int32_t* threads, int32_t* eval
 const struct ::dd_mlp* ctx_warm_model(const struct ::dd_ctx* c);
 cudaStream_t ctx_stream(const struct ::dd_ctx* c);
 cudaError_t eval_smem_setup(const Geom& g);
+
+// Host checks shared by the entry points (dd_api.cu): a window descriptor
+// (DD_OK or DD_ERR_ARG; with two polarity planes the events must carry p),
+// and a hypothesis in the domain -64 <= D tau <= 3/4.
+int check_events(const ::dd_events* ev, int32_t planes);
+bool d_ok(float D, float tau);
 
 }  // namespace dd

@@ -20,6 +20,7 @@
 #include "../../include/dd.h"
 
 #include <cfloat>
+#include <mutex>
 
 namespace dd {
 
@@ -262,18 +263,21 @@ cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_window
 // t, so over the bucket's time range its extremes are at the four corners.
 // An event at row y can reach the rows only if (y - FOE_y) s meets them for
 // some s in that range; the rows that can are a contiguous range of the
-// bucket's row-sorted events.  Binary32 with margins far above its rounding
-// error (1e-4 relative on s, 1e-3 of a bucket in t, 1/16 pixel on the band's
-// edges): a superset.
+// bucket's row-sorted events.  Binary32 with correctly rounded operations
+// (relative error of each scale below 10 x 2^-24 on the domain
+// -64 <= D tau <= 3/4, of each row bound below 1e-6 of at most 4096 px) and
+// margins far above that: 1e-4 relative on s, 1e-3 of a bucket in t (an
+// event of bucket b has t bscale in [b (1 - 2^-24), (b + 1)(1 + 2^-24))),
+// 1/16 pixel on the band's edges.  A superset.
 __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float Dl, float Dh, float tau,
                                    float bscale, int b, int y0, int y1, int& e0, int& e1) {
-    const float tl = fmaxf(0.0f, __fdividef((float)b - 1e-3f, bscale));
-    const float th = fminf(tau, __fdividef((float)b + 1.001f, bscale));
+    const float tl = fmaxf(0.0f, __fdiv_rn((float)b - 1e-3f, bscale));
+    const float th = fminf(tau, __fdiv_rn((float)b + 1.001f, bscale));
     const float tref = warp_tref(g, tau);
     float smin = 3.0e38f, smax = -3.0e38f;
     for (int i = 0; i < 4; i++) {
         const float D = (i & 1) ? Dh : Dl, t = (i & 2) ? th : tl;
-        const float s = __fdividef(1.0f - D * t, 1.0f - D * tref);
+        const float s = __fdiv_rn(1.0f - D * t, 1.0f - D * tref);
         smin = fminf(smin, s);
         smax = fmaxf(smax, s);
     }
@@ -281,8 +285,8 @@ __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float 
     smax *= 1.0f + 1e-4f;
     const float A = (float)y0 - 0.5625f - g.fy;
     const float B = (float)(y1 - 1) + 0.5625f - g.fy;
-    const float dylo = __fdividef(A, A >= 0.0f ? smax : smin);
-    const float dyhi = __fdividef(B, B >= 0.0f ? smin : smax);
+    const float dylo = __fdiv_rn(A, A >= 0.0f ? smax : smin);
+    const float dyhi = __fdiv_rn(B, B >= 0.0f ? smin : smax);
     // The margins above exceed the few-ulp error of this arithmetic, and
     // rounding a bound that is off by less than a row outward to an integer
     // row never drops a row the exact bound admits.
@@ -367,11 +371,15 @@ __device__ __forceinline__ Seg seg_range(const Geom& g, float dx, float dy, floa
 // cell): the sum of squares grows by 2v + 1 from the cell's previous count v
 // and C counts increments (32 bits: callers fold it into 64 bits often
 // enough that it cannot wrap).  Dense images (many increments per cell): the
-// increment alone, the sums taken from the tile afterwards.
-template <bool DENSE>
+// increment alone, the sums taken from the tile afterwards.  Undo: the
+// decrement that takes back an earlier sparse increment of the same cell.
+enum BumpMode : int { BUMP_SPARSE = 0, BUMP_DENSE = 1, BUMP_UNDO = 2 };
+template <int MODE>
 __device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, uint32_t& C) {
-    if (DENSE) {
+    if (MODE == BUMP_DENSE) {
         atomicAdd(cell, 1u);
+    } else if (MODE == BUMP_UNDO) {
+        atomicSub(cell, 1u);
     } else {
         const uint32_t v = atomicAdd(cell, 1u);
         S += 2u * v + 1u;
@@ -379,12 +387,12 @@ __device__ __forceinline__ void bump(uint32_t* cell, unsigned long long& S, uint
     }
 }
 
-template <bool DENSE>
+template <int MODE>
 __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float dn, float rm, float sa, float sb,
                                          int addr, int y0, int y1, uint32_t* tile, unsigned long long& S,
                                          uint32_t& C) {
     if (mode == SEG_ONE) {
-        if (DD_IN(addr, (y1 - y0) * tile_pitch(g), 2u)) bump<DENSE>(&tile[addr], S, C);
+        if (DD_IN(addr, (y1 - y0) * tile_pitch(g), 2u)) bump<MODE>(&tile[addr], S, C);
         return;
     }
     const bool major_x = mode == SEG_X;
@@ -400,12 +408,12 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
         const int j0 = max(max(min(j1, j2), 0), y0), jn = min(min(max(j1, j2), g.H - 1), y1 - 1);
         for (int j = j0; j <= jn; j++)
             if (DD_IN((j - y0) * tile_pitch(g) + k, (y1 - y0) * tile_pitch(g), 2u))
-                bump<DENSE>(&tile[(j - y0) * tile_pitch(g) + k], S, C);
+                bump<MODE>(&tile[(j - y0) * tile_pitch(g) + k], S, C);
     } else {
         const int j0 = max(min(j1, j2), 0), jn = min(max(j1, j2), g.W - 1);
         uint32_t* row = tile + (k - y0) * tile_pitch(g);
         for (int j = j0; j <= jn; j++)
-            if (DD_IN((k - y0) * tile_pitch(g) + j, (y1 - y0) * tile_pitch(g), 2u)) bump<DENSE>(&row[j], S, C);
+            if (DD_IN((k - y0) * tile_pitch(g) + j, (y1 - y0) * tile_pitch(g), 2u)) bump<MODE>(&row[j], S, C);
     }
 }
 
@@ -415,20 +423,20 @@ __device__ __forceinline__ void seg_cell(const Geom& g, int mode, int k, float d
 // position of the next run and the current run's offset from positions to
 // event indices) only moves forward; positions stay below
 // erange[MAX_TB + n_tb].
+constexpr int MAX_TB = 8;    // time buckets of the event sort
+
 struct Cursor {
     const int* erange;
     int cur_b, next_f, delta;
-    __device__ __forceinline__ Cursor(const int* er, int max_tb) : erange(er), cur_b(0) {
-        next_f = er[max_tb + 1];
-        delta = er[0] - er[max_tb];
-        mtb = max_tb;
+    __device__ __forceinline__ Cursor(const int* er, int) : erange(er), cur_b(0) {
+        next_f = er[MAX_TB + 1];
+        delta = er[0] - er[MAX_TB];
     }
-    int mtb;
     __device__ __forceinline__ int at(int f) {
         while (f >= next_f) {
             cur_b++;
-            delta = erange[cur_b] - erange[mtb + cur_b];
-            next_f = erange[mtb + cur_b + 1];
+            delta = erange[cur_b] - erange[MAX_TB + cur_b];
+            next_f = erange[MAX_TB + cur_b + 1];
         }
         return f + delta;
     }
@@ -436,7 +444,6 @@ struct Cursor {
 
 
 
-constexpr int MAX_TB = 8;    // time buckets of the event sort
 constexpr int QUEUE = 64;    // queued long-segment events per warp (a power of two, >= 63)
 constexpr int MAX_WARPS = 16;   // warps of a k_eval block (at most 512 threads)
 
@@ -461,13 +468,13 @@ struct UnitPtrs {
 // Eqs. (16) and (19) for the unit's share of events, positions [f_begin,
 // total): Hbar into the tile, N_full into `full`, and (sparse) S and C.
 // Per-warp rings of queued long segments (see bound_pass).
-struct SegQueue {
+struct __align__(16) SegQueue {
     int e[MAX_WARPS * QUEUE];
     float sa[MAX_WARPS * QUEUE], sb[MAX_WARPS * QUEUE];
     int x[MAX_WARPS * QUEUE], y[MAX_WARPS * QUEUE];
 };
 
-template <bool DENSE>
+template <int MODE>
 __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, const Task& tk, float tau, uint32_t* tile,
                                            SegQueue& queue, int y0, int y1, int f_begin, int total, Cursor& cur,
                                            unsigned long long& S, unsigned long long& C, unsigned long long& full) {
@@ -493,7 +500,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
         const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
         if (cmax <= 2) {
             for (int i = 0; i < sg.count; i++)
-                seg_cell<DENSE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
+                seg_cell<MODE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
             C += Ci;
             return;
         }
@@ -513,7 +520,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
             const float orm = __shfl_sync(0xffffffffu, sg.rm, o);
             const float osa = __shfl_sync(0xffffffffu, sg.sa, o);
             const float osb = __shfl_sync(0xffffffffu, sg.sb, o);
-            if (gi < tot) seg_cell<DENSE>(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
+            if (gi < tot) seg_cell<MODE>(g, om, ok + gi, odn, orm, osa, osb, oa, y0, y1, tile, S, Ci);
         }
         C += Ci;
     };
@@ -567,7 +574,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
                     // in s, so the segment covers that pixel only.
                     if ((unsigned)xa < (unsigned)W && ya_here) {
                         uint32_t Ci = 0;
-                        if (DD_IN((ya - y0) * P + xa, rows * P, 1u)) bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
+                        if (DD_IN((ya - y0) * P + xa, rows * P, 1u)) bump<MODE>(&tile[(ya - y0) * P + xa], S, Ci);
                         C += Ci;
                     }
                 } else if ((xa == xb && abs(ya - yb) == 1) || (ya == yb && abs(xa - xb) == 1)) {
@@ -577,10 +584,10 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
                     // lies in the frame and in this band).
                     uint32_t Ci = 0;
                     if ((unsigned)xa < (unsigned)W && ya_here && DD_IN((ya - y0) * P + xa, rows * P, 1u))
-                        bump<DENSE>(&tile[(ya - y0) * P + xa], S, Ci);
+                        bump<MODE>(&tile[(ya - y0) * P + xa], S, Ci);
                     if ((unsigned)xb < (unsigned)W && (unsigned)(yb - y0) < (unsigned)rows &&
                         DD_IN((yb - y0) * P + xb, rows * P, 1u))
-                        bump<DENSE>(&tile[(yb - y0) * P + xb], S, Ci);
+                        bump<MODE>(&tile[(yb - y0) * P + xb], S, Ci);
                     C += Ci;
                 } else {
                     pend = true;
@@ -674,15 +681,15 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
             if ((unsigned)(uy - y0) >= (unsigned)rows) continue;
             const int ux = cell_of(g.fx, v.dx, s);
             if ((unsigned)ux < (unsigned)W && DD_IN((uy - y0) * P + ux, rows * P, 1u))
-                bump<false>(&tile[(uy - y0) * P + ux], S, Ct);
+                bump<BUMP_SPARSE>(&tile[(uy - y0) * P + ux], S, Ct);
         }
         C = Ct;
     } else {
         dense = bound_cells(g, tk.D_lo, tk.D_hi, tau) >= DENSE_CELLS;
         if (dense)
-            bound_pass<true>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
+            bound_pass<BUMP_DENSE>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
         else
-            bound_pass<false>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
+            bound_pass<BUMP_SPARSE>(g, p, tk, tau, tile, queue, y0, y1, f_begin, total, cur, S, C, full);
     }
     __syncthreads();
 
@@ -815,6 +822,209 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     }
 }
 
+// The bound's work for one event (Eqs. 16 and 19 restricted to the tile rows
+// [y0, y1)), as bound_pass does it, with the event's own lane walking its
+// segment: the widened scale range over [Dl, Dh], the end cells, N_full into
+// F and the covered cells.  BUMP_UNDO takes back exactly the increments an
+// earlier BUMP_SPARSE call made for the same event and interval.
+template <int MODE>
+__device__ __forceinline__ void bound_event(const Geom& g, const UnitPtrs& p, int e, float Dl, float gl, float Dh,
+                                            float gh, int y0, int y1, uint32_t* tile, unsigned long long& S,
+                                            uint32_t& C, uint32_t& F) {
+    const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
+    const Ev v = p.ev[e];
+    const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
+    const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
+    const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
+    const int ya = cell_of(g.fy, v.dy, sa), yb = cell_of(g.fy, v.dy, sb);
+    if (max(ya, yb) < y0 || min(ya, yb) >= y1) return;
+    const int xa = cell_of(g.fx, v.dx, sa), xb = cell_of(g.fx, v.dx, sb);
+    const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
+    if (MODE != BUMP_UNDO && (unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
+        ya_here)
+        F++;
+    if (xa == xb && ya == yb) {
+        if ((unsigned)xa < (unsigned)W && ya_here && DD_IN((ya - y0) * P + xa, rows * P, 1u))
+            bump<MODE>(&tile[(ya - y0) * P + xa], S, C);
+    } else if ((xa == xb && abs(ya - yb) == 1) || (ya == yb && abs(xa - xb) == 1)) {
+        if ((unsigned)xa < (unsigned)W && ya_here && DD_IN((ya - y0) * P + xa, rows * P, 1u))
+            bump<MODE>(&tile[(ya - y0) * P + xa], S, C);
+        if ((unsigned)xb < (unsigned)W && (unsigned)(yb - y0) < (unsigned)rows && DD_IN((yb - y0) * P + xb, rows * P, 1u))
+            bump<MODE>(&tile[(yb - y0) * P + xb], S, C);
+    } else {
+        const float2 r = p.rcp[e];
+        const Seg sg = seg_range(g, v.dx, v.dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+        for (int i = 0; i < sg.count; i++)
+            seg_cell<MODE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, C);
+    }
+}
+
+// The contrast at D for one event (Eqs. 11-12) restricted to the tile rows.
+template <int MODE>
+__device__ __forceinline__ void point_event(const Geom& g, const Ev& v, float D, float gD, int y0, int y1,
+                                            uint32_t* tile, unsigned long long& S, uint32_t& C) {
+    const int rows = y1 - y0, P = tile_pitch(g);
+    const float sc = warp_s(D, v.t, gD);
+    const int uy = cell_of(g.fy, v.dy, sc);
+    if ((unsigned)(uy - y0) >= (unsigned)rows) return;
+    const int ux = cell_of(g.fx, v.dx, sc);
+    if ((unsigned)ux < (unsigned)g.W && DD_IN((uy - y0) * P + ux, rows * P, 1u))
+        bump<MODE>(&tile[(uy - y0) * P + ux], S, C);
+}
+
+// Unstable events a fused unit can list (the long-segment queue's memory).
+constexpr int FUSE_LIST = (int)(sizeof(SegQueue) / sizeof(int));
+
+// One fused unit: the three tasks of one expanded interval [lo, hi] with
+// centre c -- the contrast at c (Eqs. 11-13) and the bounds over [lo, c] and
+// [c, hi] (Eqs. 14-19) -- on one row band, with one pass over the events.
+// Per event, the range [RN(min(s_lo, s_c, s_hi)(1 - 2^-19)),
+// RN(max(s_lo, s_c, s_hi)(1 + 2^-19))] of its binary32 scales at lo, c and hi
+// (computed as the tasks compute them) contains every scale the three tasks
+// use: s_c itself and the widened ends of both halves (rounding is
+// monotone).  Each cell coordinate is monotone in s, so when both ends of
+// that range fall in one pixel, every task puts the event in that pixel and
+// nowhere else: a stable event, counted once into the tile for all three (its
+// increments give a common sum of squares S_C and count N_C, which is also
+// each bound's N_full share).  The other events are listed as unstable; each
+// task in turn adds its own increments for them on top of the common counts,
+// each increment returning the cell's previous count v, so that the task's
+// sum of squares is S_C + sum(2v + 1); the centre's and the left half's
+// increments are taken back before the next task.  The sums, and so the keys,
+// are those of three separate passes.  A band with more unstable events than
+// the list holds runs as three ordinary units instead.
+__device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp, const Task& tl, const Task& tr,
+                                Partial* part_p, Partial* part_l, Partial* part_r, int ti, float tau, uint32_t* tile,
+                                unsigned long long (*red)[32], int* erange, int* s_n, int* s_last, SegQueue& queue) {
+    const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
+    const int y0 = band * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
+    const int32_t* row_off = p.row_off + (size_t)plane * g.n_tb * g.H;
+    const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float lo = tl.D_lo, c = tp.D_lo, hi = tr.D_hi;
+    if (threadIdx.x < 32) {
+        int e0 = 0, e1 = 0;
+        if (lane < g.n_tb)
+            bucket_event_range(g, row_off, lo, hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0, e1);
+        const int len = e1 - e0, incl = warp_incl_scan(len);
+        if (lane < g.n_tb) {
+            erange[lane] = e0;
+            erange[MAX_TB + lane] = incl - len;
+        }
+        if (lane == g.n_tb - 1) erange[MAX_TB + g.n_tb] = incl;
+        if (lane == 0) *s_n = 0;
+    }
+    __syncthreads();
+    const int total = erange[MAX_TB + g.n_tb];
+    Cursor cur(erange, MAX_TB);
+    const float tref = warp_tref(g, tau);
+    const float glo = warp_g(lo, tref), gc = warp_g(c, tref), ghi = warp_g(hi, tref);
+    int* list = reinterpret_cast<int*>(&queue);
+
+    // Pass over the candidates: stable events into the tile, the rest listed.
+    unsigned long long SC = 0;
+    uint32_t NC = 0;
+    for (int base = wid * 32; base < total; base += nw * 32) {
+        const int f = base + lane;
+        bool uns = false;
+        int e = 0;
+        if (f < total) {
+            e = cur.at(f);
+            if (!DD_IN(e, p.n_ev, 4u)) e = 0;
+            const Ev v = p.ev[e];
+            const float a = warp_s(lo, v.t, glo), b = warp_s(c, v.t, gc), d = warp_s(hi, v.t, ghi);
+            const float wa = __fmul_rn(fmin_t(fmin_t(a, b), d), WIDEN_DN);
+            const float wb = __fmul_rn(fmax_t(fmax_t(a, b), d), WIDEN_UP);
+            const int ya = cell_of(g.fy, v.dy, wa), yb = cell_of(g.fy, v.dy, wb);
+            if (max(ya, yb) >= y0 && min(ya, yb) < y1) {
+                const int xa = cell_of(g.fx, v.dx, wa), xb = cell_of(g.fx, v.dx, wb);
+                if (xa == xb && ya == yb) {
+                    if ((unsigned)xa < (unsigned)W && DD_IN((ya - y0) * P + xa, rows * P, 1u))
+                        bump<BUMP_SPARSE>(&tile[(ya - y0) * P + xa], SC, NC);
+                } else {
+                    uns = true;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, uns);
+        if (m) {
+            int at = 0;
+            if (lane == 0) at = atomicAdd(s_n, __popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            const int pos = at + __popc(m & ((1u << lane) - 1u));
+            if (uns && pos < FUSE_LIST) list[pos] = e;
+        }
+    }
+    __syncthreads();
+    const int n = *s_n;
+    if (n > FUSE_LIST) {                          // too many unstable events: three ordinary units
+        const int words = rows * P;
+        for (int i = threadIdx.x; i < words; i += blockDim.x) tile[i] = 0u;
+        __syncthreads();
+        for (int k = 0; k < 3; k++) {
+            UnitPtrs q = p;
+            q.part = k == 0 ? part_p : (k == 1 ? part_l : part_r);
+            const Task tk = k == 0 ? tp : (k == 1 ? tl : tr);
+            eval_unit(g, q, tk, ti, 0, 1, tau, tile, red, erange, s_last, queue);
+            __syncthreads();
+        }
+        return;
+    }
+    // Each task's own increments for the unstable events, on top of the
+    // common counts: the centre, then the left half, then the right half.
+    unsigned long long Sp = 0, Sl = 0, Sr = 0, Sx = 0;
+    uint32_t Cp = 0, Cl = 0, Cr = 0, Fl = 0, Fr = 0, Cx = 0, Fx = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        point_event<BUMP_SPARSE>(g, p.ev[list[i]], c, gc, y0, y1, tile, Sp, Cp);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        point_event<BUMP_UNDO>(g, p.ev[list[i]], c, gc, y0, y1, tile, Sx, Cx);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        bound_event<BUMP_SPARSE>(g, p, list[i], lo, glo, c, gc, y0, y1, tile, Sl, Cl, Fl);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        bound_event<BUMP_UNDO>(g, p, list[i], lo, glo, c, gc, y0, y1, tile, Sx, Cx, Fx);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        bound_event<BUMP_SPARSE>(g, p, list[i], c, gc, hi, ghi, y0, y1, tile, Sr, Cr, Fr);
+    __syncthreads();
+
+    // The tile leaves zeroed (its padding column stays zero): 16-byte words,
+    // then the tail.
+    {
+        const int words = rows * P, quads = words >> 2;
+        uint4* t4 = reinterpret_cast<uint4*>(tile);
+        for (int i = threadIdx.x; i < quads; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = 4 * quads + threadIdx.x; i < words; i += blockDim.x) tile[i] = 0u;
+    }
+    // Sums of the three tasks: per warp, then per block (in the list's memory).
+    unsigned long long* wsum = reinterpret_cast<unsigned long long*>(&queue);   // [8][MAX_WARPS]
+    auto put = [&](int k, unsigned long long x) {
+        x = warp_sum(x);
+        if (lane == 0) wsum[k * MAX_WARPS + wid] = x;
+    };
+    put(0, SC + Sp);
+    put(1, (unsigned long long)NC + Cp);
+    put(2, SC + Sl);
+    put(3, (unsigned long long)NC + Cl);
+    put(4, (unsigned long long)NC + Fl);
+    put(5, SC + Sr);
+    put(6, (unsigned long long)NC + Cr);
+    put(7, (unsigned long long)NC + Fr);
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x;
+        unsigned long long t = 0;
+        for (int w = 0; w < nw; w++) t += wsum[k * MAX_WARPS + w];
+        // k: 0 centre S, 1 centre N_in, then S, cells, N_full of the left (2-4) and right (5-7) halves
+        Partial* q = k < 2 ? part_p : (k < 5 ? part_l : part_r);
+        const int f = k < 2 ? k : (k < 5 ? k - 2 : k - 5);
+        unsigned long long* dst = f == 0 ? &q->S : (f == 1 ? &q->cells[plane] : &q->full[plane]);
+        if (t) atomicAdd(dst, t);
+    }
+}
+
 // IWE evaluation of the round's job list.  A grid of resident blocks takes
 // units (job, row band) from a counter; block 0 clears the other parity's
 // list and counter for the control blocks of this round.
@@ -823,7 +1033,7 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     __shared__ SegQueue queue;
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
-    __shared__ int s_unit, s_last;
+    __shared__ int s_unit, s_last, s_n;
     Sched* sch = a.sch;
     const int par = sch->round & 1;
     const int n_units = sch->n_jobs[par] * g.n_tiles;
@@ -854,7 +1064,8 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         const Job jb = jobs[j];
         const int64_t ev_off = a.wins[jb.win].ev_off;
         const float tau = a.wins[jb.win].tau;
-        const Task tk = a.tasks[(size_t)jb.win * a.task_stride + jb.task];
+        const Task* wt = a.tasks + (size_t)jb.win * a.task_stride;
+        const Task tk = wt[jb.task];
         UnitPtrs p;
         p.ev = a.ev + ev_off;
         p.rcp = a.rcp + ev_off;
@@ -867,7 +1078,13 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
         p.acc = a.mg.acc ? a.mg.acc + (size_t)jb.task * task_cells : nullptr;
         p.done = a.mg.done ? a.mg.done + (size_t)jb.task * g.n_tiles : nullptr;
         p.sums = a.mg.sums ? a.mg.sums + (size_t)jb.task * g.n_tiles : nullptr;
-        eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last, queue);
+        if (jb.splits < 0) {                      // one expanded interval: its three tasks together
+            Partial* wp = a.part + (size_t)jb.win * a.task_stride;
+            eval_fused_unit(g, p, tk, wt[jb.split], wt[jb.split + 1], wp + jb.task, wp + jb.split,
+                            wp + jb.split + 1, ti, tau, tile, red, erange, &s_n, &s_last, queue);
+        } else {
+            eval_unit(g, p, tk, ti, jb.split, max(1, jb.splits), tau, tile, red, erange, &s_last, queue);
+        }
         if (threadIdx.x == 0) s_unit = gridDim.x + next;
         __syncthreads();                          // the unit is done; s_unit is set
     }
@@ -1110,6 +1327,8 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
     __shared__ Node q_stage[Q_STAGE];
     __shared__ Node q_head[MAX_POP];               // the merged queue's first entries, for the dequeue
     __shared__ float2 bound_iv[3 * MAX_POP];      // the next round's bound tasks' intervals
+    __shared__ int16_t t_fuse[3 * MAX_POP];       // per next-round task: 0 own jobs, -1 part of a fused
+                                                  // job, k > 0 the centre of a fused job (left half k - 1)
     __shared__ int s_nk, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int w = blockIdx.x;
@@ -1373,13 +1592,15 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             for (int base = 0; base < np; base += 32) {   // centre and bisection
                 const int j = base + lane;
                 const bool v = j < np;
-                bool split = false;
+                bool split = false, fuse = false;
                 if (v) {
                     Popped& p = s.pop[j];
                     p.c = centre(p.lo, p.hi);
                     const float w = __fsub_rn(p.hi, p.lo);
                     p.leaf = !(w > s.tol) || !(p.c > p.lo) || !(p.c < p.hi);
                     split = !p.leaf;
+                    // narrow intervals: centre and halves evaluated by one fused job
+                    fuse = split && g.fuse_cells > 0.0f && bound_cells(g, p.lo, p.hi, s.tau) - 1.0f <= g.fuse_cells;
                 }
                 const unsigned sb = __ballot_sync(0xffffffffu, split);
                 if (v) {
@@ -1390,10 +1611,13 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                     a.kind = TASK_POINT;
                     a.splits = 1;
                     tasks[j] = a;
+                    t_fuse[j] = 0;
                     if (split) {
                         const int t = np + 2 * (nl_before + __popc(sb & ((1u << lane) - 1u)));
                         p.t_left = t;
                         p.t_right = t + 1;
+                        t_fuse[j] = fuse ? (int16_t)(t + 1) : (int16_t)0;
+                        t_fuse[t] = t_fuse[t + 1] = fuse ? (int16_t)-1 : (int16_t)0;
                         Task l, r;
                         l.D_lo = p.lo;
                         l.D_hi = p.c;
@@ -1433,16 +1657,22 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             const int nt = s.n_tasks, np = s.n_pop;
             auto dense_at = [&](int q) {
                 const int t = nt - 1 - q;
-                return split_ok && q < nt && t >= np && bound_cells(g, bound_iv[t].x, bound_iv[t].y, s.tau) >= DENSE_CELLS;
+                return split_ok && q < nt && t >= np && t_fuse[t] == 0 &&
+                       bound_cells(g, bound_iv[t].x, bound_iv[t].y, s.tau) >= DENSE_CELLS;
             };
-            int nd = 0;
-            for (int c0 = 0; c0 < nt; c0 += 32) nd += __popc(__ballot_sync(0xffffffffu, dense_at(c0 + lane)));
+            int nd = 0, nabs = 0;                 // dense bound tasks; tasks inside fused jobs
+            for (int c0 = 0; c0 < nt; c0 += 32) {
+                nd += __popc(__ballot_sync(0xffffffffu, dense_at(c0 + lane)));
+                nabs += __popc(__ballot_sync(0xffffffffu, c0 + lane < nt && t_fuse[nt - 1 - c0 - lane] < 0));
+            }
+            const int units = (nt - nabs) * g.n_tiles;   // one per job and band before any split
             auto splits_at = [&](int q, int& seen) {
                 const bool d = dense_at(q);
                 const unsigned db = __ballot_sync(0xffffffffu, d);
                 const int rank = seen + __popc(db & ((1u << lane) - 1u));
                 seen += __popc(db);
-                return q < nt ? (d ? fill_splits(g, nt * g.n_tiles, nd, rank) : 1) : 0;
+                if (q >= nt || t_fuse[nt - 1 - q] < 0) return 0;
+                return d ? fill_splits(g, units, nd, rank) : 1;
             };
             int run = 0, base = 0;
             int total = 0, seen = 0;
@@ -1465,12 +1695,13 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
                 const int t = nt - 1 - q;
                 const int c = splits_at(q, seen);
                 const int incl = warp_incl_scan(c);
+                const int fz = c > 0 ? (int)t_fuse[t] : 0;
                 for (int k = 0; k < c; k++) {
                     Job j;
                     j.win = w;
                     j.task = t;
-                    j.split = k;
-                    j.splits = c;
+                    j.split = fz > 0 ? fz - 1 : k;
+                    j.splits = fz > 0 ? -1 : c;
                     jobs[base + run + incl - c + k] = j;
                 }
                 run += __shfl_sync(0xffffffffu, incl, 31);
@@ -1513,28 +1744,38 @@ cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Nod
     return cudaGetLastError();
 }
 
-// The dynamic shared-memory limit is a per-function attribute shared by all
-// contexts: only ever raise it.
+// Function attributes are per device: the carveout and the dynamic
+// shared-memory limit of k_eval are set on the current device the first time
+// it is used, and the limit only ever raised, under one lock (contexts of
+// several host threads and devices share these records).
+constexpr int SMEM_MAX_DEVICES = 64;
+static std::mutex g_smem_mu;
+static bool g_carveout[SMEM_MAX_DEVICES];
+static int g_smem_bytes[SMEM_MAX_DEVICES];
+
 cudaError_t eval_smem_setup(const Geom& g) {
-    static bool carveout = false;
-    if (!carveout) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= SMEM_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    if (!g_carveout[dev]) {
         // One shared-memory carveout for every kernel of the library, so that
         // consecutive launches never wait for an L1 / shared reconfiguration.
         const void* fns[] = {(const void*)k_eval, (const void*)k_control, (const void*)k_init,
                              (const void*)k_keys, (const void*)k_row_hist, (const void*)k_row_scan,
                              (const void*)k_row_scatter};
         for (const void* f : fns) {
-            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 (int)cudaSharedmemCarveoutMaxShared);
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) return e;
         }
-        carveout = true;
+        g_carveout[dev] = true;
     }
-    static int current = 0;
-    int bytes = g.band_rows * tile_pitch(g) * (int)sizeof(uint32_t);
-    if (bytes <= current) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) current = bytes;
+    const int bytes = g.band_rows * tile_pitch(g) * (int)sizeof(uint32_t);
+    if (bytes <= g_smem_bytes[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) g_smem_bytes[dev] = bytes;
     return e;
 }
 

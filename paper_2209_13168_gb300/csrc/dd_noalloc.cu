@@ -65,11 +65,6 @@ int scratch_base(int dev, unsigned char** out) {
     return DD_OK;
 }
 
-bool d_in_domain(float D, float tau) {
-    if (!std::isfinite(D)) return false;
-    double dt = (double)D * (double)tau;
-    return dt <= 0.75 && dt >= -64.0;
-}
 
 }  // namespace
 
@@ -79,12 +74,12 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     if (!std::isfinite(foe_x) || !std::isfinite(foe_y) || foe_x < 0.0f || foe_y < 0.0f || foe_x > (float)W ||
         foe_y > (float)H)
         return DD_ERR_ARG;
-    if (!ev || !ev->device_ptrs || ev->n < 0 || nD < 0 || (nD > 0 && (!D || !K))) return DD_ERR_ARG;
-    if (ev->n > 0 && (!ev->x || !ev->y || !ev->t)) return DD_ERR_ARG;
-    if (!std::isfinite(ev->tau) || !(ev->tau > 0.0f) || !std::isfinite(ev->t0)) return DD_ERR_ARG;
+    if (!ev || !ev->device_ptrs || nD < 0 || (nD > 0 && (!D || !K))) return DD_ERR_ARG;
     if (ev->n > NA_MAX_EVENTS) return DD_ERR_CAPACITY;
+    // the descriptor and domain checks of dd_contrast (polarity unused)
+    if (dd::check_events(ev, 1) != DD_OK) return DD_ERR_ARG;
     for (int32_t j = 0; j < nD; j++)
-        if (!d_in_domain(D[j], ev->tau)) return DD_ERR_ARG;
+        if (!dd::d_ok(D[j], ev->tau)) return DD_ERR_ARG;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DD_ERR_NO_DEVICE;
@@ -92,12 +87,16 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     int rc = scratch_base(dev, &base);
     if (rc) return rc;
 
-    dd::Geom g;
+    dd::Geom g{};
     g.W = W;
     g.H = H;
     g.fx = foe_x;
     g.fy = foe_y;
-    int rows = (int)(96 * 1024 / (4 * W));       // the same band rule as dd_create's default
+    // Bands of about 96 KB of counts: taller than dd_create's default of
+    // 40 KB, because a contrast-only call has no bound tasks to split over
+    // several blocks, so fewer, taller units mean fewer candidate-run set-ups
+    // per hypothesis.  The keys are exact sums and do not depend on the band.
+    int rows = (int)(96 * 1024 / (4 * W));
     if (rows < 1) rows = 1;
     if (rows > H) rows = H;
     g.band_rows = rows;

@@ -44,7 +44,7 @@ def evaluate(windows, W2, H2, keep=0.25, seed=0, pop_k=None, reps=3, gamma=0.0, 
         out[name] = {"ms_per_window": dt * 1e3, "mean_abs_err_D": float(np.mean(err)),
                      "max_abs_err_D": float(np.max(err)), "mean_nodes": float(np.mean([r["nodes_expanded"] for r in res]))}
     out["speedup"] = out["full"]["ms_per_window"] / out["fast"]["ms_per_window"]
-    out["knobs"] = {name: {k: getattr(c.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits")}
+    out["knobs"] = {name: {k: getattr(c.cfg, k) for k in ("pop_k", "band_rows", "threads", "max_splits", "fuse_span")}
                     for name, c in (("full", full), ("fast", fast))}
     out["frame"] = "%dx%d -> %dx%d, keep %.2f" % (w0.W, w0.H, W2, H2, keep)
     out["gamma"] = gamma

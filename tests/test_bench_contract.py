@@ -72,3 +72,17 @@ def test_profile_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
     assert bench.kernel_hash() == h
     k.write_text(k.read_text() + "static int changed;\n")           # code does
     assert bench.kernel_hash() != h and bench.profile_traffic(bench.kernel_hash()) is None
+
+
+def test_clock_sampler_names_the_visible_gpu_not_the_rank():
+    # nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES: the
+    # sampled GPU is named by the device's UUID, else by the visible-devices
+    # entry the local rank maps to, and only without either by the index.
+    import bench
+    u = "58e7a8b3-1c2d-4e5f-8a9b-0c1d2e3f4a5b"
+    assert bench.nvsmi_gpu_id(u, "3,5", 1) == "GPU-" + u
+    assert bench.nvsmi_gpu_id("GPU-" + u, None, 0) == "GPU-" + u
+    assert bench.nvsmi_gpu_id(None, "3,5", 1) == "5"
+    assert bench.nvsmi_gpu_id(None, "GPU-abc,GPU-def", 0) == "GPU-abc"
+    assert bench.nvsmi_gpu_id(None, None, 2) == "2"
+    assert bench.nvsmi_gpu_id(None, "", 0) == "0"
