@@ -263,21 +263,25 @@ cudaError_t launch_ingest(const Geom& g, const WinIn* wins_dev, int32_t n_window
 // t, so over the bucket's time range its extremes are at the four corners.
 // An event at row y can reach the rows only if (y - FOE_y) s meets them for
 // some s in that range; the rows that can are a contiguous range of the
-// bucket's row-sorted events.  Binary32 with correctly rounded operations
-// (relative error of each scale below 10 x 2^-24 on the domain
-// -64 <= D tau <= 3/4, of each row bound below 1e-6 of at most 4096 px) and
-// margins far above that: 1e-4 relative on s, 1e-3 of a bucket in t (an
-// event of bucket b has t bscale in [b (1 - 2^-24), (b + 1)(1 + 2^-24))),
-// 1/16 pixel on the band's edges.  A superset.
+// bucket's row-sorted events.  Binary32, each operation correctly rounded
+// (relative error 2^-24; quotients as products with rounded reciprocals):
+// every scale has relative error below 12 x 2^-24 on the domain
+// -64 <= D tau <= 3/4, the bucket's time edges below 3 x 2^-24, and the row
+// bounds (at most 4096 px) below 3 x 2^-24, all far under the margins: 1e-4
+// relative on s, 1e-3 of a bucket in t (an event of bucket b has t bscale in
+// [b (1 - 2^-24), (b + 1)(1 + 2^-24)), b < 8), 1/16 pixel on the band's
+// edges.  A superset.
 __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float Dl, float Dh, float tau,
                                    float bscale, int b, int y0, int y1, int& e0, int& e1) {
-    const float tl = fmaxf(0.0f, __fdiv_rn((float)b - 1e-3f, bscale));
-    const float th = fminf(tau, __fdiv_rn((float)b + 1.001f, bscale));
+    const float rb = __frcp_rn(bscale);
+    const float tl = fmaxf(0.0f, __fmul_rn((float)b - 1e-3f, rb));
+    const float th = fminf(tau, __fmul_rn((float)b + 1.001f, rb));
     const float tref = warp_tref(g, tau);
+    const float gl = __frcp_rn(1.0f - Dl * tref), gh = __frcp_rn(1.0f - Dh * tref);
     float smin = 3.0e38f, smax = -3.0e38f;
     for (int i = 0; i < 4; i++) {
         const float D = (i & 1) ? Dh : Dl, t = (i & 2) ? th : tl;
-        const float s = __fdiv_rn(1.0f - D * t, 1.0f - D * tref);
+        const float s = (1.0f - D * t) * ((i & 1) ? gh : gl);
         smin = fminf(smin, s);
         smax = fmaxf(smax, s);
     }
@@ -285,8 +289,8 @@ __device__ void bucket_event_range(const Geom& g, const int32_t* row_off, float 
     smax *= 1.0f + 1e-4f;
     const float A = (float)y0 - 0.5625f - g.fy;
     const float B = (float)(y1 - 1) + 0.5625f - g.fy;
-    const float dylo = __fdiv_rn(A, A >= 0.0f ? smax : smin);
-    const float dyhi = __fdiv_rn(B, B >= 0.0f ? smin : smax);
+    const float dylo = A * __frcp_rn(A >= 0.0f ? smax : smin);
+    const float dyhi = B * __frcp_rn(B >= 0.0f ? smin : smax);
     // The margins above exceed the few-ulp error of this arithmetic, and
     // rounding a bound that is off by less than a row outward to an integer
     // row never drops a row the exact bound admits.
@@ -467,16 +471,26 @@ struct UnitPtrs {
 
 // Eqs. (16) and (19) for the unit's share of events, positions [f_begin,
 // total): Hbar into the tile, N_full into `full`, and (sparse) S and C.
-// Per-warp rings of queued long segments (see bound_pass).
-struct __align__(16) SegQueue {
-    int e[MAX_WARPS * QUEUE];
-    float sa[MAX_WARPS * QUEUE], sb[MAX_WARPS * QUEUE];
-    int x[MAX_WARPS * QUEUE], y[MAX_WARPS * QUEUE];
+// Per-warp rings of queued long segments (see bound_pass): QUEUE records of
+// five words (event, s_a, s_b, both end cells' x, both end cells' y) per warp
+// of the block, in dynamic shared memory after the tile (so a block's ring
+// memory grows with its warps: 1,280 bytes per warp).
+constexpr int QREC = 5;
+struct SegQueue {
+    int* rec;       // [warps * QUEUE][QREC]
+    int cap;        // warps * QUEUE records
 };
+
+// Dynamic shared memory of a k_eval block: the band tile (rounded up to 16
+// bytes) and the segment rings of its warps.
+__host__ __device__ inline int eval_tile_words(const Geom& g) { return (g.band_rows * tile_pitch(g) + 3) & ~3; }
+__host__ __device__ inline size_t eval_smem_bytes(const Geom& g, int threads) {
+    return sizeof(uint32_t) * (size_t)eval_tile_words(g) + sizeof(int) * (size_t)QREC * QUEUE * (threads / 32);
+}
 
 template <int MODE>
 __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, const Task& tk, float tau, uint32_t* tile,
-                                           SegQueue& queue, int y0, int y1, int f_begin, int total, Cursor& cur,
+                                           SegQueue queue, int y0, int y1, int f_begin, int total, Cursor& cur,
                                            unsigned long long& S, unsigned long long& C, unsigned long long& full) {
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -533,11 +547,11 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
     const int qb = wid * QUEUE;
     int q_head = 0, q_tail = 0;
     auto take = [&](int i, int& e, float& sa, float& sb, int& xa, int& ya, int& xb, int& yb) {
-        const int k = qb + (i & (QUEUE - 1));
-        e = queue.e[k];
-        sa = queue.sa[k];
-        sb = queue.sb[k];
-        const int px = queue.x[k], py = queue.y[k];
+        const int* r = queue.rec + QREC * (qb + (i & (QUEUE - 1)));
+        e = r[0];
+        sa = __int_as_float(r[1]);
+        sb = __int_as_float(r[2]);
+        const int px = r[3], py = r[4];
         xa = (int)(short)(px & 0xFFFF);
         xb = px >> 16;
         ya = (int)(short)(py & 0xFFFF);
@@ -596,12 +610,12 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
         }
         const unsigned pm = __ballot_sync(0xffffffffu, pend);
         if (pend) {
-            const int k = qb + ((q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1));
-            queue.e[k] = e;
-            queue.sa[k] = sa;
-            queue.sb[k] = sb;
-            queue.x[k] = (xa & 0xFFFF) | (xb << 16);
-            queue.y[k] = (ya & 0xFFFF) | (yb << 16);
+            int* r = queue.rec + QREC * (qb + ((q_tail + __popc(pm & ((1u << lane) - 1u))) & (QUEUE - 1)));
+            r[0] = e;
+            r[1] = __float_as_int(sa);
+            r[2] = __float_as_int(sb);
+            r[3] = (xa & 0xFFFF) | (xb << 16);
+            r[4] = (ya & 0xFFFF) | (yb << 16);
         }
         q_tail += __popc(pm);
         if (q_tail - q_head >= 32) {
@@ -635,7 +649,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
 // clears the accumulated band.  The tile arrives zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
-                                          int* erange, int* s_last, SegQueue& queue) {
+                                          int* erange, int* s_last, SegQueue queue) {
     // Unit ti is row band `band` of polarity plane `plane`: the plane's own
     // run of sorted events, its own image and its own counts.
     const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
@@ -824,21 +838,20 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
 
 // The bound's work for one event (Eqs. 16 and 19 restricted to the tile rows
 // [y0, y1)), as bound_pass does it, with the event's own lane walking its
-// segment: the widened scale range over [Dl, Dh], the end cells, N_full into
-// F and the covered cells.  BUMP_UNDO takes back exactly the increments an
-// earlier BUMP_SPARSE call made for the same event and interval.
+// segment: from its offsets (dx, dy) and its binary32 scales at the
+// interval's ends (sl, sh), the widened scale range, the end cells, N_full
+// into F and the covered cells.  BUMP_UNDO takes back exactly the increments
+// an earlier BUMP_SPARSE call made for the same event and interval.
 template <int MODE>
-__device__ __forceinline__ void bound_event(const Geom& g, const UnitPtrs& p, int e, float Dl, float gl, float Dh,
-                                            float gh, int y0, int y1, uint32_t* tile, unsigned long long& S,
+__device__ __forceinline__ void bound_event(const Geom& g, const UnitPtrs& p, int e, float dx, float dy, float sl,
+                                            float sh, int y0, int y1, uint32_t* tile, unsigned long long& S,
                                             uint32_t& C, uint32_t& F) {
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
-    const Ev v = p.ev[e];
-    const float sl = warp_s(Dl, v.t, gl), sh = warp_s(Dh, v.t, gh);
     const float sa = __fmul_rn(sl < sh ? sl : sh, WIDEN_DN);
     const float sb = __fmul_rn(sl < sh ? sh : sl, WIDEN_UP);
-    const int ya = cell_of(g.fy, v.dy, sa), yb = cell_of(g.fy, v.dy, sb);
+    const int ya = cell_of(g.fy, dy, sa), yb = cell_of(g.fy, dy, sb);
     if (max(ya, yb) < y0 || min(ya, yb) >= y1) return;
-    const int xa = cell_of(g.fx, v.dx, sa), xb = cell_of(g.fx, v.dx, sb);
+    const int xa = cell_of(g.fx, dx, sa), xb = cell_of(g.fx, dx, sb);
     const bool ya_here = (unsigned)(ya - y0) < (unsigned)rows;
     if (MODE != BUMP_UNDO && (unsigned)xa < (unsigned)W && (unsigned)xb < (unsigned)W && (unsigned)yb < (unsigned)g.H &&
         ya_here)
@@ -853,27 +866,25 @@ __device__ __forceinline__ void bound_event(const Geom& g, const UnitPtrs& p, in
             bump<MODE>(&tile[(yb - y0) * P + xb], S, C);
     } else {
         const float2 r = p.rcp[e];
-        const Seg sg = seg_range(g, v.dx, v.dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
+        const Seg sg = seg_range(g, dx, dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
         for (int i = 0; i < sg.count; i++)
             seg_cell<MODE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, C);
     }
 }
 
-// The contrast at D for one event (Eqs. 11-12) restricted to the tile rows.
+// The contrast's work for one event (Eqs. 11-12) restricted to the tile rows,
+// from its offsets and its binary32 scale.
 template <int MODE>
-__device__ __forceinline__ void point_event(const Geom& g, const Ev& v, float D, float gD, int y0, int y1,
+__device__ __forceinline__ void point_event(const Geom& g, float dx, float dy, float sc, int y0, int y1,
                                             uint32_t* tile, unsigned long long& S, uint32_t& C) {
     const int rows = y1 - y0, P = tile_pitch(g);
-    const float sc = warp_s(D, v.t, gD);
-    const int uy = cell_of(g.fy, v.dy, sc);
+    const int uy = cell_of(g.fy, dy, sc);
     if ((unsigned)(uy - y0) >= (unsigned)rows) return;
-    const int ux = cell_of(g.fx, v.dx, sc);
+    const int ux = cell_of(g.fx, dx, sc);
     if ((unsigned)ux < (unsigned)g.W && DD_IN((uy - y0) * P + ux, rows * P, 1u))
         bump<MODE>(&tile[(uy - y0) * P + ux], S, C);
 }
 
-// Unstable events a fused unit can list (the long-segment queue's memory).
-constexpr int FUSE_LIST = (int)(sizeof(SegQueue) / sizeof(int));
 
 // One fused unit: the three tasks of one expanded interval [lo, hi] with
 // centre c -- the contrast at c (Eqs. 11-13) and the bounds over [lo, c] and
@@ -895,7 +906,7 @@ constexpr int FUSE_LIST = (int)(sizeof(SegQueue) / sizeof(int));
 // the list holds runs as three ordinary units instead.
 __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp, const Task& tl, const Task& tr,
                                 Partial* part_p, Partial* part_l, Partial* part_r, int ti, float tau, uint32_t* tile,
-                                unsigned long long (*red)[32], int* erange, int* s_n, int* s_last, SegQueue& queue) {
+                                unsigned long long (*red)[32], int* erange, int* s_n, int* s_last, SegQueue queue) {
     const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
     const int y0 = band * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
     const int32_t* row_off = p.row_off + (size_t)plane * g.n_tb * g.H;
@@ -919,7 +930,8 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
     Cursor cur(erange, MAX_TB);
     const float tref = warp_tref(g, tau);
     const float glo = warp_g(lo, tref), gc = warp_g(c, tref), ghi = warp_g(hi, tref);
-    int* list = reinterpret_cast<int*>(&queue);
+    int* list = queue.rec;                        // unstable events (the segment rings' memory)
+    const int list_cap = QREC * queue.cap;
 
     // Pass over the candidates: stable events into the tile, the rest listed.
     unsigned long long SC = 0;
@@ -952,12 +964,12 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
             if (lane == 0) at = atomicAdd(s_n, __popc(m));
             at = __shfl_sync(0xffffffffu, at, 0);
             const int pos = at + __popc(m & ((1u << lane) - 1u));
-            if (uns && pos < FUSE_LIST) list[pos] = e;
+            if (uns && pos < list_cap) list[pos] = e;
         }
     }
     __syncthreads();
     const int n = *s_n;
-    if (n > FUSE_LIST) {                          // too many unstable events: three ordinary units
+    if (n > list_cap) {                           // too many unstable events: three ordinary units
         const int words = rows * P;
         for (int i = threadIdx.x; i < words; i += blockDim.x) tile[i] = 0u;
         __syncthreads();
@@ -971,23 +983,49 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
         return;
     }
     // Each task's own increments for the unstable events, on top of the
-    // common counts: the centre, then the left half, then the right half.
+    // common counts: the centre, then the left half, then the right half.  A
+    // thread's first listed event stays in registers (offsets and its three
+    // scales) through the five passes; further ones are read again.
     unsigned long long Sp = 0, Sl = 0, Sr = 0, Sx = 0;
     uint32_t Cp = 0, Cl = 0, Cr = 0, Fl = 0, Fr = 0, Cx = 0, Fx = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        point_event<BUMP_SPARSE>(g, p.ev[list[i]], c, gc, y0, y1, tile, Sp, Cp);
+    int e1 = -1;
+    float ex = 0.0f, ey = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    if ((int)threadIdx.x < n) {
+        e1 = list[threadIdx.x];
+        const Ev v = p.ev[e1];
+        ex = v.dx;
+        ey = v.dy;
+        s1 = warp_s(lo, v.t, glo);
+        s2 = warp_s(c, v.t, gc);
+        s3 = warp_s(hi, v.t, ghi);
+    }
+    auto each = [&](auto&& f) {
+        if (e1 >= 0) f(e1, ex, ey, s1, s2, s3);
+        for (int i = threadIdx.x + blockDim.x; i < n; i += blockDim.x) {
+            const int e = list[i];
+            const Ev v = p.ev[e];
+            f(e, v.dx, v.dy, warp_s(lo, v.t, glo), warp_s(c, v.t, gc), warp_s(hi, v.t, ghi));
+        }
+    };
+    each([&](int, float dx, float dy, float, float b, float) {
+        point_event<BUMP_SPARSE>(g, dx, dy, b, y0, y1, tile, Sp, Cp);
+    });
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        point_event<BUMP_UNDO>(g, p.ev[list[i]], c, gc, y0, y1, tile, Sx, Cx);
+    each([&](int, float dx, float dy, float, float b, float) {
+        point_event<BUMP_UNDO>(g, dx, dy, b, y0, y1, tile, Sx, Cx);
+    });
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        bound_event<BUMP_SPARSE>(g, p, list[i], lo, glo, c, gc, y0, y1, tile, Sl, Cl, Fl);
+    each([&](int e, float dx, float dy, float a, float b, float) {
+        bound_event<BUMP_SPARSE>(g, p, e, dx, dy, a, b, y0, y1, tile, Sl, Cl, Fl);
+    });
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        bound_event<BUMP_UNDO>(g, p, list[i], lo, glo, c, gc, y0, y1, tile, Sx, Cx, Fx);
+    each([&](int e, float dx, float dy, float a, float b, float) {
+        bound_event<BUMP_UNDO>(g, p, e, dx, dy, a, b, y0, y1, tile, Sx, Cx, Fx);
+    });
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        bound_event<BUMP_SPARSE>(g, p, list[i], c, gc, hi, ghi, y0, y1, tile, Sr, Cr, Fr);
+    each([&](int e, float dx, float dy, float, float b, float d) {
+        bound_event<BUMP_SPARSE>(g, p, e, dx, dy, b, d, y0, y1, tile, Sr, Cr, Fr);
+    });
     __syncthreads();
 
     // The tile leaves zeroed (its padding column stays zero): 16-byte words,
@@ -999,7 +1037,7 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
         for (int i = 4 * quads + threadIdx.x; i < words; i += blockDim.x) tile[i] = 0u;
     }
     // Sums of the three tasks: per warp, then per block (in the list's memory).
-    unsigned long long* wsum = reinterpret_cast<unsigned long long*>(&queue);   // [8][MAX_WARPS]
+    unsigned long long* wsum = reinterpret_cast<unsigned long long*>(queue.rec);   // [8][MAX_WARPS]
     auto put = [&](int k, unsigned long long x) {
         x = warp_sum(x);
         if (lane == 0) wsum[k * MAX_WARPS + wid] = x;
@@ -1030,7 +1068,6 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
 // list and counter for the control blocks of this round.
 __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     extern __shared__ __align__(16) uint32_t tile[];
-    __shared__ SegQueue queue;
     __shared__ unsigned long long red[3][32];
     __shared__ int erange[2 * MAX_TB + 1];
     __shared__ int s_unit, s_last, s_n;
@@ -1045,6 +1082,9 @@ __global__ void __launch_bounds__(512, 3) k_eval(Geom g, EvalArgs a) {
     int32_t* work = &sch->work[par];
     const Job* jobs = a.jobs + (size_t)par * a.job_stride;
     const int tile_words = g.band_rows * tile_pitch(g);
+    SegQueue queue;
+    queue.rec = reinterpret_cast<int*>(tile + eval_tile_words(g));
+    queue.cap = (int)(blockDim.x >> 5) * QUEUE;
     const int bins1 = bins_of(g) + 1;
     const size_t task_cells = (size_t)g.planes * g.W * g.H;
     // Block b starts with unit b; later units come from the counter, which
@@ -1110,7 +1150,7 @@ cudaError_t check_flags(uint32_t* flags, int32_t* checked, bool reset) {
 
 int eval_resident_blocks(const Geom& g, int threads) {
     int per_sm = 0, dev = 0, sms = 0;
-    size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
+    const size_t smem = eval_smem_bytes(g, threads);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval, threads, smem) != cudaSuccess) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
@@ -1119,8 +1159,7 @@ int eval_resident_blocks(const Geom& g, int threads) {
 
 cudaError_t launch_eval(const Geom& g, const EvalArgs& a, int threads, int grid_blocks, cudaStream_t s) {
     if (grid_blocks <= 0) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)g.band_rows * tile_pitch(g) * sizeof(uint32_t);
-    k_eval<<<grid_blocks, threads, smem, s>>>(g, a);
+    k_eval<<<grid_blocks, threads, eval_smem_bytes(g, threads), s>>>(g, a);
     return cudaGetLastError();
 }
 
@@ -1772,7 +1811,7 @@ cudaError_t eval_smem_setup(const Geom& g) {
         }
         g_carveout[dev] = true;
     }
-    const int bytes = g.band_rows * tile_pitch(g) * (int)sizeof(uint32_t);
+    const int bytes = (int)eval_smem_bytes(g, 32 * MAX_WARPS);   // any block size up to 512 threads
     if (bytes <= g_smem_bytes[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) g_smem_bytes[dev] = bytes;

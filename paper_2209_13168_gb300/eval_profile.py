@@ -30,11 +30,17 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--window", default="config2", choices=["config2", "descent"])
     ap.add_argument("--warmup", type=int, default=0, help="untimed graph solves first (not seen as rounds)")
+    ap.add_argument("--fuse-span", type=int, default=None, help="dd_config.fuse_span (default: the tuned value)")
+    for k in ("band-rows", "threads", "pop-k", "max-splits"):
+        ap.add_argument("--" + k, type=int, default=None, help="override the tuned " + k.replace("-", "_"))
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     w, params, mode, pop_k = window(a.window)
     kw = {"pop_k": pop_k} if pop_k else {}
+    for k in ("fuse_span", "band_rows", "threads", "pop_k", "max_splits"):
+        if getattr(a, k) is not None:
+            kw[k] = getattr(a, k)
     ctx = dd.Context.tuned(w.W, w.H, w.foe_x, w.foe_y, w.n, mode=mode, **kw)
     ev = dd.Events.of(w, device="cuda")
     for _ in range(a.warmup):
