@@ -370,6 +370,10 @@ def run_extras(dd, torch):
     out["serving"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8, windows=sw)
     out["serving"]["workload"] = ("4 descents at 1280x720, 189 windows each (0.2 s every 0.1 s of flight, 50k-833k "
                                   "events), Poisson arrivals at 40 windows/s per stream (4x real time)")
+    # the same with every window's events in pinned host memory: each latency
+    # includes its upload (copied on a copy stream while other windows run)
+    out["serving_host_inputs"] = serve_bench.run(rate_hz=40.0, n_streams=4, check=8, windows=sw, host=True)
+    out["serving_host_inputs"]["workload"] = out["serving"]["workload"] + "; inputs in pinned host memory"
     out["serving_sweep"] = []
     for rate in (10.0, 20.0, 80.0, 160.0):
         r = serve_bench.run(rate_hz=rate, n_streams=4, check=0, windows=sw)

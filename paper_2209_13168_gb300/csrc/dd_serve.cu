@@ -4,8 +4,11 @@
 // events with its whole search state (sorted events, row tables, queue,
 // tasks, partials).  One host thread runs the loop:
 //   1. admit: every request whose arrival time has passed takes a free slot;
-//      its events are copied in, sorted, and its search starts (its first
-//      jobs join the job list of the next round);
+//      device-resident events are sorted and its search starts (its first
+//      jobs join the job list of the next round); host-array events are
+//      first copied into the slot by an upload thread on a copy stream, so
+//      the rounds of the other windows go on meanwhile, and the search starts
+//      between rounds once the copy has landed;
 //   2. one round over all busy slots: a single evaluation launch for the jobs
 //      of every busy window, then one control block per slot;
 //   3. retire: windows that finished hand back their result and free their
@@ -58,7 +61,15 @@ struct dd_server {
     int64_t E = 0;
     int bins = 0, max_chunks = 0;
     bool cancel_pending = false;  // a running request was cancelled (under mu)
+    bool up_stop = false;         // the upload thread ends (under mu)
+    int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // host-array uploads
+    std::vector<cudaEvent_t> up_ev;       // per slot: its uploaded events have landed
+    std::vector<int> up_state;            // per slot: 0 none, 1 waiting for the upload thread, 2 copies
+                                          // issued (under mu)
+    std::deque<int> up_queue;             // slots for the upload thread (under mu)
+    std::thread up_th;
 
     // device, per slot
     dd::Ev* ev = nullptr;
@@ -81,7 +92,7 @@ struct dd_server {
     dd::MlpDev model{};
     bool has_model = false;
 
-    // pinned host
+    // pinned host (window descriptors and parameters staged per slot)
     int32_t* h_phase = nullptr;
     dd::SolveState* h_st = nullptr;
     dd::WinIn* h_win = nullptr;
@@ -143,6 +154,11 @@ void free_server(dd_server* s) {
     release_host(s->h_par);
     if (s->stream) cudaStreamDestroy(s->stream);
     s->stream = nullptr;
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    s->copy_stream = nullptr;
+    for (cudaEvent_t e : s->up_ev)
+        if (e) cudaEventDestroy(e);
+    s->up_ev.clear();
 }
 
 size_t slot_bytes(const dd_server* s) {
@@ -186,10 +202,15 @@ int alloc_server(dd_server* s) {
     A((void**)&s->feat_counts, sizeof(int32_t) * dd::FEATURES);
     AH((void**)&s->h_phase, sizeof(int32_t) * S);
     AH((void**)&s->h_st, sizeof(dd::SolveState) * S);
-    AH((void**)&s->h_win, sizeof(dd::WinIn));
-    AH((void**)&s->h_par, sizeof(dd::WinParams));
+    AH((void**)&s->h_win, sizeof(dd::WinIn) * S);
+    AH((void**)&s->h_par, sizeof(dd::WinParams) * S);
     if (rc) return rc;
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return DD_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return DD_ERR_CUDA;
+    s->up_ev.assign(S, nullptr);
+    s->up_state.assign(S, 0);
+    for (size_t k = 0; k < S; k++)
+        if (cudaEventCreateWithFlags(&s->up_ev[k], cudaEventDisableTiming) != cudaSuccess) return DD_ERR_CUDA;
     // Every slot starts free: a finished search takes no part in a round.
     std::memset(s->h_st, 0, sizeof(dd::SolveState) * S);
     for (size_t w = 0; w < S; w++) s->h_st[w].phase = dd::PH_DONE;
@@ -203,31 +224,43 @@ int alloc_server(dd_server* s) {
     return DD_OK;
 }
 
-// Start the search of request r in slot k (all asynchronous on the stream).
-cudaError_t admit(dd_server* s, int k, const Request& r) {
+// Copy the host-array events of request r into slot k's input buffers on
+// the copy stream (the calling thread blocks only while pageable memory is
+// staged; pinned memory returns at once) and mark their arrival with the
+// slot's event.
+cudaError_t upload(dd_server* s, int k, const Request& r) {
     const dd_events& e = r.ev;
-    dd::WinIn& wi = *s->h_win;
+    const size_t off = (size_t)k * s->E;
+    cudaError_t c = cudaSuccess;
+    if (e.n > 0) {
+        c = cudaMemcpyAsync(s->in_x + off, e.x, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice, s->copy_stream);
+        if (c == cudaSuccess)
+            c = cudaMemcpyAsync(s->in_y + off, e.y, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice, s->copy_stream);
+        if (c == cudaSuccess)
+            c = cudaMemcpyAsync(s->in_t + off, e.t, sizeof(float) * e.n, cudaMemcpyHostToDevice, s->copy_stream);
+        if (c == cudaSuccess && s->g.planes > 1)
+            c = cudaMemcpyAsync(s->in_p + off, e.p, sizeof(int8_t) * e.n, cudaMemcpyHostToDevice, s->copy_stream);
+    }
+    if (c == cudaSuccess) c = cudaEventRecord(s->up_ev[k], s->copy_stream);
+    return c;
+}
+
+// Start the search of request r in slot k (all asynchronous on the serving
+// stream): host-array events are read from the slot's input buffers, where
+// the upload put them; device arrays in place.
+cudaError_t start_search(dd_server* s, int k, const Request& r) {
+    const dd_events& e = r.ev;
+    dd::WinIn& wi = s->h_win[k];
+    const size_t off = (size_t)k * s->E;
     wi.x = e.x;
     wi.y = e.y;
     wi.t = e.t;
     wi.p = s->g.planes > 1 ? e.p : nullptr;
-    const size_t off = (size_t)k * s->E;
     if (!e.device_ptrs && e.n > 0) {
-        cudaError_t c1 = cudaMemcpyAsync(s->in_x + off, e.x, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice, s->stream);
-        cudaError_t c2 = cudaMemcpyAsync(s->in_y + off, e.y, sizeof(int16_t) * e.n, cudaMemcpyHostToDevice, s->stream);
-        cudaError_t c3 = cudaMemcpyAsync(s->in_t + off, e.t, sizeof(float) * e.n, cudaMemcpyHostToDevice, s->stream);
-        if (c1 != cudaSuccess) return c1;
-        if (c2 != cudaSuccess) return c2;
-        if (c3 != cudaSuccess) return c3;
-        if (s->g.planes > 1) {
-            cudaError_t c4 = cudaMemcpyAsync(s->in_p + off, e.p, sizeof(int8_t) * e.n, cudaMemcpyHostToDevice,
-                                             s->stream);
-            if (c4 != cudaSuccess) return c4;
-            wi.p = s->in_p + off;
-        }
         wi.x = s->in_x + off;
         wi.y = s->in_y + off;
         wi.t = s->in_t + off;
+        if (s->g.planes > 1) wi.p = s->in_p + off;
     }
     wi.n = e.n;
     wi.ev_off = (int64_t)off;
@@ -235,7 +268,7 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
     wi.tau = e.tau;
     wi.chunk0 = 0;
     wi.pad = 0;
-    dd::WinParams& q = *s->h_par;
+    dd::WinParams& q = s->h_par[k];
     const double M = (double)s->g.W * s->g.H;
     q.gamma_K = (dd::i128)std::floor(r.p.gamma * M * M);
     q.D_lo = r.p.D_lo;
@@ -245,13 +278,12 @@ cudaError_t admit(dd_server* s, int k, const Request& r) {
     q.D_warm = r.p.warm == DD_WARM_GIVEN ? r.p.D_warm : 0.0f;
     q.w_warm = r.p.warm == DD_WARM_GIVEN ? r.p.w_warm : 0.0f;
     q.pad0 = q.pad1 = 0;
-    cudaError_t c = cudaMemcpyAsync(s->wins + k, s->h_win, sizeof(dd::WinIn), cudaMemcpyHostToDevice, s->stream);
+    // The slot's staging entries are rewritten only when the slot is started
+    // again, after this search has retired (a later synchronised round), so
+    // these copies need no wait.
+    cudaError_t c = cudaMemcpyAsync(s->wins + k, &wi, sizeof(dd::WinIn), cudaMemcpyHostToDevice, s->stream);
     if (c != cudaSuccess) return c;
-    c = cudaMemcpyAsync(s->params + k, s->h_par, sizeof(dd::WinParams), cudaMemcpyHostToDevice, s->stream);
-    if (c != cudaSuccess) return c;
-    // The pinned staging structs are reused by the next admission: wait for
-    // these two small copies.
-    c = cudaStreamSynchronize(s->stream);
+    c = cudaMemcpyAsync(s->params + k, &q, sizeof(dd::WinParams), cudaMemcpyHostToDevice, s->stream);
     if (c != cudaSuccess) return c;
     const int32_t n_chunks = (int32_t)((e.n + dd::CHUNK - 1) / dd::CHUNK);
     c = dd::launch_ingest(s->g, s->wins + k, 1, s->chunk_zero, n_chunks, s->ev, s->rcp,
@@ -312,6 +344,33 @@ void fail_all(dd_server* s, int status) {
     s->cv.notify_all();
 }
 
+// The upload thread: copies the host-array events of admitted requests into
+// their slots on the copy stream, so that the serving thread never waits for
+// a copy.
+void uploader(dd_server* s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        int k = -1;
+        Request r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return !s->up_queue.empty() || s->up_stop; });
+            if (s->up_queue.empty()) return;
+            k = s->up_queue.front();
+            s->up_queue.pop_front();
+            r = s->reqs[s->slot_req[k]];
+        }
+        const cudaError_t c = upload(s, k, r);
+        if (c != cudaSuccess) {
+            fail_all(s, DD_ERR_CUDA);
+            return;
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->up_state[k] = 2;
+        s->cv.notify_all();
+    }
+}
+
 void loop(dd_server* s) {
     const int64_t M = (int64_t)s->g.W * s->g.H;
     dd::EvalArgs a;
@@ -329,8 +388,9 @@ void loop(dd_server* s) {
     a.mg.acc = nullptr;
     a.mg.done = nullptr;
     a.mg.sums = nullptr;
+    cudaSetDevice(s->device);
     for (;;) {
-        std::vector<std::pair<int, uint64_t>> admits;
+        std::vector<std::pair<int, uint64_t>> starts;   // searches to start before this round
         int busy = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -345,13 +405,48 @@ void loop(dd_server* s) {
                     s->slot_req[k] = id;
                     r.slot = k;
                     r.state = 1;
-                    admits.emplace_back(k, id);
+                    s->admitted++;
+                    if (!r.ev.device_ptrs && r.ev.n > 0) {   // host arrays: to the upload thread first
+                        s->up_state[k] = 1;
+                        s->up_queue.push_back(k);
+                        s->cv.notify_all();
+                    } else {
+                        starts.emplace_back(k, id);
+                    }
+                }
+                // uploads that have landed: their searches start now (or,
+                // cancelled meanwhile, they finish without one)
+                int uploading = 0;
+                for (int k = 0; k < s->S; k++) {
+                    if (s->up_state[k] == 2 && cudaEventQuery(s->up_ev[k]) == cudaSuccess) {
+                        s->up_state[k] = 0;
+                        Request& r = s->reqs[s->slot_req[k]];
+                        if (r.cancel) {
+                            std::memset(&r.res, 0, sizeof(r.res));
+                            r.res.status = DD_ERR_CANCELLED;
+                            r.status = DD_ERR_CANCELLED;
+                            r.state = 2;
+                            r.done_t = now_s();
+                            s->slot_req[k] = 0;
+                            s->cv.notify_all();
+                        } else {
+                            starts.emplace_back(k, s->slot_req[k]);
+                        }
+                    }
+                    uploading += s->up_state[k] != 0;
                 }
                 busy = 0;
-                for (int k = 0; k < s->S; k++) busy += s->slot_req[k] != 0;
-                if (busy) break;
-                if (s->stopping && s->waiting.empty()) return;
-                if (s->waiting.empty()) {
+                int searching = 0;
+                for (int k = 0; k < s->S; k++) {
+                    busy += s->slot_req[k] != 0;
+                    searching += s->slot_req[k] != 0 && s->up_state[k] == 0;
+                }
+                if (searching) break;
+                if (s->stopping && s->waiting.empty() && !uploading) return;
+                if (uploading) {
+                    // nothing to evaluate until an upload lands
+                    s->cv.wait_for(lk, std::chrono::microseconds(20));
+                } else if (s->waiting.empty()) {
                     s->cv.wait(lk);
                 } else {
                     const double dt = s->reqs[s->waiting.front()].arrival - now_s();
@@ -359,17 +454,16 @@ void loop(dd_server* s) {
                 }
             }
         }
-        for (auto& ad : admits) {
+        for (auto& ad : starts) {
             Request r;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 r = s->reqs[ad.second];
             }
-            if (admit(s, ad.first, r) != cudaSuccess) {
+            if (start_search(s, ad.first, r) != cudaSuccess) {
                 fail_all(s, DD_ERR_CUDA);
                 return;
             }
-            s->admitted++;
         }
         if (busy > s->peak_busy) s->peak_busy = busy;
         // Cancelled running requests: their slots' searches stop at this
@@ -380,7 +474,7 @@ void loop(dd_server* s) {
             std::lock_guard<std::mutex> lk(s->mu);
             if (s->cancel_pending) {
                 for (int k = 0; k < s->S; k++) {
-                    if (!s->slot_req[k]) continue;
+                    if (!s->slot_req[k] || s->up_state[k]) continue;   // an upload's cancel is seen as it lands
                     Request& r = s->reqs[s->slot_req[k]];
                     if (r.cancel && !r.cancel_sent) {
                         r.cancel_sent = true;
@@ -414,7 +508,7 @@ void loop(dd_server* s) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
             for (int k = 0; k < s->S; k++)
-                if (s->slot_req[k] && s->h_phase[k] == dd::PH_DONE) done.push_back(k);
+                if (s->slot_req[k] && s->up_state[k] == 0 && s->h_phase[k] == dd::PH_DONE) done.push_back(k);
         }
         for (int k : done) {
             if (cudaMemcpyAsync(s->h_st + k, s->st + k, sizeof(dd::SolveState), cudaMemcpyDeviceToHost, s->stream) !=
@@ -454,6 +548,10 @@ int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server
     dd_server* s = new (std::nothrow) dd_server();
     if (!s) return DD_ERR_OOM;
     dd::ctx_info(ctx, &s->g, &s->threads, &s->eval_blocks, &s->max_tasks, &s->pop_k, &s->qcap, &s->max_rounds);
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return DD_ERR_NO_DEVICE;
+    }
     s->g.max_splits = 1;
     if (const dd_mlp* m = dd::ctx_warm_model(ctx)) {
         int dev = -1;
@@ -486,8 +584,21 @@ int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server
         return rc;
     }
     try {
+        s->up_th = std::thread(uploader, s);
+    } catch (...) {
+        free_server(s);
+        delete s;
+        return DD_ERR_OOM;
+    }
+    try {
         s->th = std::thread(loop, s);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->up_stop = true;
+            s->cv.notify_all();
+        }
+        s->up_th.join();
         free_server(s);
         delete s;
         return DD_ERR_OOM;
@@ -606,6 +717,12 @@ int dd_serve_stop(dd_server* s) {
         s->cv.notify_all();
     }
     if (s->th.joinable()) s->th.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->up_stop = true;
+        s->cv.notify_all();
+    }
+    if (s->up_th.joinable()) s->up_th.join();
     const int rc = s->failed;
     free_server(s);
     delete s;

@@ -126,3 +126,34 @@ def test_cancel_waiting_running_and_finished_requests():
         srv.cancel(t_done)                             # already collected
     srv.stop()
     ctx.close()
+
+
+def test_host_inputs_are_uploaded_beside_running_windows():
+    # Host-array windows are copied into their slots by the upload thread
+    # while device-resident windows run; their searches start once the copy
+    # has landed.  Every result equals the window solved alone; a host window
+    # cancelled right after submission ends cancelled, whether it was still
+    # waiting, uploading or running.
+    heavy = serve_config5(0, 188)
+    light = [serve_config5(1, 20 + 30 * i, n_scale=0.05) for i in range(4)]
+    ctx = dd.Context(1280, 720, 640.0, 360.0, pop_k=8)
+    solo = [ctx.solve(dd.Events.of(w, device="cuda"), *PARAMS) for w in light]
+    srv = dd.Server(ctx, max_slots=3, max_events=1 << 20)
+    tickets = [srv.submit(dd.Events.of(w, device=None if i % 2 == 0 else "cuda"), PARAMS)
+               for i, w in enumerate(light)]
+    t_heavy = srv.submit(dd.Events.of(heavy), PARAMS)
+    srv.cancel(t_heavy)
+    for t, want in zip(tickets, solo):
+        got = srv.wait(t)
+        for k in KEYS:
+            assert got[k] == want[k], k
+    with pytest.raises(dd.DDError) as e:
+        srv.wait(t_heavy)
+    assert e.value.status == dd.DD_ERR_CANCELLED
+    # an uncancelled host window after it: served, identical to its solo solve
+    want = ctx.solve(dd.Events.of(light[2], device="cuda"), *PARAMS)
+    got = srv.wait(srv.submit(dd.Events.of(light[2]), PARAMS))
+    for k in KEYS:
+        assert got[k] == want[k], k
+    srv.stop()
+    ctx.close()
