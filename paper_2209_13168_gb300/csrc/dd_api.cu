@@ -157,7 +157,7 @@ void drop_graph(dd_ctx* c) {
 }
 
 dd::EvalArgs eval_args(dd_ctx* c, uint32_t* iwe_out, bool single) {
-    dd::EvalArgs a;
+    dd::EvalArgs a{};
     a.ev = c->ev;
     a.rcp = c->rcp;
     a.row_off = c->row_off;

@@ -36,7 +36,8 @@ enum TaskKind : int32_t { TASK_POINT = 0, TASK_BOUND = 1 };
 
 // One evaluation: the contrast at D_lo (TASK_POINT) or the bound over
 // [D_lo, D_hi] (TASK_BOUND).  `splits` (>= 1) is how many blocks share each
-// of its row bands; it changes the schedule only, never the result.
+// of its row bands, each taking its own rows of the band; it changes the
+// schedule only, never the result.
 struct Task {
     float D_lo, D_hi;
     int32_t kind, splits;
@@ -181,6 +182,9 @@ __host__ __device__ inline float warp_tref(const Geom& g, float tau) { return g.
 // dense (their tiles are summed in one pass) and are the ones worth
 // splitting over several blocks.  A schedule estimate only.
 constexpr float DENSE_CELLS = 4.0f;
+// Split bands of bounds below SPLIT_ROWS_CELLS are divided by rows, longer
+// ones by events (see eval_unit).
+constexpr float SPLIT_ROWS_CELLS = 64.0f;
 __host__ __device__ inline float bound_cells(const Geom& g, float D_lo, float D_hi, float tau) {
     const float gl = 1.0f / (1.0f - D_lo * tau), gh = 1.0f / (1.0f - D_hi * tau);
     return 1.0f + (gh > gl ? gh - gl : gl - gh) * 0.25f * (float)(g.W + g.H);
@@ -192,13 +196,14 @@ __host__ __device__ inline float bound_cells(const Geom& g, float D_lo, float D_
 // (split_target blocks), the spare blocks go to the dense bound tasks as extra
 // splits, spread evenly (an extra split of a task adds n_tiles units), so the
 // round runs as one wave of shorter units; none once the round fills the grid
-// (other tasks never split: their units are short already).  A schedule
-// choice only.
+// (other tasks never split: their units are short already).  A split holds at
+// least one row of a band.  A schedule choice only.
 __host__ __device__ inline int32_t fill_splits(const Geom& g, int32_t units, int32_t nb, int32_t rank) {
     if (g.split_target <= 0 || nb <= 0 || units >= g.split_target) return 1;
     const int32_t extra = (g.split_target - units) / g.n_tiles;
     const int32_t s = 1 + extra / nb + (rank < extra % nb ? 1 : 0);
-    return s > g.max_splits ? g.max_splits : s;
+    const int32_t cap = g.max_splits < g.band_rows ? g.max_splits : g.band_rows;   // a split holds a row at least
+    return s > cap ? cap : s;
 }
 
 // Row pitch of a shared-memory IWE tile: odd, so that the cells of one
@@ -212,11 +217,30 @@ inline int32_t time_buckets(int32_t H) {
     return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
-// Merge buffers of split jobs (single-window searches only).
+// Merge buffers of event-split jobs (single-window searches only).
 struct Merge {
     uint32_t* acc;                 // [task][planes * M] counts, zero between uses
     int32_t* done;                 // [task][tile] finished splits, zero between uses
     Partial* sums;                 // [task][tile] sums of the splits, zero between uses
+};
+
+// Everything a control step (Algorithm 1's bookkeeping for a round) reads or
+// writes; one control block per window.
+struct CtlArgs {
+    int32_t n_windows;
+    struct SolveState* st_all;
+    struct Node* queues;
+    Task* tasks_all;
+    int32_t task_stride;
+    Partial* part_all;
+    const int32_t* err_all;
+    struct TraceRec* trace;
+    Job* jobs_all;
+    int32_t job_stride;
+    struct Sched* sch;
+    cudaGraphConditionalHandle loop;
+    int32_t use_loop, split_ok;
+    int32_t* phase_out;
 };
 
 // Everything an evaluation launch reads or writes.
@@ -254,6 +278,9 @@ cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* 
                         cudaStream_t s, int32_t w0 = 0, int32_t split_ok = -1);
 // One control block per window 0 .. n_windows - 1; phase_out (nullable)
 // receives each window's phase after the round.
+CtlArgs control_args(int32_t n_windows, SolveState* st, Node* queues, Task* tasks, int32_t task_stride, Partial* part,
+                     const int32_t* err, TraceRec* trace, Job* jobs, int32_t job_stride, Sched* sch,
+                     cudaGraphConditionalHandle loop, int32_t use_loop, int32_t split_ok, int32_t* phase_out);
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
                            int32_t task_stride, Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,

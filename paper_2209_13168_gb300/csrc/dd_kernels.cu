@@ -458,9 +458,9 @@ struct UnitPtrs {
     const int32_t* row_off;       // the window's bin offsets
     Partial* part;                // the task's sums (atomic accumulation over its row bands)
     uint32_t* out;                // nullable: the task's image [H][W]
-    uint32_t* acc;                // split jobs: the task's accumulator [H][W]
-    int32_t* done;                // split jobs: finished splits per tile
-    Partial* sums;                // split jobs: sums of the splits per tile
+    uint32_t* acc;                // event-split jobs: the task's accumulator [H][W]
+    int32_t* done;                // event-split jobs: finished splits per tile
+    Partial* sums;                // event-split jobs: sums of the splits per tile
 #ifdef DD_CHECKED
     int64_t n_ev;                 // the window's event count
 #endif
@@ -484,9 +484,7 @@ struct SegQueue {
 // Dynamic shared memory of a k_eval block: the band tile (rounded up to 16
 // bytes) and the segment rings of its warps.
 __host__ __device__ inline int eval_tile_words(const Geom& g) { return (g.band_rows * tile_pitch(g) + 3) & ~3; }
-__host__ __device__ inline size_t eval_smem_bytes(const Geom& g, int threads) {
-    return sizeof(uint32_t) * (size_t)eval_tile_words(g) + sizeof(int) * (size_t)QREC * QUEUE * (threads / 32);
-}
+__host__ __device__ inline size_t eval_smem_bytes(const Geom& g, int threads);
 
 template <int MODE>
 __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, const Task& tk, float tau, uint32_t* tile,
@@ -639,13 +637,19 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
 }
 
 // One unit: split `split` of `splits` of one task's row band `ti`.  The block
-// scatters its share of the events that can reach the band's rows into the
-// shared tile.  Sparse images: each increment returns the cell's previous
-// count v and the band's sum of squares grows by (v + 1)^2 - v^2 = 2v + 1,
-// so the tile is only cleared afterwards; dense bound images: one pass over
-// the tile takes S and C and clears it.  A split task adds its tile into the
-// L2 accumulator; each addition of u onto a count w adds (w + u)^2 - w^2 to
-// S, so the splits' sums add up to the band's, and the last split to finish
+// scatters the events that can reach its rows into the shared tile.  Sparse
+// images: each increment returns the cell's previous count v and the band's
+// sum of squares grows by (v + 1)^2 - v^2 = 2v + 1, so the tile is only
+// cleared afterwards; dense bound images: one pass over the tile takes S and
+// C and clears it.  A split band is divided by rows when its bound's segments
+// are short (bound_cells below SPLIT_ROWS_CELLS): split s owns rows
+// [y0 + R s/splits, y0 + R (s + 1)/splits) of the band's R rows and counts the
+// events that reach them in its own rows of the tile, so the splits share no
+// cell.  With long segments (where every thin slice would read nearly all of
+// the band's candidates) the band is divided by events instead: split s
+// takes its share of the band's candidates, adds its tile into the L2
+// accumulator, and each addition of u onto a count w adds (w + u)^2 - w^2 to
+// S, so the splits' sums add up to the band's; the last split to finish
 // clears the accumulated band.  The tile arrives zeroed and leaves zeroed.
 __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, const Task& tk, int ti, int split,
                                           int splits, float tau, uint32_t* tile, unsigned long long (*red)[32],
@@ -653,7 +657,10 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     // Unit ti is row band `band` of polarity plane `plane`: the plane's own
     // run of sorted events, its own image and its own counts.
     const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
-    const int y0 = band * g.band_rows, y1 = min(y0 + g.band_rows, g.H);
+    const bool by_rows = splits > 1 && bound_cells(g, tk.D_lo, tk.D_hi, tau) < SPLIT_ROWS_CELLS;
+    const int b0 = band * g.band_rows, R = min(b0 + g.band_rows, g.H) - b0;
+    const int y0 = by_rows ? b0 + (int)((long long)R * split / splits) : b0;
+    const int y1 = by_rows ? b0 + (int)((long long)R * (split + 1) / splits) : b0 + R;
     const int32_t* row_off = p.row_off + (size_t)plane * g.n_tb * g.H;
     const size_t plane_off = (size_t)plane * g.W * g.H;
     const int W = g.W, P = tile_pitch(g), rows = y1 - y0;
@@ -663,7 +670,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     // the run's offset in the concatenation of all runs (MAX_TB + n_tb: total).
     if (threadIdx.x < 32) {
         int e0 = 0, e1 = 0;
-        if (lane < g.n_tb)
+        if (lane < g.n_tb && y1 > y0)
             bucket_event_range(g, row_off, tk.D_lo, tk.D_hi, tau, __fdiv_rn((float)g.n_tb, tau), lane, y0, y1, e0,
                                e1);
         const int len = e1 - e0, incl = warp_incl_scan(len);
@@ -676,8 +683,8 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     __syncthreads();
     unsigned long long full = 0;
     const int all = erange[MAX_TB + g.n_tb];
-    const int f_begin = (int)((long long)all * split / splits);
-    const int total = (int)((long long)all * (split + 1) / splits);
+    const int f_begin = by_rows ? 0 : (int)((long long)all * split / splits);
+    const int total = by_rows ? all : (int)((long long)all * (split + 1) / splits);
     Cursor cur(erange, MAX_TB);
 
     unsigned long long S = 0, C = 0;
@@ -711,7 +718,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     unsigned long long Cl = C;
     // Tile rows have pitch P (odd), frame rows pitch W: warps take rows, lanes
     // take columns.
-    if (splits == 1) {
+    if (splits == 1 || by_rows) {
         if (out) {
             if (dense) S = Cl = 0;
             for (int r = wid; r < rows; r += nw)
@@ -1063,6 +1070,28 @@ __device__ void eval_fused_unit(const Geom& g, const UnitPtrs& p, const Task& tp
     }
 }
 
+constexpr int Q_STAGE = 256;   // queued intervals staged in shared memory for the merge
+
+// Shared memory of one control step (one block of k_control per window).
+struct __align__(16) CtlShared {
+    SolveState s;
+    i128 key[3 * MAX_POP];
+    unsigned long long cells[3 * MAX_POP];
+    Node kids[2 * MAX_POP + 1];
+    Node sorted_kids[2 * MAX_POP + 1];
+    Node q_stage[Q_STAGE];
+    Node q_head[MAX_POP];               // the merged queue's first entries, for the dequeue
+    float2 bound_iv[3 * MAX_POP];       // the next round's bound tasks' intervals
+    int16_t t_fuse[3 * MAX_POP];        // per next-round task: 0 own jobs, -1 part of a fused
+                                        // job, k > 0 the centre of a fused job (left half k - 1)
+    int s_nk, s_stop;
+};
+
+
+__host__ __device__ inline size_t eval_smem_bytes(const Geom& g, int threads) {
+    return sizeof(uint32_t) * (size_t)eval_tile_words(g) + sizeof(int) * (size_t)QREC * QUEUE * (threads / 32);
+}
+
 // IWE evaluation of the round's job list.  A grid of resident blocks takes
 // units (job, row band) from a counter; block 0 clears the other parity's
 // list and counter for the control blocks of this round.
@@ -1326,7 +1355,6 @@ __device__ __forceinline__ int rank_in(const Node* q, int n, const Node& e) {
 }
 
 constexpr int CTL_THREADS = 256;
-constexpr int Q_STAGE = 256;   // queued intervals staged in shared memory for the merge
 
 __device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
     unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
@@ -1352,25 +1380,30 @@ __device__ __forceinline__ i128 warp_max_i128(i128 v) {
 // merge into the other buffer, a dequeue takes a prefix.  The last block to
 // finish counts the windows still searching, advances the round and sets the
 // graph loop condition (with one window, its block does so directly).
-__global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windows, SolveState* st_all,
-                                                        Node* queues, Task* tasks_all, int32_t task_stride,
-                                                        Partial* part_all, const int32_t* err_all,
-                                                        TraceRec* trace, Job* jobs_all, int32_t job_stride,
-                                                        Sched* sch, cudaGraphConditionalHandle loop,
-                                                        int32_t use_loop, int32_t split_ok, int32_t* phase_out) {
-    __shared__ SolveState s;
-    __shared__ i128 key[3 * MAX_POP];
-    __shared__ unsigned long long cells[3 * MAX_POP];
-    __shared__ Node kids[2 * MAX_POP + 1];
-    __shared__ Node sorted_kids[2 * MAX_POP + 1];
-    __shared__ Node q_stage[Q_STAGE];
-    __shared__ Node q_head[MAX_POP];               // the merged queue's first entries, for the dequeue
-    __shared__ float2 bound_iv[3 * MAX_POP];      // the next round's bound tasks' intervals
-    __shared__ int16_t t_fuse[3 * MAX_POP];       // per next-round task: 0 own jobs, -1 part of a fused
-                                                  // job, k > 0 the centre of a fused job (left half k - 1)
-    __shared__ int s_nk, s_stop;
+__device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, int w, CtlShared& sm) {
+    SolveState& s = sm.s;
+    i128* key = sm.key;
+    unsigned long long* cells = sm.cells;
+    Node* kids = sm.kids;
+    Node* sorted_kids = sm.sorted_kids;
+    Node* q_stage = sm.q_stage;
+    Node* q_head = sm.q_head;
+    float2* bound_iv = sm.bound_iv;
+    int16_t* t_fuse = sm.t_fuse;
+    int& s_nk = sm.s_nk;
+    int& s_stop = sm.s_stop;
+    const int32_t n_windows = c.n_windows, task_stride = c.task_stride, job_stride = c.job_stride;
+    const int32_t use_loop = c.use_loop, split_ok = c.split_ok;
+    SolveState* st_all = c.st_all;
+    Node* queues = c.queues;
+    Task* tasks_all = c.tasks_all;
+    Partial* part_all = c.part_all;
+    const int32_t* err_all = c.err_all;
+    TraceRec* trace = c.trace;
+    Job* jobs_all = c.jobs_all;
+    Sched* sch = c.sch;
+    int32_t* phase_out = c.phase_out;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int w = blockIdx.x;
     const int par = sch->round & 1;
     SolveState* st = st_all + w;
     Task* tasks = tasks_all + (size_t)w * task_stride;
@@ -1757,7 +1790,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
         const int active = s.phase != PH_DONE ? 1 : 0;
         sch->running = active;
         sch->round += 1;
-        if (use_loop) cudaGraphSetConditional(loop, active ? 1u : 0u);
+        if (use_loop) cudaGraphSetConditional(c.loop, active ? 1u : 0u);
     } else if (tid == 0) {
         __threadfence();
         if (s.phase != PH_DONE) atomicAdd(&sch->active, 1);
@@ -1768,18 +1801,46 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, int32_t n_windo
             sch->active = 0;
             sch->ticket = 0;
             sch->round += 1;
-            if (use_loop) cudaGraphSetConditional(loop, active > 0 ? 1u : 0u);
+            if (use_loop) cudaGraphSetConditional(c.loop, active > 0 ? 1u : 0u);
         }
     }
+}
+
+__global__ void __launch_bounds__(CTL_THREADS) k_control(Geom g, CtlArgs c) {
+    __shared__ CtlShared sm;
+    control_body(g, c, blockIdx.x, sm);
+}
+
+
+CtlArgs control_args(int32_t n_windows, SolveState* st, Node* queues, Task* tasks, int32_t task_stride, Partial* part,
+                     const int32_t* err, TraceRec* trace, Job* jobs, int32_t job_stride, Sched* sch,
+                     cudaGraphConditionalHandle loop, int32_t use_loop, int32_t split_ok, int32_t* phase_out) {
+    CtlArgs c;
+    c.n_windows = n_windows;
+    c.st_all = st;
+    c.queues = queues;
+    c.tasks_all = tasks;
+    c.task_stride = task_stride;
+    c.part_all = part;
+    c.err_all = err;
+    c.trace = trace;
+    c.jobs_all = jobs;
+    c.job_stride = job_stride;
+    c.sch = sch;
+    c.loop = loop;
+    c.use_loop = use_loop;
+    c.split_ok = split_ok < 0 ? (n_windows == 1) : split_ok;
+    c.phase_out = phase_out;
+    return c;
 }
 
 cudaError_t launch_control(const Geom& g, int32_t n_windows, SolveState* st, Node* queues, Task* tasks,
                            int32_t task_stride, Partial* part, const int32_t* err, TraceRec* trace,
                            Job* jobs, int32_t job_stride, Sched* sch, cudaGraphConditionalHandle loop,
                            int32_t use_loop, cudaStream_t s, int32_t split_ok, int32_t* phase_out) {
-    if (split_ok < 0) split_ok = n_windows == 1;
-    k_control<<<n_windows, CTL_THREADS, 0, s>>>(g, n_windows, st, queues, tasks, task_stride, part, err, trace, jobs,
-                                                job_stride, sch, loop, use_loop, split_ok, phase_out);
+    const CtlArgs c = control_args(n_windows, st, queues, tasks, task_stride, part, err, trace, jobs, job_stride, sch,
+                                   loop, use_loop, split_ok, phase_out);
+    k_control<<<n_windows, CTL_THREADS, 0, s>>>(g, c);
     return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     if (dd::launch_ingest(g, win, 1, chunk_win, n_chunks, ev_sorted, rcp, row_count, row_off, cursor, err, s) !=
         cudaSuccess)
         return DD_ERR_CUDA;
-    dd::EvalArgs a;
+    dd::EvalArgs a{};
     a.ev = ev_sorted;
     a.rcp = rcp;
     a.row_off = row_off;
@@ -164,9 +164,6 @@ extern "C" int dd_contrast_noalloc(int32_t W, int32_t H, float foe_x, float foe_
     a.sch = sch;
     a.part = part;
     a.iwe_out = nullptr;
-    a.mg.acc = nullptr;
-    a.mg.done = nullptr;
-    a.mg.sums = nullptr;
     dd::Task h_tasks[NA_MAX_TASKS];
     dd::Job h_jobs[NA_MAX_TASKS];
     dd::Sched h_sch;

@@ -373,7 +373,7 @@ void uploader(dd_server* s) {
 
 void loop(dd_server* s) {
     const int64_t M = (int64_t)s->g.W * s->g.H;
-    dd::EvalArgs a;
+    dd::EvalArgs a{};
     a.ev = s->ev;
     a.rcp = s->rcp;
     a.row_off = s->row_off;
@@ -385,9 +385,6 @@ void loop(dd_server* s) {
     a.sch = s->sch;
     a.part = s->part;
     a.iwe_out = nullptr;
-    a.mg.acc = nullptr;
-    a.mg.done = nullptr;
-    a.mg.sums = nullptr;
     cudaSetDevice(s->device);
     for (;;) {
         std::vector<std::pair<int, uint64_t>> starts;   // searches to start before this round
