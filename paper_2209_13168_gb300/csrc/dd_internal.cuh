@@ -186,7 +186,12 @@ constexpr float DENSE_CELLS = 4.0f;
 // ones by events (see eval_unit).
 constexpr float SPLIT_ROWS_CELLS = 64.0f;
 __host__ __device__ inline float bound_cells(const Geom& g, float D_lo, float D_hi, float tau) {
+#ifdef __CUDA_ARCH__
+    // an estimate: fast reciprocals (deterministic, so every unit of a task agrees)
+    const float gl = __fdividef(1.0f, 1.0f - D_lo * tau), gh = __fdividef(1.0f, 1.0f - D_hi * tau);
+#else
     const float gl = 1.0f / (1.0f - D_lo * tau), gh = 1.0f / (1.0f - D_hi * tau);
+#endif
     return 1.0f + (gh > gl ? gh - gl : gl - gh) * 0.25f * (float)(g.W + g.H);
 }
 

@@ -1084,6 +1084,8 @@ struct __align__(16) CtlShared {
     float2 bound_iv[3 * MAX_POP];       // the next round's bound tasks' intervals
     int16_t t_fuse[3 * MAX_POP];        // per next-round task: 0 own jobs, -1 part of a fused
                                         // job, k > 0 the centre of a fused job (left half k - 1)
+    int8_t t_dense[3 * MAX_POP];        // per next-round task: a dense bound that may be split
+    int16_t t_jobs[3 * MAX_POP];        // per next-round task, in job order: its number of jobs
     int s_nk, s_stop;
 };
 
@@ -1390,6 +1392,8 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
     Node* q_head = sm.q_head;
     float2* bound_iv = sm.bound_iv;
     int16_t* t_fuse = sm.t_fuse;
+    int8_t* t_dense = sm.t_dense;
+    int16_t* t_jobs = sm.t_jobs;
     int& s_nk = sm.s_nk;
     int& s_stop = sm.s_stop;
     const int32_t n_windows = c.n_windows, task_stride = c.task_stride, job_stride = c.job_stride;
@@ -1684,12 +1688,16 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
                     a.splits = 1;
                     tasks[j] = a;
                     t_fuse[j] = 0;
+                    t_dense[j] = 0;
                     if (split) {
                         const int t = np + 2 * (nl_before + __popc(sb & ((1u << lane) - 1u)));
                         p.t_left = t;
                         p.t_right = t + 1;
                         t_fuse[j] = fuse ? (int16_t)(t + 1) : (int16_t)0;
                         t_fuse[t] = t_fuse[t + 1] = fuse ? (int16_t)-1 : (int16_t)0;
+                        // dense bounds (splittable when the round is small), decided once here
+                        t_dense[t] = split_ok && !fuse && bound_cells(g, p.lo, p.c, s.tau) >= DENSE_CELLS;
+                        t_dense[t + 1] = split_ok && !fuse && bound_cells(g, p.c, p.hi, s.tau) >= DENSE_CELLS;
                         Task l, r;
                         l.D_lo = p.lo;
                         l.D_hi = p.c;
@@ -1726,46 +1734,40 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
         // contributes that many jobs (fill_splits for the dense bounds, ranked
         // in this loop's order; every other task has one split).
         if (s.phase != PH_DONE) {
-            const int nt = s.n_tasks, np = s.n_pop;
-            auto dense_at = [&](int q) {
-                const int t = nt - 1 - q;
-                return split_ok && q < nt && t >= np && t_fuse[t] == 0 &&
-                       bound_cells(g, bound_iv[t].x, bound_iv[t].y, s.tau) >= DENSE_CELLS;
-            };
+            const int nt = s.n_tasks;
             int nd = 0, nabs = 0;                 // dense bound tasks; tasks inside fused jobs
             for (int c0 = 0; c0 < nt; c0 += 32) {
-                nd += __popc(__ballot_sync(0xffffffffu, dense_at(c0 + lane)));
-                nabs += __popc(__ballot_sync(0xffffffffu, c0 + lane < nt && t_fuse[nt - 1 - c0 - lane] < 0));
+                const int q = c0 + lane, t = nt - 1 - q;
+                nd += __popc(__ballot_sync(0xffffffffu, q < nt && t_dense[t]));
+                nabs += __popc(__ballot_sync(0xffffffffu, q < nt && t_fuse[t] < 0));
             }
             const int units = (nt - nabs) * g.n_tiles;   // one per job and band before any split
-            auto splits_at = [&](int q, int& seen) {
-                const bool d = dense_at(q);
+            int total = 0, seen = 0;
+            for (int c0 = 0; c0 < nt; c0 += 32) {     // jobs per task, counted once
+                const int q = c0 + lane, t = nt - 1 - q;
+                const bool d = q < nt && t_dense[t];
                 const unsigned db = __ballot_sync(0xffffffffu, d);
                 const int rank = seen + __popc(db & ((1u << lane) - 1u));
                 seen += __popc(db);
-                if (q >= nt || t_fuse[nt - 1 - q] < 0) return 0;
-                return d ? fill_splits(g, units, nd, rank) : 1;
-            };
-            int run = 0, base = 0;
-            int total = 0, seen = 0;
-            for (int c0 = 0; c0 < nt; c0 += 32) {
-                const int c = splits_at(c0 + lane, seen);
-                total += __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
+                const int c = q >= nt || t_fuse[t] < 0 ? 0 : (d ? fill_splits(g, units, nd, rank) : 1);
+                if (q < nt) t_jobs[q] = (int16_t)c;
+                total += __reduce_add_sync(0xffffffffu, (unsigned)c);
             }
+            int base = 0;
             if (lane == 0) {
                 if (n_windows == 1) {             // the only block: the list is its own
                     sch->n_jobs[par ^ 1] = total;
-                    base = 0;
                 } else {
                     base = atomicAdd(&sch->n_jobs[par ^ 1], total);
                 }
             }
             base = __shfl_sync(0xffffffffu, base, 0);
-            seen = 0;
+            __syncwarp();
+            int run = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {
                 const int q = c0 + lane;
                 const int t = nt - 1 - q;
-                const int c = splits_at(q, seen);
+                const int c = q < nt ? (int)t_jobs[q] : 0;
                 const int incl = warp_incl_scan(c);
                 const int fz = c > 0 ? (int)t_fuse[t] : 0;
                 for (int k = 0; k < c; k++) {
