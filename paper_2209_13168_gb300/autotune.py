@@ -152,7 +152,8 @@ def fast_mode_windows(W2=160, H2=90, keep=0.25, step=20):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_TABLE)
-    ap.add_argument("--quick", action="store_true", help="fewer candidates")
+    ap.add_argument("--quick", action="store_true",
+                    help="fewer candidates: the band heights, block sizes, pop widths and split caps that won on this GPU")
     ap.add_argument("--reps", type=int, default=3, help="timed repetitions per candidate (single windows)")
     ap.add_argument("--only", default=None, help="tune only the jobs whose name contains this (e.g. 1280x720)")
     args = ap.parse_args()
@@ -164,8 +165,8 @@ def main():
     table = load_table(args.out)
     cand = None
     if args.quick:
-        cand = {"band_rows": [16, 38], "threads": [256, 512], "pop_k": [16, 32], "max_splits": [8, 16],
-                "fuse_span": [-1, 25]}
+        cand = {"band_rows": [12, 16, 20, 24], "threads": [256, 512], "pop_k": [16, 32, 64], "max_splits": [8, 16],
+                "fuse_span": [-1, 15, 25, 40, 70]}
     from synth.descent import serve_config5
     jobs = [("single", [window_config1()]), ("single", [window_config2()])]
     params = batch_params3()
