@@ -180,8 +180,9 @@ __host__ __device__ inline float warp_tref(const Geom& g, float tau) { return g.
 // scale change at t = 0, |g(D_hi) - g(D_lo)| with g = 1/(1 - D tau), times a
 // typical offset from the FOE, (W + H)/4.  Bounds of at least DENSE_CELLS are
 // dense (their tiles are summed in one pass) and are the ones worth
-// splitting over several blocks.  A schedule estimate only.
-constexpr float DENSE_CELLS = 4.0f;
+// splitting over several blocks.  A schedule estimate only (the threshold
+// and the per-lane walk limit in bound_pass were set by measurement).
+constexpr float DENSE_CELLS = 2.0f;
 // Split bands of bounds below SPLIT_ROWS_CELLS are divided by rows, longer
 // ones by events (see eval_unit).
 constexpr float SPLIT_ROWS_CELLS = 64.0f;

@@ -510,7 +510,7 @@ __device__ __forceinline__ void bound_pass(const Geom& g, const UnitPtrs& p, con
             sg = seg_range(g, v.dx, v.dy, r.x, r.y, sa, sb, xa, ya, xb, yb, y0, y1);
         }
         const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)sg.count);
-        if (cmax <= 2) {
+        if (cmax <= 4) {                       // short runs: each lane walks its own
             for (int i = 0; i < sg.count; i++)
                 seg_cell<MODE>(g, sg.mode, sg.k0 + i, sg.dn, sg.rm, sg.sa, sg.sb, sg.addr, y0, y1, tile, S, Ci);
             C += Ci;
