@@ -210,8 +210,8 @@ int ensure_windows(dd_ctx* c, int nw) {
     release_host(c->h_params);
     release_host(c->h_err);
     c->win_cap = 0;
-    const int js = cap * c->max_tasks > c->max_tasks * c->g.max_splits ? cap * c->max_tasks
-                                                                        : c->max_tasks * c->g.max_splits;
+    const int jw = cap * dd::jobs_per_window(c->g, c->max_tasks);
+    const int js = jw > c->max_tasks * c->g.max_splits ? jw : c->max_tasks * c->g.max_splits;
     int rc = DD_OK;
     auto A = [&](void** p, size_t bytes) {
         if (rc == DD_OK && cudaMalloc(p, bytes) != cudaSuccess) rc = DD_ERR_OOM;
@@ -359,7 +359,7 @@ int eval_tasks(dd_ctx* c, const dd_events* ev, int32_t n, int kind, const float*
             t.D_hi = B[j0 + j];
             t.kind = kind;
             const bool dense = kind == dd::TASK_BOUND && dd::bound_cells(c->g, t.D_lo, t.D_hi, ev->tau) >= dd::DENSE_CELLS;
-            t.splits = dense ? dd::fill_splits(c->g, m * c->g.n_tiles, n_dense, rank++) : 1;
+            t.splits = dense ? dd::fill_splits(c->g, c->g.split_target, m * c->g.n_tiles, n_dense, rank++) : 1;
         }
         for (int32_t j = m - 1; j >= 0; j--)              // heavier tasks first
             for (int32_t s = 0; s < c->h_tasks[j].splits; s++) {

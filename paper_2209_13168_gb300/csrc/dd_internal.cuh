@@ -196,20 +196,29 @@ __host__ __device__ inline float bound_cells(const Geom& g, float D_lo, float D_
     return 1.0f + (gh > gl ? gh - gl : gl - gh) * 0.25f * (float)(g.W + g.H);
 }
 
-// Splits of dense bound task `rank` (0-based among the round's nb dense
-// bound tasks) in a round of `units` unsplit (task, row band) units: when the
-// round alone does not fill one wave of the resident evaluation grid
-// (split_target blocks), the spare blocks go to the dense bound tasks as extra
-// splits, spread evenly (an extra split of a task adds n_tiles units), so the
-// round runs as one wave of shorter units; none once the round fills the grid
-// (other tasks never split: their units are short already).  A split holds at
-// least one row of a band.  A schedule choice only.
-__host__ __device__ inline int32_t fill_splits(const Geom& g, int32_t units, int32_t nb, int32_t rank) {
-    if (g.split_target <= 0 || nb <= 0 || units >= g.split_target) return 1;
-    const int32_t extra = (g.split_target - units) / g.n_tiles;
+// Splits of dense bound task `rank` (0-based among the window's nb dense
+// bound tasks) in a round of `units` unsplit (task, row band) units of the
+// window: when they do not fill the window's share of one wave of the
+// resident evaluation grid (`target` blocks: split_target for a search alone,
+// split_target / n for n searches sharing the rounds), the spare blocks go to
+// the dense bound tasks as extra splits, spread evenly (an extra split of a
+// task adds n_tiles units), so the round runs as one wave of shorter units;
+// none once the round fills the share (other tasks never split: their units
+// are short already).  A split holds at least one row of a band.  A window's
+// jobs stay below its tasks + target / n_tiles.  A schedule choice only.
+__host__ __device__ inline int32_t fill_splits(const Geom& g, int32_t target, int32_t units, int32_t nb,
+                                               int32_t rank) {
+    if (target <= 0 || nb <= 0 || units >= target) return 1;
+    const int32_t extra = (target - units) / g.n_tiles;
     const int32_t s = 1 + extra / nb + (rank < extra % nb ? 1 : 0);
     const int32_t cap = g.max_splits < g.band_rows ? g.max_splits : g.band_rows;   // a split holds a row at least
     return s > cap ? cap : s;
+}
+
+// Room for one window's jobs in a round's list: its tasks plus the extra
+// splits fill_splits can give it (at most split_target / n_tiles).
+inline int32_t jobs_per_window(const Geom& g, int32_t max_tasks) {
+    return max_tasks + (g.split_target > 0 ? g.split_target / g.n_tiles : 0) + 1;
 }
 
 // Row pitch of a shared-memory IWE tile: odd, so that the cells of one
@@ -223,7 +232,8 @@ inline int32_t time_buckets(int32_t H) {
     return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
-// Merge buffers of event-split jobs (single-window searches only).
+// Merge buffers of event-split jobs (single-window searches only; without
+// them every split of a band is a split by rows).
 struct Merge {
     uint32_t* acc;                 // [task][planes * M] counts, zero between uses
     int32_t* done;                 // [task][tile] finished splits, zero between uses

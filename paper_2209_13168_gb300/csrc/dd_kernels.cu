@@ -657,7 +657,7 @@ __device__ __forceinline__ void eval_unit(const Geom& g, const UnitPtrs& p, cons
     // Unit ti is row band `band` of polarity plane `plane`: the plane's own
     // run of sorted events, its own image and its own counts.
     const int plane = ti >= g.plane_tiles ? 1 : 0, band = ti - plane * g.plane_tiles;
-    const bool by_rows = splits > 1 && bound_cells(g, tk.D_lo, tk.D_hi, tau) < SPLIT_ROWS_CELLS;
+    const bool by_rows = splits > 1 && (!p.acc || bound_cells(g, tk.D_lo, tk.D_hi, tau) < SPLIT_ROWS_CELLS);
     const int b0 = band * g.band_rows, R = min(b0 + g.band_rows, g.H) - b0;
     const int y0 = by_rows ? b0 + (int)((long long)R * split / splits) : b0;
     const int y1 = by_rows ? b0 + (int)((long long)R * (split + 1) / splits) : b0 + R;
@@ -1223,9 +1223,9 @@ __device__ __forceinline__ float centre(float lo, float hi) {
 
 // One block per window w0 + b: the search state, the first tasks (the centre
 // of the domain and the bound of the domain) and their jobs in the list the
-// next evaluation reads.  `split_ok`: bound tasks may be split (single-window
-// searches).
-__global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all, Task* tasks_all,
+// next evaluation reads.  `sharers`: the searches that share the rounds
+// (their bound tasks split to fill 1/sharers of the grid; 0: never split).
+__global__ void k_init(Geom g, int32_t sharers, int32_t w0, SolveState* st_all, Task* tasks_all,
                        int32_t task_stride, Partial* part_all, const WinIn* wins, const WinParams* params,
                        Job* jobs_all, int32_t job_stride, Sched* sch, int32_t K_pop, int32_t qcap,
                        int64_t max_rounds, int32_t trace_cap) {
@@ -1305,7 +1305,9 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
         b.D_hi = cut[i + 1];
         b.kind = TASK_BOUND;
         const bool dense = bound_cells(g, b.D_lo, b.D_hi, tau) >= DENSE_CELLS;
-        b.splits = split_ok && dense ? fill_splits(g, (1 + n_pieces) * g.n_tiles, n_dense, rank++) : 1;
+        b.splits = sharers > 0 && dense ? fill_splits(g, g.split_target / sharers, (1 + n_pieces) * g.n_tiles,
+                                                      n_dense, rank++)
+                                        : 1;
         tasks[nt++] = b;
         n_jobs += b.splits;
     }
@@ -1332,9 +1334,9 @@ __global__ void k_init(Geom g, int32_t split_ok, int32_t w0, SolveState* st_all,
 cudaError_t launch_init(const Geom& g, int32_t n_windows, SolveState* st, Task* tasks, int32_t task_stride,
                         Partial* part, const WinIn* wins, const WinParams* params, Job* jobs, int32_t job_stride,
                         Sched* sch, int32_t K_pop, int32_t qcap, int64_t max_rounds, int32_t trace_cap,
-                        cudaStream_t s, int32_t w0, int32_t split_ok) {
-    if (split_ok < 0) split_ok = n_windows == 1;
-    k_init<<<n_windows, 32, 0, s>>>(g, split_ok, w0, st, tasks, task_stride, part, wins, params, jobs, job_stride,
+                        cudaStream_t s, int32_t w0, int32_t sharers) {
+    if (sharers < 0) sharers = n_windows;
+    k_init<<<n_windows, 32, 0, s>>>(g, sharers, w0, st, tasks, task_stride, part, wins, params, jobs, job_stride,
                                     sch, K_pop, qcap, max_rounds, trace_cap);
     return cudaGetLastError();
 }
@@ -1409,6 +1411,7 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
     int32_t* phase_out = c.phase_out;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int par = sch->round & 1;
+    const int running = sch->running;             // searches still running after the last round
     SolveState* st = st_all + w;
     Task* tasks = tasks_all + (size_t)w * task_stride;
     Partial* part = part_all + (size_t)w * task_stride;
@@ -1742,6 +1745,10 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
                 nabs += __popc(__ballot_sync(0xffffffffu, q < nt && t_fuse[t] < 0));
             }
             const int units = (nt - nabs) * g.n_tiles;   // one per job and band before any split
+            // the window's share of the grid: the searches still running
+            // after the last round share it (all of them before the first)
+            const int sharers = n_windows == 1 ? 1 : (running > 0 ? running : n_windows);
+            const int target = g.split_target / sharers;
             int total = 0, seen = 0;
             for (int c0 = 0; c0 < nt; c0 += 32) {     // jobs per task, counted once
                 const int q = c0 + lane, t = nt - 1 - q;
@@ -1749,7 +1756,7 @@ __device__ __forceinline__ void control_body(const Geom& g, const CtlArgs& c, in
                 const unsigned db = __ballot_sync(0xffffffffu, d);
                 const int rank = seen + __popc(db & ((1u << lane) - 1u));
                 seen += __popc(db);
-                const int c = q >= nt || t_fuse[t] < 0 ? 0 : (d ? fill_splits(g, units, nd, rank) : 1);
+                const int c = q >= nt || t_fuse[t] < 0 ? 0 : (d ? fill_splits(g, target, units, nd, rank) : 1);
                 if (q < nt) t_jobs[q] = (int16_t)c;
                 total += __reduce_add_sync(0xffffffffu, (unsigned)c);
             }
@@ -1831,7 +1838,7 @@ CtlArgs control_args(int32_t n_windows, SolveState* st, Node* queues, Task* task
     c.sch = sch;
     c.loop = loop;
     c.use_loop = use_loop;
-    c.split_ok = split_ok < 0 ? (n_windows == 1) : split_ok;
+    c.split_ok = split_ok < 0 ? 1 : split_ok;
     c.phase_out = phase_out;
     return c;
 }

@@ -166,7 +166,7 @@ size_t slot_bytes(const dd_server* s) {
                            (s->g.planes > 1 ? sizeof(int8_t) : 0)) +
            sizeof(int32_t) * (3 * (size_t)s->bins + 1) + sizeof(dd::SolveState) +
            sizeof(dd::Node) * 2 * (size_t)s->qcap + sizeof(dd::Task) * (size_t)s->max_tasks +
-           sizeof(dd::Partial) * (size_t)s->max_tasks + sizeof(dd::Job) * 2 * (size_t)s->max_tasks;
+           sizeof(dd::Partial) * (size_t)s->max_tasks + sizeof(dd::Job) * 2 * (size_t)dd::jobs_per_window(s->g, s->max_tasks);
 }
 
 int alloc_server(dd_server* s) {
@@ -196,7 +196,7 @@ int alloc_server(dd_server* s) {
     A((void**)&s->queues, sizeof(dd::Node) * 2 * (size_t)s->qcap * S);
     A((void**)&s->tasks, sizeof(dd::Task) * (size_t)s->max_tasks * S);
     A((void**)&s->part, sizeof(dd::Partial) * (size_t)s->max_tasks * S);
-    s->job_stride = (int)(S * s->max_tasks);
+    s->job_stride = (int)(S * dd::jobs_per_window(s->g, s->max_tasks));
     A((void**)&s->jobs, sizeof(dd::Job) * 2 * (size_t)s->job_stride);
     A((void**)&s->sch, sizeof(dd::Sched));
     A((void**)&s->feat_counts, sizeof(int32_t) * dd::FEATURES);
@@ -247,8 +247,10 @@ cudaError_t upload(dd_server* s, int k, const Request& r) {
 
 // Start the search of request r in slot k (all asynchronous on the serving
 // stream): host-array events are read from the slot's input buffers, where
-// the upload put them; device arrays in place.
-cudaError_t start_search(dd_server* s, int k, const Request& r) {
+// the upload put them; device arrays in place.  `sharers`: the searches of
+// the coming round, this one included (its first bound splits by rows to
+// fill its share of the grid).
+cudaError_t start_search(dd_server* s, int k, const Request& r, int sharers) {
     const dd_events& e = r.ev;
     dd::WinIn& wi = s->h_win[k];
     const size_t off = (size_t)k * s->E;
@@ -299,7 +301,8 @@ cudaError_t start_search(dd_server* s, int k, const Request& r) {
         if (c != cudaSuccess) return c;
     }
     return dd::launch_init(s->g, 1, s->st, s->tasks, s->max_tasks, s->part, s->wins, s->params, s->jobs,
-                           s->job_stride, s->sch, s->pop_k, s->qcap, s->max_rounds, 0, s->stream, k, 0);
+                           s->job_stride, s->sch, s->pop_k, s->qcap, s->max_rounds, 0, s->stream, k,
+                           sharers > 1 ? sharers : 1);
 }
 
 void fill(const dd::SolveState& st, const dd_events& ev, int64_t M, dd_result* out) {
@@ -388,7 +391,7 @@ void loop(dd_server* s) {
     cudaSetDevice(s->device);
     for (;;) {
         std::vector<std::pair<int, uint64_t>> starts;   // searches to start before this round
-        int busy = 0;
+        int busy = 0, searching = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
@@ -433,7 +436,7 @@ void loop(dd_server* s) {
                     uploading += s->up_state[k] != 0;
                 }
                 busy = 0;
-                int searching = 0;
+                searching = 0;
                 for (int k = 0; k < s->S; k++) {
                     busy += s->slot_req[k] != 0;
                     searching += s->slot_req[k] != 0 && s->up_state[k] == 0;
@@ -457,7 +460,7 @@ void loop(dd_server* s) {
                 std::lock_guard<std::mutex> lk(s->mu);
                 r = s->reqs[ad.second];
             }
-            if (start_search(s, ad.first, r) != cudaSuccess) {
+            if (start_search(s, ad.first, r, searching) != cudaSuccess) {
                 fail_all(s, DD_ERR_CUDA);
                 return;
             }
@@ -492,7 +495,7 @@ void loop(dd_server* s) {
         // One round over every busy slot.
         if (dd::launch_eval(s->g, a, s->threads, s->eval_blocks, s->stream) != cudaSuccess ||
             dd::launch_control(s->g, s->S, s->st, s->queues, s->tasks, s->max_tasks, s->part, s->err, nullptr,
-                               s->jobs, s->job_stride, s->sch, 0, 0, s->stream, 0, s->phase) != cudaSuccess ||
+                               s->jobs, s->job_stride, s->sch, 0, 0, s->stream, 1, s->phase) != cudaSuccess ||
             cudaMemcpyAsync(s->h_phase, s->phase, sizeof(int32_t) * s->S, cudaMemcpyDeviceToHost, s->stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -549,7 +552,6 @@ int dd_serve_start(dd_ctx* ctx, int32_t max_slots, int64_t max_events, dd_server
         delete s;
         return DD_ERR_NO_DEVICE;
     }
-    s->g.max_splits = 1;
     if (const dd_mlp* m = dd::ctx_warm_model(ctx)) {
         int dev = -1;
         s->has_model = dd::mlp_device_view(m, &s->model, &dev);
